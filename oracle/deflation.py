@@ -1,0 +1,64 @@
+"""Exact deflation (Sect. 2).
+
+The k smallest singular triplets of a Gamma5-Hermitian D come from the
+eigenpairs of the Hermitian Q = Gamma5 D = X Lambda X^H: the left singular
+vectors are U = Gamma5 X sign(Lambda), the singular values Sigma = |Lambda|
+and the right singular vectors V = X; the k smallest |lambda| give the k
+smallest sigma.  The deflated trace term is (Eq. small_trace_term)
+
+    tr(D^{-1} U_k U_k^H) = tr(U_k^H V_k Sigma_k^{-1}) = sum_i (u_i^H v_i) / sigma_i.
+
+Deflation data are held in the generic form used by the estimator: for the
+traced operator A = D^{-1} = V Sigma^{-1} U^H, left vectors L = V, right
+vectors R = U and values a = 1/sigma, so that A's deflated part is
+L diag(a) R^H and its trace is sum_i a_i r_i^H l_i.
+
+Pinned in tests/test_oracle_deflation.py: the singular values equal a direct
+SVD's, D V = U Sigma, the trace term equals tr(D^{-1} U U^H) from a dense
+inverse, and k = n removes the whole operator (zero-variance samples).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclasses.dataclass
+class Deflation:
+    L: np.ndarray      # (n, k) left vectors of the traced operator
+    R: np.ndarray      # (n, k) right vectors
+    a: np.ndarray      # (k,) singular values of the traced operator
+    lam: np.ndarray    # (k,) eigenvalues of the Hermitian operator they came from
+
+    @property
+    def k(self) -> int:
+        return self.a.shape[0]
+
+    def trace_term(self) -> complex:
+        """sum_i a_i r_i^H l_i (Eq. small_trace_term)."""
+        return complex(np.sum(self.a * np.einsum("ik,ik->k", self.R.conj(), self.L)))
+
+
+def smallest_triplets(D, g5: np.ndarray, k: int):
+    """(sigma, U, V, lam): the k smallest singular triplets of D via eig(Gamma5 D).
+
+    Ordered by increasing |lambda|; dense Hermitian eigensolver (numpy eigh).
+    """
+    Dd = D.toarray() if sp.issparse(D) else np.asarray(D)
+    Q = g5[:, None] * Dd
+    Q = 0.5 * (Q + Q.conj().T)           # exact Hermitian part (Q is Hermitian up to rounding)
+    lam, X = np.linalg.eigh(Q)
+    order = np.argsort(np.abs(lam), kind="stable")[:k]
+    lam, X = lam[order], X[:, order]
+    sigma = np.abs(lam)
+    U = g5[:, None] * X * np.sign(lam)[None, :]
+    V = X
+    return sigma, U, V, lam
+
+
+def coarsest_deflation(D, g5: np.ndarray, k: int) -> Deflation:
+    """Deflation of the traced operator D^{-1} by D's k smallest triplets."""
+    sigma, U, V, lam = smallest_triplets(D, g5, k)
+    return Deflation(L=V, R=U, a=1.0 / sigma, lam=lam)
