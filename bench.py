@@ -1,0 +1,465 @@
+#!/usr/bin/env python
+"""Benchmark of deflated MG-MLMC on GB300: MG-MLMC samples/s on the 128x128
+Wilson-Schwinger workload (3-level multigrid, 4x4 then 2x2 aggregates, 8 test
+vectors per spin, 64 deflated triplets of the coarsest operator, 256 Z2
+vectors per level solved as one multi-RHS block to relative residual 1e-12).
+
+One step = one block of 256 samples on every term of the telescoping sum
+(two multigrid-preconditioned solves per difference-level sample, one solve
+plus the deflation projections for the coarsest term, FP64 sample assembly).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank runs an independent
+replica on its own GPU (the estimator's samples are independent; no data-path
+collective); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+METRIC = "MG-MLMC samples/s"
+UNIT = "samples/s"
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="schwinger-128x128")
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
+                    help="multigrid precision of the headline run (the outer solve is FP64 in both)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--ttt-tol", type=float, default=1e-2,
+                    help="relative error of the time-to-trace run (0 = skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2211_15383_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kclass):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary, if the
+    kernels have not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_sources_sha") != kernel_sources_sha():
+        return None
+    e = d.get("classes", {}).get(kclass)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+def roofline(report, peaks, fp64_peak, fp32_peak):
+    """Roofline of the kernel class with the largest device time."""
+    cls, st = max(report.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_s = st["ms"] * 1e-3 / st["count"]
+    prec = cls.split(".")[-1]
+    bytes_l = st["bytes"] / st["count"]
+    flops_l = st["flops"] / st["count"]
+    if prec == "f64":
+        # FP64 kernels on GB300 are bound by the FP64 pipe (~1/64 of the FP32 rate),
+        # far below their HBM time: ALU roofline against the measured FMA peak.
+        ach = flops_l / per_launch_s / 1e12
+        peak = fp64_peak / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": "measured FP64 FMA throughput (mgmlmc_fma_peak)"}
+    else:
+        ach = bytes_l / per_launch_s / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    out.update({"kernel": cls, "launches": st["count"], "avg_launch_us": per_launch_s * 1e6,
+                "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
+                "traffic": ncu_traffic(cls), "share_of_profiled_time":
+                    st["ms"] / sum(v["ms"] for v in report.values())})
+    return out
+
+
+def class_summary(report, top=8):
+    tot = sum(v["ms"] for v in report.values())
+    items = sorted(report.items(), key=lambda kv: -kv[1]["ms"])[:top]
+    return {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / tot, 4), "launches": v["count"],
+                "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] else None,
+                "TFLOP/s": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] else None}
+            for k, v in items}
+
+
+# ----------------------------------------------------------------------------- GPU runs
+def make_ctx(pkg, w, prec):
+    t0 = time.time()
+    ctx = pkg.Context(mg_precision=prec, max_block_rhs=w.nrhs)
+    ctx.set_gauge(w.gauge())
+    ctx.set_mass(w.m0)
+    t1 = time.time()
+    ctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
+    t2 = time.time()
+    ctx.compute_deflation(w.k, 1e-9, 400)
+    t3 = time.time()
+    return ctx, {"gauge_upload_s": t1 - t0, "hierarchy_s": t2 - t1, "deflation_s": t3 - t2}
+
+
+def run_steps(ctx, w, nterms, first_step, K, seed):
+    for k in range(K):
+        for t in range(nterms):
+            ctx.estimate_level(t, (first_step + k) * w.nrhs, w.nrhs, seed, samples=False)
+
+
+def timed_region(torch, ws, fn):
+    barrier(ws)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(ws)
+    return max_over_ranks(e0.elapsed_time(e1) * 1e-3, ws)
+
+
+def gpu_arm(args, rank, ws, local):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_15383_gb300 as pkg
+
+    w = inputs.workload(args.workload)
+    peaks = measured_peaks()
+    fp64_peak = pkg.fma_peak(64)
+    fp32_peak = pkg.fma_peak(32)
+    ctx, setup = make_ctx(pkg, w, args.precision)
+    nterms, _ = ctx.num_terms()
+    K, W = args.steps, args.warmup
+    seed = w.noise_seed + 7919 * rank
+    run_steps(ctx, w, nterms, 0, W, seed)                                   # warm-up
+    ctx.profile(True, reset=True)
+    clk = Clocks(local)
+    clk.start()
+    sec = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W, K, seed))
+    clocks = clk.stop()
+    ctx.profile(False)
+    report = ctx.profile_report()
+    launches = int(report.pop("__launches__", {}).get("count", 0)) if "__launches__" in report else None
+    samples = K * nterms * w.nrhs * ws
+    value = samples / sec
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": sec / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == 64 else "f64 outer / f32 multigrid",
+           "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, "
+                   f"counter-based Z2 noise",
+           "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "m0": w.m0, "beta": w.beta,
+                      "levels": w.nlevels, "agg": [list(a) for a in w.agg], "nvec": list(w.nvec),
+                      "deflated_triplets": w.k, "block_rhs": w.nrhs, "terms": nterms,
+                      "solve_tol": 1e-12, "mg_precision": args.precision,
+                      "l2": "inputs exceed L2: one FP64 fine-level block of 256 rhs is "
+                            f"{2 * w.Lx * w.Lt * w.nrhs * 16 / 1e6:.0f} MB > 129 MB",
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+           "setup": setup, "clocks": clocks,
+           "roofline": roofline(report, peaks, fp64_peak, fp32_peak),
+           "kernel_classes": class_summary(report),
+           "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
+                     "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
+           "iters": {t: ctx.get_stats(t)["iters"] for t in range(nterms)}}
+    if launches is not None:
+        out["gpu_launches"] = launches
+    # end-to-end through the public C ABI with host probe vectors and host samples
+    if not args.no_e2e:
+        dims = w.level_dims()
+        _, levels = ctx.num_terms()
+        n_of = [dims[lv - 1][0] * dims[lv - 1][1] * dims[lv - 1][2] for lv in levels]
+        probes = []
+        for k in range(K):
+            per = []
+            for t in range(nterms):
+                u = inputs.uniform(9000 + rank, 100 * k + t, w.nrhs * n_of[t])
+                arr = torch.empty((w.nrhs, n_of[t]), dtype=torch.int8, pin_memory=True)
+                arr.numpy()[:] = np.where(u < 0.5, 1, -1).reshape(w.nrhs, n_of[t])
+                per.append(arr)
+            probes.append(per)
+        outs = [torch.empty((w.nrhs, 2), dtype=torch.float64, pin_memory=True) for _ in range(nterms)]
+
+        def e2e_steps():
+            for k in range(K):
+                for t in range(nterms):
+                    o = outs[t].numpy().view(np.complex128).reshape(-1)
+                    ctx.estimate_level_probes(t, probes[k][t].numpy(), out=o)
+
+        sec_e2e = timed_region(torch, ws, e2e_steps)
+        out["e2e"] = {"value": samples / sec_e2e, "unit": UNIT,
+                      "h2d_bytes_per_step": int(sum(w.nrhs * n for n in n_of)),
+                      "d2h_bytes_per_step": int(nterms * w.nrhs * 16),
+                      "path": "mgmlmc_estimate_level_probes: pinned host int8 probes in, host samples out"}
+    # time to tr(D^-1) at a fixed relative error (MLMC loop of the library)
+    if args.ttt_tol > 0:
+        t0 = time.time()
+        res = ctx.estimate_trace(args.ttt_tol, 10 ** 6, seed + 1)
+        ttt = time.time() - t0
+        out["time_to_trace"] = {"rel_tol": args.ttt_tol, "seconds_excl_setup": ttt,
+                                "seconds_incl_setup": ttt + sum(setup.values()),
+                                "trace": [res["trace"].real, res["trace"].imag], "rel_err": res["rel_err"],
+                                "converged": bool(res["converged"]),
+                                "samples_per_term": [t["nsamples"] for t in res["terms"]]}
+    # mixed precision on the same workload, error against the FP64 run
+    if not args.no_mixed and args.precision == 64:
+        ref = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+        ctx.close()
+        torch.cuda.empty_cache()
+        mctx, msetup = make_ctx(pkg, w, 32)
+        got = [mctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+        errs = [float(np.max(np.abs(g - r) / np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2)))))
+                for g, r in zip(got, ref)]
+        run_steps(mctx, w, nterms, 0, W, seed)
+        mctx.profile(True, reset=True)
+        msec = timed_region(torch, ws, lambda: run_steps(mctx, w, nterms, W, K, seed))
+        mctx.profile(False)
+        mrep = mctx.profile_report()
+        mrep.pop("__launches__", None)
+        fine = {k: v for k, v in mrep.items() if k.startswith("D1.f32")}
+        stencil = None
+        if fine:
+            v = fine["D1.f32"]
+            stencil = {"kernel": "D1.f32 (fine Wilson stencil)", "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                       "frac_of_measured_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                       "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
+                       "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"]}
+        out["mixed"] = {"value": samples / msec, "unit": UNIT, "ms_per_step": msec / K * 1e3,
+                        "speedup_vs_f64": (samples / msec) / value, "setup": msetup,
+                        "max_rel_sample_error_vs_f64_per_term": errs,
+                        "roofline": roofline(mrep, peaks, fp64_peak, fp32_peak),
+                        "kernel_classes": class_summary(mrep), "stencil_hbm": stencil}
+        mctx.close()
+    else:
+        ctx.close()
+    return out, w
+
+
+# ----------------------------------------------------------------------------- CPU (oracle)
+_W = {}
+
+
+def _cpu_init(H, defl):
+    from oracle import estimator as oest
+    _W["H"], _W["defl"] = H, defl
+    _W["S"] = oest.DirectSolvers(H)
+    _W["terms"] = oest.term_list(H.nlevels)
+    for lev in range(1, H.nlevels + 1):   # factorise up front
+        _W["S"].solve(lev, np.zeros((H.D[lev - 1].shape[0], 1), np.complex128))
+
+
+def _cpu_job(job):
+    from oracle import estimator as oest
+    t, first, count, seed = job
+    term = _W["terms"][t]
+    d = _W["defl"] if term[1] is None else None
+    s = oest.noise_samples(_W["H"], term, seed, first, count, _W["S"], d)
+    return len(s)
+
+
+def cpu_oracle_setup(w):
+    from oracle import deflation as odefl
+    from oracle import hierarchy as ohier
+    t0 = time.time()
+    H = ohier.build_hierarchy(w.gauge(), w.m0, w.agg, w.nvec, w.start_vectors(), w.setup_iters)
+    defl = odefl.coarsest_deflation(H.D[-1], H.g5[-1], w.k)
+    return H, defl, time.time() - t0
+
+
+def cpu_oracle_rate(w, H, defl, seconds, procs, per_term=None):
+    """Samples/s of the oracle (direct sparse-LU solves), the same per-step mix of
+    terms, samples split over `procs` single-threaded spawned processes."""
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+    ctxm = mp.get_context("spawn")
+    nterms = H.nlevels
+    with ctxm.Pool(procs, initializer=_cpu_init, initargs=(H, defl)) as pool:
+        pool.map(_cpu_job, [(t, 10 ** 7 + p, 1, w.noise_seed) for p in range(procs) for t in range(nterms)])
+        if per_term is None:   # size the sample for ~`seconds` of wall time
+            t0 = time.time()
+            pool.map(_cpu_job, [(t, 2 * 10 ** 7 + p, 1, w.noise_seed) for p in range(procs) for t in range(nterms)])
+            one = time.time() - t0
+            per_term = max(1, int(seconds / one))
+        jobs = [(t, 3 * 10 ** 7 + 1000 * p, per_term, w.noise_seed) for p in range(procs) for t in range(nterms)]
+        t0 = time.time()
+        n = sum(pool.map(_cpu_job, jobs))
+        dt = time.time() - t0
+    return n / dt, n, dt, per_term
+
+
+def cpu_baseline(w, seconds):
+    procs = os.cpu_count() or 1
+    H, defl, setup_s = cpu_oracle_setup(w)
+    rate, n, dt, per = cpu_oracle_rate(w, H, defl, seconds, procs)
+    return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{n} samples ({per} per term per process, {H.nlevels} terms, {procs} spawned "
+                      f"single-threaded processes) of {w.name}, direct sparse-LU solves; "
+                      f"{dt:.1f} s wall; oracle setup {setup_s:.0f} s not timed"}
+
+
+def reference_arm(args, rank, ws):
+    """The oracle timed on the host cores (rank 0 only)."""
+    w = inputs.workload(args.workload)
+    if rank != 0:
+        return None
+    procs = os.cpu_count() or 1
+    H, defl, setup_s = cpu_oracle_setup(w)
+    budget = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    _, _, _, per = cpu_oracle_rate(w, H, defl, budget, procs)
+    rates, times, ns = [], [], []
+    for k in range(args.warmup + args.steps):
+        r, n, dt, _ = cpu_oracle_rate(w, H, defl, budget, procs, per_term=per)
+        if k >= args.warmup:
+            rates.append(r)
+            times.append(dt)
+            ns.append(n)
+    value = sum(ns) / sum(times)
+    sample = (f"each step {ns[0]} samples ({per} per term per process, {H.nlevels} terms, {procs} spawned "
+              f"single-threaded processes) of {w.name} by direct sparse-LU solves; setup {setup_s:.0f} s not timed")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+            "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, Z2 noise",
+            "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "levels": w.nlevels,
+                       "deflated_triplets": w.k, "block_rhs": w.nrhs},
+            "cpu_baseline": {"kind": "oracle", "cores": procs, "sample": sample, "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_setup(args)
+    if args.impl == "reference":
+        out = reference_arm(args, rank, ws)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    out, w = gpu_arm(args, rank, ws, local)
+    if rank == 0:
+        if not args.no_cpu and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

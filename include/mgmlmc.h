@@ -1,0 +1,234 @@
+/*
+ * mgmlmc.h -- C ABI of the GB300 (sm_103a) deflated multigrid multilevel
+ * Monte Carlo library: stochastic estimation of tr(D^{-1}) for the 2D
+ * Wilson-Schwinger operator D (Frommer & Ramirez-Hidalgo, "Deflated Multigrid
+ * Multilevel Monte Carlo", Lattice 2022).
+ *
+ * General conventions
+ *  - Every call returns an int status (mgmlmc_status); no exception, abort or
+ *    exit crosses the ABI.  After a failure mgmlmc_last_error(ctx) holds text.
+ *  - Complex numbers are interleaved (re, im) doubles.  Host arrays are owned
+ *    by the caller and only read or written during the call.
+ *  - Device state (gauge links, hierarchy, deflation space, Krylov work space)
+ *    is owned by the context and released by mgmlmc_destroy.  Device memory is
+ *    taken from the caller's allocator callback when one is given (the Python
+ *    binding passes PyTorch's caching allocator), else from cudaMalloc.
+ *  - All GPU work runs on the CUDA stream given to mgmlmc_create.  Calls that
+ *    return host data synchronise that stream.  A context is not thread safe.
+ *  - Vectors of level l have n_l = sites_l * d_l complex entries ordered
+ *    site-major (site = x + lx * t), then dof; d_1 = 2 (spin), d_l = 2 nvec_{l-1}
+ *    on coarse levels, whose first nvec dof form spin block 0 (Gamma5 = +1) and
+ *    the next nvec spin block 1 (Gamma5 = -1).
+ *  - Multi-vector host arrays are [vector][n_l] (one vector after another).
+ */
+#ifndef MGMLMC_H
+#define MGMLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGMLMC_MAX_LEVELS 6
+
+typedef enum {
+    MGMLMC_OK = 0,
+    MGMLMC_EINVAL = -1,          /* invalid argument                                  */
+    MGMLMC_ENOMEM = -2,          /* device or host allocation refused                 */
+    MGMLMC_ENOTCONVERGED = -3,   /* an iteration hit its cap; partial results marked   */
+    MGMLMC_ETIMEOUT = -4,        /* a bounded device wait gave up                      */
+    MGMLMC_ECUDA = -5,           /* CUDA runtime error                                 */
+    MGMLMC_ENOTIMPL = -6,        /* combination not implemented                        */
+    MGMLMC_ENAN = -7,            /* NaN/Inf met in the data                            */
+    MGMLMC_ESTATE = -8           /* call out of order (e.g. estimate before hierarchy) */
+} mgmlmc_status;
+
+typedef struct mgmlmc_ctx mgmlmc_ctx;
+
+/* Device allocator hooks: alloc returns a device pointer (NULL = refused). */
+typedef void* (*mgmlmc_alloc_fn)(void* user, size_t bytes);
+typedef void (*mgmlmc_free_fn)(void* user, void* ptr);
+
+typedef struct {
+    int mg_precision;     /* 64: FP64 multigrid preconditioner ("plain FP64 path");
+                             32: FP32 V-cycle with a BF16 tensor-core coarsest solve
+                             (mixed).  The outer FGMRES, its residuals and every sample
+                             are FP64 in both cases.                          [64]    */
+    double solve_tol;     /* relative residual ||b - D x|| / ||b|| of every solve;
+                             Sect. 4.3 uses 1e-12.                             [1e-12] */
+    int fgmres_restart;   /* Krylov basis size m of the outer FGMRES(m).       [24]    */
+    int max_iters;        /* cap on outer iterations of one solve.             [2000]  */
+    int nu_pre;           /* pre-smoothing MR steps per level (Eq. two_level_mg). [0]  */
+    int nu_post;          /* post-smoothing MR steps per level.                [4]     */
+    int max_block_rhs;    /* most right-hand sides solved together.            [256]   */
+    int verbose;          /* 1: iteration counts on stderr.                    [0]     */
+} mgmlmc_options;
+
+/* Per-term statistics of the samples drawn so far (FP64, Sect. 3.2). */
+typedef struct {
+    int64_t nsamples;     /* N_l                                   */
+    double sum_re, sum_im;/* sum of samples s_j                    */
+    double sum_abs2;      /* sum of |s_j|^2                         */
+    double mean_re, mean_im;
+    double variance;      /* unbiased E|s - mean|^2                 */
+    double seconds;       /* device time spent on this term         */
+    int64_t iters;        /* outer FGMRES iterations, summed        */
+} mgmlmc_level_stats;
+
+typedef struct {
+    double trace_re, trace_im;   /* sum of term means + deflated part          */
+    double rel_err;              /* sqrt(sum_l V_l / N_l) / |trace|             */
+    double deflated_part;        /* tr(V Sigma^{-1} U^H) term (real part)       */
+    int nterms;
+    int converged;               /* rel_err <= rel_tol                          */
+    int rounds;
+    mgmlmc_level_stats term[MGMLMC_MAX_LEVELS];
+} mgmlmc_trace_result;
+
+/* Operators for mgmlmc_apply. */
+typedef enum {
+    MGMLMC_OP_D = 0,      /* y = D_l x                       (l = 1..L)           */
+    MGMLMC_OP_PH = 1,     /* y = P_l^H x   (level l -> l+1)   (l = 1..L-1)         */
+    MGMLMC_OP_P = 2,      /* y = P_l x     (level l+1 -> l)   (l = 1..L-1)         */
+    MGMLMC_OP_G5 = 3,     /* y = Gamma5^l x                                         */
+    MGMLMC_OP_PREC = 4,   /* y = one multigrid cycle from level l applied to x      */
+    MGMLMC_OP_DINV_C = 5  /* y = stored inverse of the coarsest D_L applied to x    */
+} mgmlmc_opkind;
+
+/* Fill *opt with the defaults shown in brackets above. */
+void mgmlmc_default_options(mgmlmc_options* opt);
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  alloc/free may be NULL (then cudaMalloc and
+ * cudaFree).  opt may be NULL (defaults).  On success *out owns all state. */
+int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream,
+                  mgmlmc_alloc_fn alloc, mgmlmc_free_fn free_fn, void* alloc_user);
+
+/* Release every device allocation of the context, then the context. */
+void mgmlmc_destroy(mgmlmc_ctx* ctx);
+
+/* Text of the last error of this context ("" if none).  Valid until the next call. */
+const char* mgmlmc_last_error(const mgmlmc_ctx* ctx);
+
+/* Gauge field (Sect. 1: U(1) links of the Schwinger model).  theta is a host
+ * array [t][x][mu] of Lt*Lx*2 link angles, U_mu(x) = exp(i theta); mu = 0 is
+ * space (periodic), mu = 1 is time (antiperiodic fermion boundary).  Lx, Lt
+ * even and >= 2.  Invalidates any hierarchy and deflation. */
+int mgmlmc_set_gauge(mgmlmc_ctx* ctx, int Lx, int Lt, const double* theta);
+
+/* Wilson mass m0: D = (m0 + 2) - 1/2 sum_mu [(1 - sigma_mu) U_mu(x) T_{+mu}
+ * + (1 + sigma_mu) U_mu^*(x - mu) T_{-mu}] with sigma_0 = sigma_1, sigma_1 =
+ * sigma_2 (Pauli), Gamma5 = sigma_3.  Invalidates hierarchy and deflation. */
+int mgmlmc_set_mass(mgmlmc_ctx* ctx, double m0);
+
+/* Multigrid hierarchy (Sect. 3.1; spin-preserving aggregation, Sect. 4.2).
+ * nlevels = L in 1..MGMLMC_MAX_LEVELS; for l = 1..L-1 aggregates of
+ * agg_x[l-1] x agg_t[l-1] sites of level l and nvec[l-1] test vectors.
+ * start_vectors[l-1] is a host array [nvec][n_l] of complex start vectors;
+ * the setup runs setup_iters rounds of inverse iteration v <- D_l^{-1} v
+ * (solved to relative residual setup_tol), v <- v/||v||, then orthonormalises
+ * each vector's restriction to an (aggregate, spin block) in vector order
+ * (modified Gram-Schmidt) to form P_l, and D_{l+1} = P_l^H D_l P_l.
+ * setup_iters = 0 uses the start vectors as they are.  Returns
+ * MGMLMC_EINVAL if a block has fewer rows than nvec or a vector block is
+ * rank deficient.  Invalidates deflation. */
+int mgmlmc_set_hierarchy(mgmlmc_ctx* ctx, int nlevels, const int* agg_x, const int* agg_t,
+                         const int* nvec, int setup_iters, double setup_tol,
+                         const double* const* start_vectors);
+
+/* Terms of the telescoping sum (Eq. mgmlmc).  nskip levels listed in skip
+ * (2..L-1) are left out of the sum, giving Eq. skip_level for skip = {2}:
+ * tr(D^{-1}) = tr(D_1^{-1} - P_1 P_2 D_3^{-1} P_2^H P_1^H) + ... .  nskip = 0
+ * restores the plain sum.  Term t (0-based) then has fine level
+ * term_level[t] and coarse level term_level[t+1] (none for the last term). */
+int mgmlmc_set_terms(mgmlmc_ctx* ctx, int nskip, const int* skip);
+int mgmlmc_num_terms(const mgmlmc_ctx* ctx, int* nterms, int* term_level /* [MGMLMC_MAX_LEVELS] */);
+
+/* Exact deflation of the coarsest term (Sect. 2): the k smallest singular
+ * triplets of D_L from the eigenpairs of Q_L = Gamma5^L D_L (U = Gamma5 X
+ * sign(Lambda), Sigma = |Lambda|, V = X), found by subspace iteration on
+ * Q_L^{-1} with Rayleigh-Ritz until every residual ||Q x - lambda x|| <=
+ * tol |lambda| (Sect. 4.3 uses tol = 1e-9), at most max_iters iterations.
+ * k = 0 removes deflation.  Also computes tau = tr(V Sigma^{-1} U^H) (Eq.
+ * small_trace_term) in FP64 from the stored factors. */
+int mgmlmc_compute_deflation(mgmlmc_ctx* ctx, int k, double tol, int max_iters);
+
+/* Host copies of the deflation: lambda[k], sigma[k], U and V as [k][n_L]
+ * complex, tau (2 doubles).  Any pointer may be NULL. */
+int mgmlmc_get_deflation(mgmlmc_ctx* ctx, double* lambda, double* sigma, double* U,
+                         double* V, double* tau);
+
+/* nsamples Hutchinson samples of term t (0-based; Sect. 3.2):
+ *   s_j = x_j^H D_a^{-1} x_j - (P^H x_j)^H D_b^{-1} (P^H x_j)   (difference term)
+ *   s_j = x_j^H D_L^{-1} x_j - (V^H x_j)^H Sigma^{-1} (U^H x_j) (deflated coarsest)
+ * with P = P_{a->b} the prolongation between the term's levels and x_j the Z2
+ * vector j = first_sample + i drawn on the device: entry k is +1 or -1 by the
+ * low bit of sm(sm(sm(seed ^ a) ^ j) ^ k), sm = one splitmix64 step.  Solves to
+ * opt.solve_tol in blocks of at most opt.max_block_rhs.  samples_out (host,
+ * 2*nsamples doubles, may be NULL) receives s_j; *stats (may be NULL) receives
+ * this call's statistics, and the context adds them to the term's running
+ * totals.  MGMLMC_ENOTCONVERGED if a solve hit opt.max_iters. */
+int mgmlmc_estimate_level(mgmlmc_ctx* ctx, int term, int64_t first_sample, int nsamples,
+                          uint64_t seed, double* samples_out, mgmlmc_level_stats* stats);
+
+/* Same as mgmlmc_estimate_level but with caller-supplied real probe vectors:
+ * probes is a host array [nsamples][n_a] of signed bytes (the entries of x_j,
+ * e.g. +-1 for Z2 noise), copied to the device inside the call. */
+int mgmlmc_estimate_level_probes(mgmlmc_ctx* ctx, int term, int nsamples, const int8_t* probes,
+                                 double* samples_out, mgmlmc_level_stats* stats);
+
+/* Running totals of term t since the last mgmlmc_reset_stats. */
+int mgmlmc_get_stats(mgmlmc_ctx* ctx, int term, mgmlmc_level_stats* stats);
+int mgmlmc_reset_stats(mgmlmc_ctx* ctx);
+
+/* Multilevel Monte Carlo estimate of tr(D^{-1}) (Eq. mgmlmc, with deflation
+ * of the coarsest term when computed): pilot of 16 samples per term, then
+ * rounds that raise N_l towards eps^-2 sqrt(V_l/C_l) sum_m sqrt(V_m C_m)
+ * (eps = rel_tol |estimate|; at most doubling per round) until
+ * sqrt(sum_l V_l/N_l) <= rel_tol |estimate| or max_samples in total.
+ * costs[t] gives fixed per-sample costs C_l (NULL: measured device seconds).
+ * Sample indices of term t run 0, 1, 2, ... on the noise stream of seed. */
+int mgmlmc_estimate_trace(mgmlmc_ctx* ctx, double rel_tol, int64_t max_samples, uint64_t seed,
+                          const double* costs, mgmlmc_trace_result* out);
+
+/* Test hook: y = op(x) for nrhs host vectors [nrhs][n_in] -> [nrhs][n_out]. */
+int mgmlmc_apply(mgmlmc_ctx* ctx, int op, int level, int nrhs, const double* x, double* y);
+
+/* Solve D_l x = b for nrhs host vectors [nrhs][n_l] with the outer FGMRES to
+ * opt.solve_tol; *iters (may be NULL) receives the outer iteration count. */
+int mgmlmc_solve(mgmlmc_ctx* ctx, int level, int nrhs, const double* b, double* x, int* iters);
+
+/* Test hook: the Z2 vectors of mgmlmc_estimate_level as doubles [nsamples][n_l]. */
+int mgmlmc_noise(mgmlmc_ctx* ctx, int level, int64_t first_sample, int nsamples, uint64_t seed,
+                 double* x);
+
+/* Test hook: the test vectors after the setup iteration, [nvec][n_l] complex. */
+int mgmlmc_get_test_vectors(mgmlmc_ctx* ctx, int level, double* v);
+
+/* Per-operation timing (Sect. 4.3 times D_l, deflations, P_l, P_l^H and axpy
+ * separately): with enable = 1 every launch of a kernel class is bracketed by
+ * CUDA events on the context's stream and its algorithmic bytes and flops are
+ * recorded; reset = 1 clears the totals.  Classes: "D<l>.<prec>" operator
+ * applications, "PH<l>", "P<l>" restriction/prolongation, "Dinv.<prec>"
+ * coarsest solve, "mr<l>" smoother updates, "orth" Gram-Schmidt, "defl"
+ * deflation projections. */
+int mgmlmc_profile(mgmlmc_ctx* ctx, int enable, int reset);
+
+/* JSON object {class: {"count", "ms", "bytes", "flops"}} of the totals so far,
+ * written to buf (capacity cap, NUL-terminated); *needed receives the length. */
+int mgmlmc_profile_report(mgmlmc_ctx* ctx, char* buf, size_t cap, size_t* needed);
+
+/* Measurement helper (no counterpart in the paper): achieved fused
+ * multiply-add throughput of the current device in FLOP/s for precision 64 or
+ * 32, from a kernel of independent FMA chains on every SM (best of 3). */
+int mgmlmc_fma_peak(int precision, double* flops_per_s);
+
+/* Level geometry: sites per direction, dof per site, n_l. */
+int mgmlmc_level_info(const mgmlmc_ctx* ctx, int level, int* lx, int* lt, int* d, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGMLMC_H */

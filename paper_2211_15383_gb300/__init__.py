@@ -1,0 +1,8 @@
+"""GB300 (sm_103a) deflated multigrid multilevel Monte Carlo for tr(D^{-1}) of
+the 2D Wilson-Schwinger operator (Frommer & Ramirez-Hidalgo, Lattice 2022).
+
+The computation lives in ``libmgmlmc.so`` (CUDA kernels behind the C ABI of
+``include/mgmlmc.h``); ``Context`` is its thin Python binding.
+"""
+from ._lib import (Context, MgmlmcError, Options, default_options, fma_peak, load, LIB_PATH,  # noqa: F401
+                   OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C)

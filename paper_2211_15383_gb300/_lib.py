@@ -1,0 +1,321 @@
+"""Thin Python binding of the C ABI in include/mgmlmc.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libmgmlmc.so``.  PyTorch provides the device memory (its caching
+allocator, through the library's allocator callback) and the CUDA stream.
+There is no CPU fallback: without the built library or a CUDA device the
+binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmgmlmc.so")
+
+MAX_LEVELS = 6
+OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C = range(6)
+
+STATUS = {0: "MGMLMC_OK", -1: "MGMLMC_EINVAL", -2: "MGMLMC_ENOMEM", -3: "MGMLMC_ENOTCONVERGED",
+          -4: "MGMLMC_ETIMEOUT", -5: "MGMLMC_ECUDA", -6: "MGMLMC_ENOTIMPL", -7: "MGMLMC_ENAN",
+          -8: "MGMLMC_ESTATE"}
+
+
+class MgmlmcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("mg_precision", C.c_int), ("solve_tol", C.c_double), ("fgmres_restart", C.c_int),
+                ("max_iters", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
+                ("max_block_rhs", C.c_int), ("verbose", C.c_int)]
+
+
+class LevelStats(C.Structure):
+    _fields_ = [("nsamples", C.c_int64), ("sum_re", C.c_double), ("sum_im", C.c_double),
+                ("sum_abs2", C.c_double), ("mean_re", C.c_double), ("mean_im", C.c_double),
+                ("variance", C.c_double), ("seconds", C.c_double), ("iters", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TraceResult(C.Structure):
+    _fields_ = [("trace_re", C.c_double), ("trace_im", C.c_double), ("rel_err", C.c_double),
+                ("deflated_part", C.c_double), ("nterms", C.c_int), ("converged", C.c_int),
+                ("rounds", C.c_int), ("term", LevelStats * MAX_LEVELS)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+# (name, restype, argtypes) of every entry point declared in include/mgmlmc.h
+SIGNATURES = [
+    ("mgmlmc_default_options", None, [C.POINTER(Options)]),
+    ("mgmlmc_create", C.c_int, [C.POINTER(_P), C.POINTER(Options), _P, ALLOC_FN, FREE_FN, _P]),
+    ("mgmlmc_destroy", None, [_P]),
+    ("mgmlmc_last_error", C.c_char_p, [_P]),
+    ("mgmlmc_set_gauge", C.c_int, [_P, C.c_int, C.c_int, _D]),
+    ("mgmlmc_set_mass", C.c_int, [_P, C.c_double]),
+    ("mgmlmc_set_hierarchy", C.c_int, [_P, C.c_int, _I, _I, _I, C.c_int, C.c_double, C.POINTER(_D)]),
+    ("mgmlmc_set_terms", C.c_int, [_P, C.c_int, _I]),
+    ("mgmlmc_num_terms", C.c_int, [_P, _I, _I]),
+    ("mgmlmc_compute_deflation", C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
+    ("mgmlmc_get_deflation", C.c_int, [_P, _D, _D, _D, _D, _D]),
+    ("mgmlmc_estimate_level", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D, C.POINTER(LevelStats)]),
+    ("mgmlmc_estimate_level_probes", C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int8), _D,
+                                               C.POINTER(LevelStats)]),
+    ("mgmlmc_get_stats", C.c_int, [_P, C.c_int, C.POINTER(LevelStats)]),
+    ("mgmlmc_reset_stats", C.c_int, [_P]),
+    ("mgmlmc_estimate_trace", C.c_int, [_P, C.c_double, C.c_int64, C.c_uint64, _D, C.POINTER(TraceResult)]),
+    ("mgmlmc_apply", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D, _D]),
+    ("mgmlmc_solve", C.c_int, [_P, C.c_int, C.c_int, _D, _D, _I]),
+    ("mgmlmc_noise", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D]),
+    ("mgmlmc_get_test_vectors", C.c_int, [_P, C.c_int, _D]),
+    ("mgmlmc_level_info", C.c_int, [_P, C.c_int, _I, _I, _I, C.POINTER(C.c_int64)]),
+    ("mgmlmc_profile", C.c_int, [_P, C.c_int, C.c_int]),
+    ("mgmlmc_profile_report", C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    ("mgmlmc_fma_peak", C.c_int, [C.c_int, _D]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmgmlmc.so and declare every entry point (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise MgmlmcError(-5, f"{path} not built: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _cplx(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def fma_peak(precision: int) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device, precision 64 or 32."""
+    v = C.c_double()
+    code = load().mgmlmc_fma_peak(int(precision), C.byref(v))
+    if code != 0:
+        raise MgmlmcError(code, "fma_peak failed")
+    return v.value
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().mgmlmc_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One mgmlmc context: all device state of one trace problem.
+
+    Methods carry the names of the C entry points without the ``mgmlmc_``
+    prefix.  Host arrays use numpy; vectors of level l are complex arrays of
+    shape (nvec, n_l).
+    """
+
+    def __init__(self, options: Options | None = None, torch_memory: bool = True, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise MgmlmcError(-5, "a CUDA device is required (this library has no CPU path)")
+        self.lib = load()
+        self.options = options if options is not None else default_options(**kw)
+        self._mem = {}
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if torch_memory:
+            def _alloc(user, nbytes):
+                try:
+                    t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+                except Exception:
+                    return None
+                self._mem[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(user, ptr):
+                self._mem.pop(ptr, None)
+
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+        else:
+            self._alloc_cb, self._free_cb = ALLOC_FN(), FREE_FN()
+        h = C.c_void_p()
+        self._check(self.lib.mgmlmc_create(C.byref(h), C.byref(self.options), stream, self._alloc_cb,
+                                           self._free_cb, None), h)
+        self.h = h
+
+    # ---------------------------------------------------------------- plumbing
+    def _check(self, code, h=None):
+        if code != 0:
+            hh = h if h is not None else self.h
+            msg = self.lib.mgmlmc_last_error(hh).decode() if hh else ""
+            raise MgmlmcError(code, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgmlmc_destroy(self.h)
+            self.h = None
+            self._mem.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- problem
+    def set_gauge(self, theta: np.ndarray):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        Lt, Lx, two = th.shape
+        assert two == 2
+        self._check(self.lib.mgmlmc_set_gauge(self.h, Lx, Lt, _dptr(th)))
+
+    def set_mass(self, m0: float):
+        self._check(self.lib.mgmlmc_set_mass(self.h, float(m0)))
+
+    def set_hierarchy(self, agg, nvec, start_vectors, setup_iters: int = 4, setup_tol: float = 1e-12):
+        nl = len(agg) + 1
+        ax = (C.c_int * max(1, nl - 1))(*[a[0] for a in agg])
+        at = (C.c_int * max(1, nl - 1))(*[a[1] for a in agg])
+        nv = (C.c_int * max(1, nl - 1))(*list(nvec))
+        keep = [_cplx(v) for v in start_vectors]
+        ptrs = (_D * max(1, nl - 1))(*[k.ctypes.data_as(_D) for k in keep])
+        self._check(self.lib.mgmlmc_set_hierarchy(self.h, nl, ax, at, nv, int(setup_iters), float(setup_tol), ptrs))
+
+    def set_terms(self, skip=()):
+        arr = (C.c_int * max(1, len(skip)))(*skip)
+        self._check(self.lib.mgmlmc_set_terms(self.h, len(skip), arr))
+
+    def num_terms(self):
+        n = C.c_int()
+        lv = (C.c_int * MAX_LEVELS)()
+        self._check(self.lib.mgmlmc_num_terms(self.h, C.byref(n), lv))
+        return n.value, list(lv)[: n.value]
+
+    def level_info(self, level: int):
+        lx, lt, d, n = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+        self._check(self.lib.mgmlmc_level_info(self.h, level, C.byref(lx), C.byref(lt), C.byref(d), C.byref(n)))
+        return lx.value, lt.value, d.value, n.value
+
+    # ---------------------------------------------------------------- deflation
+    def compute_deflation(self, k: int, tol: float = 1e-9, max_iters: int = 200):
+        self._check(self.lib.mgmlmc_compute_deflation(self.h, int(k), float(tol), int(max_iters)))
+
+    def get_deflation(self, k: int, L: int):
+        n = self.level_info(L)[3]
+        lam, sig = np.zeros(k), np.zeros(k)
+        U = np.zeros((k, n), np.complex128)
+        V = np.zeros((k, n), np.complex128)
+        tau = np.zeros(2)
+        self._check(self.lib.mgmlmc_get_deflation(self.h, _dptr(lam), _dptr(sig), U.ctypes.data_as(_D),
+                                                  V.ctypes.data_as(_D), _dptr(tau)))
+        return lam, sig, U, V, complex(tau[0], tau[1])
+
+    # ---------------------------------------------------------------- estimation
+    def estimate_level(self, term: int, first: int, nsamples: int, seed: int, samples: bool = True):
+        out = np.zeros(nsamples, np.complex128) if samples else None
+        st = LevelStats()
+        ptr = out.ctypes.data_as(_D) if samples else None
+        self._check(self.lib.mgmlmc_estimate_level(self.h, term, int(first), int(nsamples), C.c_uint64(seed),
+                                                   ptr, C.byref(st)))
+        return out, st.as_dict()
+
+    def estimate_level_probes(self, term: int, probes: np.ndarray, samples: bool = True, out=None):
+        pr = np.ascontiguousarray(probes, dtype=np.int8)
+        ns = pr.shape[0]
+        if out is None and samples:
+            out = np.zeros(ns, np.complex128)
+        st = LevelStats()
+        self._check(self.lib.mgmlmc_estimate_level_probes(
+            self.h, term, ns, pr.ctypes.data_as(C.POINTER(C.c_int8)),
+            out.ctypes.data_as(_D) if out is not None else None, C.byref(st)))
+        return out, st.as_dict()
+
+    def get_stats(self, term: int):
+        st = LevelStats()
+        self._check(self.lib.mgmlmc_get_stats(self.h, term, C.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(self.lib.mgmlmc_reset_stats(self.h))
+
+    def estimate_trace(self, rel_tol: float, max_samples: int, seed: int, costs=None):
+        res = TraceResult()
+        cst = None
+        if costs is not None:
+            arr = np.ascontiguousarray(costs, dtype=np.float64)
+            cst = _dptr(arr)
+        self._check(self.lib.mgmlmc_estimate_trace(self.h, float(rel_tol), int(max_samples), C.c_uint64(seed),
+                                                   cst, C.byref(res)))
+        d = {k: getattr(res, k) for k, _ in TraceResult._fields_ if k != "term"}
+        d["terms"] = [res.term[t].as_dict() for t in range(res.nterms)]
+        d["trace"] = complex(res.trace_re, res.trace_im)
+        return d
+
+    # ---------------------------------------------------------------- test hooks
+    def apply(self, op: int, level: int, x: np.ndarray, n_out: int):
+        xx = _cplx(np.atleast_2d(x))
+        y = np.zeros((xx.shape[0], n_out), np.complex128)
+        self._check(self.lib.mgmlmc_apply(self.h, op, level, xx.shape[0], xx.ctypes.data_as(_D),
+                                          y.ctypes.data_as(_D)))
+        return y
+
+    def solve(self, level: int, b: np.ndarray):
+        bb = _cplx(np.atleast_2d(b))
+        x = np.zeros_like(bb)
+        it = C.c_int()
+        self._check(self.lib.mgmlmc_solve(self.h, level, bb.shape[0], bb.ctypes.data_as(_D),
+                                          x.ctypes.data_as(_D), C.byref(it)))
+        return x, it.value
+
+    def noise(self, level: int, first: int, nsamples: int, seed: int):
+        n = self.level_info(level)[3]
+        x = np.zeros((nsamples, n))
+        self._check(self.lib.mgmlmc_noise(self.h, level, int(first), int(nsamples), C.c_uint64(seed), _dptr(x)))
+        return x
+
+    def profile(self, enable: bool = True, reset: bool = False):
+        self._check(self.lib.mgmlmc_profile(self.h, int(enable), int(reset)))
+
+    def profile_report(self) -> dict:
+        import json
+        need = C.c_size_t()
+        self._check(self.lib.mgmlmc_profile_report(self.h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value + 1)
+        self._check(self.lib.mgmlmc_profile_report(self.h, buf, need.value + 1, C.byref(need)))
+        return json.loads(buf.value.decode())
+
+    def get_test_vectors(self, level: int, nvec: int):
+        n = self.level_info(level)[3]
+        v = np.zeros((nvec, n), np.complex128)
+        self._check(self.lib.mgmlmc_get_test_vectors(self.h, level, v.ctypes.data_as(_D)))
+        return v

@@ -1,0 +1,572 @@
+// C ABI entry points (declared and documented in include/mgmlmc.h).  Every
+// entry catches all exceptions and turns them into a status code.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "context.h"
+
+using mg::Ctx;
+using mg::Error;
+
+#define API_BEGIN(ctxp)                          \
+    if (!(ctxp)) return MGMLMC_EINVAL;           \
+    Ctx& c = (ctxp)->c;                          \
+    c.err.clear();                               \
+    try {
+#define API_END                                                  \
+    }                                                            \
+    catch (const Error& e) {                                     \
+        c.err = e.what();                                        \
+        return e.code;                                           \
+    }                                                            \
+    catch (const std::bad_alloc&) {                              \
+        c.err = "host allocation failed";                        \
+        return MGMLMC_ENOMEM;                                    \
+    }                                                            \
+    catch (const std::exception& e) {                            \
+        c.err = e.what();                                        \
+        return MGMLMC_ECUDA;                                     \
+    }                                                            \
+    return MGMLMC_OK;
+
+namespace {
+
+void check_options(const mgmlmc_options& o) {
+    MG_REQUIRE(o.mg_precision == 64 || o.mg_precision == 32, MGMLMC_EINVAL, "options: mg_precision must be 64 or 32");
+    MG_REQUIRE(o.solve_tol > 0 && o.solve_tol < 1, MGMLMC_EINVAL, "options: 0 < solve_tol < 1");
+    MG_REQUIRE(o.fgmres_restart >= 1 && o.fgmres_restart <= 63, MGMLMC_EINVAL, "options: 1 <= fgmres_restart <= 63");
+    MG_REQUIRE(o.max_iters >= 1, MGMLMC_EINVAL, "options: max_iters >= 1");
+    MG_REQUIRE(o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post <= 64, MGMLMC_EINVAL,
+               "options: smoothing steps");
+    MG_REQUIRE(o.max_block_rhs >= 1 && o.max_block_rhs <= 4096, MGMLMC_EINVAL, "options: 1 <= max_block_rhs <= 4096");
+}
+
+void require_level(const Ctx& c, int level) {
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "no hierarchy: call mgmlmc_set_hierarchy first");
+    MG_REQUIRE(level >= 1 && level <= c.L, MGMLMC_EINVAL, "level out of range");
+}
+
+struct TermLevels {
+    int a, b;          // 0-based fine / coarse level; b = -1 for the last term
+    bool deflated;
+};
+
+TermLevels term_levels(const Ctx& c, int t) {
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "no hierarchy: call mgmlmc_set_hierarchy first");
+    MG_REQUIRE(t >= 0 && t < c.nterms, MGMLMC_EINVAL, "term out of range");
+    TermLevels tl;
+    tl.a = c.term_level[t];
+    tl.b = (t + 1 < c.nterms) ? c.term_level[t + 1] : -1;
+    tl.deflated = (tl.b < 0 && c.defl.k > 0 && tl.a == c.L - 1);
+    return tl;
+}
+
+// Samples of one block: smp[j] = x_j^H D_a^{-1} x_j - (P^H x_j)^H D_b^{-1} (P^H x_j) [- deflated part].
+bool run_term_block(Ctx& c, const TermLevels& tl, const double2* X, int Nb, double2* smp, long long* iters) {
+    const mg::Level& La = c.lev[tl.a];
+    const double tol = c.opt.solve_tol;
+    bool all_ok = true;
+    int ok = 0;
+    double2* Z = c.scratch<double2>("est_Z", (size_t)La.n * Nb);
+    *iters += mg::solve(c, tl.a, X, Z, Nb, tol, &ok);
+    all_ok &= ok != 0;
+    double2* part = c.scratch<double2>("est_part", (size_t)mg::reduce_groups(La.n, Nb) * Nb);
+    mg::launch_dot<double2, double2>(smp, X, Z, La.n, Nb, part, c.stream);
+    if (tl.b >= 0) {
+        const double2* Ycur = X;
+        for (int l = tl.a; l < tl.b; ++l) {
+            double2* Yn = c.scratch<double2>("est_Y" + std::to_string(l + 1), (size_t)c.lev[l + 1].n * Nb);
+            mg::apply_restrict<double2>(c, l, Yn, Ycur, Nb);
+            Ycur = Yn;
+        }
+        const mg::Level& Lb = c.lev[tl.b];
+        double2* W = c.scratch<double2>("est_W", (size_t)Lb.n * Nb);
+        *iters += mg::solve(c, tl.b, Ycur, W, Nb, tol, &ok);
+        all_ok &= ok != 0;
+        double2* s2 = c.scratch<double2>("est_s2", Nb);
+        double2* part2 = c.scratch<double2>("est_part2", (size_t)mg::reduce_groups(Lb.n, Nb) * Nb);
+        mg::launch_dot<double2, double2>(s2, Ycur, W, Lb.n, Nb, part2, c.stream);
+        mg::launch_axpy_rhs<double2, double2>(smp, nullptr, nullptr, -1.0, s2, 1, Nb, c.stream);
+    }
+    if (tl.deflated) {
+        const int k = c.defl.k;
+        double2* A = c.scratch<double2>("est_A", (size_t)k * Nb);
+        double2* B = c.scratch<double2>("est_B", (size_t)k * Nb);
+        const int groups = mg::gemm_hn_groups(La.n, k, Nb);
+        double2* part3 = c.scratch<double2>("est_part3", (size_t)groups * k * Nb);
+        mg::ProfScope ps(c, "defl.f64", 2.0 * La.n * k * 16 + (double)La.n * Nb * 16, 2.0 * 8.0 * La.n * k * Nb);
+        mg::launch_gemm_hn<double2>(A, c.defl.Rv, X, La.n, k, Nb, part3, groups, c.stream);
+        mg::launch_gemm_hn<double2>(B, c.defl.Lv, X, La.n, k, Nb, part3, groups, c.stream);
+        mg::launch_deflation_correction(smp, A, B, c.defl.a, k, Nb, c.stream);
+    }
+    return all_ok;
+}
+
+// Runs nsamples samples of term t with X produced by make_x(off, Nb, X).
+template <typename MakeX>
+int estimate_term(Ctx& c, int t, int nsamples, double* samples_out, mgmlmc_level_stats* out, MakeX make_x) {
+    const TermLevels tl = term_levels(c, t);
+    MG_REQUIRE(nsamples >= 0, MGMLMC_EINVAL, "nsamples must be >= 0");
+    const mg::Level& La = c.lev[tl.a];
+    const int blk = c.opt.max_block_rhs;
+    double2* X = c.scratch<double2>("est_X", (size_t)La.n * std::min(blk, std::max(nsamples, 1)));
+    double2* smp = c.scratch<double2>("est_smp", (size_t)std::max(nsamples, 1));
+    double* acc = c.scratch<double>("est_acc", 4);
+    MG_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), c.stream));
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    MG_CUDA(cudaEventRecord(e0, c.stream));
+    long long iters = 0;
+    bool ok = true;
+    for (int off = 0; off < nsamples; off += blk) {
+        const int Nb = std::min(blk, nsamples - off);
+        make_x(off, Nb, X);
+        ok &= run_term_block(c, tl, X, Nb, smp + off, &iters);
+    }
+    if (nsamples > 0) mg::launch_sample_stats(acc, smp, nsamples, c.stream);
+    MG_CUDA(cudaEventRecord(e1, c.stream));
+    double hacc[4] = {0, 0, 0, 0};
+    MG_CUDA(cudaMemcpyAsync(hacc, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (samples_out && nsamples > 0)
+        MG_CUDA(cudaMemcpyAsync(samples_out, smp, sizeof(double2) * nsamples, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    float ms = 0;
+    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mg::TermStats& S = c.stats[t];
+    S.n += nsamples;
+    S.sum_re += hacc[0];
+    S.sum_im += hacc[1];
+    S.sum_abs2 += hacc[2];
+    S.seconds += ms * 1e-3;
+    S.iters += iters;
+    if (out) {
+        out->nsamples = nsamples;
+        out->sum_re = hacc[0];
+        out->sum_im = hacc[1];
+        out->sum_abs2 = hacc[2];
+        out->mean_re = nsamples ? hacc[0] / nsamples : 0;
+        out->mean_im = nsamples ? hacc[1] / nsamples : 0;
+        out->variance = nsamples > 1 ? (hacc[2] - nsamples * (out->mean_re * out->mean_re + out->mean_im * out->mean_im)) /
+                                           (nsamples - 1)
+                                     : 0;
+        out->seconds = ms * 1e-3;
+        out->iters = iters;
+    }
+    if (!ok) throw Error(MGMLMC_ENOTCONVERGED, "a sample solve reached max_iters (samples kept)");
+    return MGMLMC_OK;
+}
+
+void fill_stats(const mg::TermStats& S, mgmlmc_level_stats* o) {
+    o->nsamples = S.n;
+    o->sum_re = S.sum_re;
+    o->sum_im = S.sum_im;
+    o->sum_abs2 = S.sum_abs2;
+    o->mean_re = S.n ? S.sum_re / S.n : 0;
+    o->mean_im = S.n ? S.sum_im / S.n : 0;
+    o->variance = S.n > 1 ? (S.sum_abs2 - S.n * (o->mean_re * o->mean_re + o->mean_im * o->mean_im)) / (S.n - 1) : 0;
+    o->seconds = S.seconds;
+    o->iters = S.iters;
+}
+
+// [nv][n] host complex -> [n][nv] device
+double2* upload_block(Ctx& c, const double* host, long long n, int nv, const char* name) {
+    double2* tmp = c.scratch<double2>(std::string(name) + "_t", (size_t)n * nv);
+    double2* out = c.scratch<double2>(name, (size_t)n * nv);
+    MG_CUDA(cudaMemcpyAsync(tmp, host, sizeof(double2) * n * nv, cudaMemcpyHostToDevice, c.stream));
+    mg::launch_transpose(out, tmp, nv, (int)n, c.stream);
+    return out;
+}
+void download_block(Ctx& c, double* host, const double2* dev, long long n, int nv, const char* name) {
+    double2* tmp = c.scratch<double2>(name, (size_t)n * nv);
+    mg::launch_transpose(tmp, dev, n, nv, c.stream);
+    MG_CUDA(cudaMemcpyAsync(host, tmp, sizeof(double2) * n * nv, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+}
+
+}  // namespace
+
+extern "C" {
+
+void mgmlmc_default_options(mgmlmc_options* o) {
+    if (!o) return;
+    o->mg_precision = 64;
+    o->solve_tol = 1e-12;
+    o->fgmres_restart = 24;
+    o->max_iters = 2000;
+    o->nu_pre = 0;
+    o->nu_post = 4;
+    o->max_block_rhs = 256;
+    o->verbose = 0;
+}
+
+int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream, mgmlmc_alloc_fn alloc,
+                  mgmlmc_free_fn free_fn, void* alloc_user) {
+    if (!out) return MGMLMC_EINVAL;
+    *out = nullptr;
+    mgmlmc_ctx* h = new (std::nothrow) mgmlmc_ctx();
+    if (!h) return MGMLMC_ENOMEM;
+    Ctx& c = h->c;
+    try {
+        mgmlmc_default_options(&c.opt);
+        if (opt) c.opt = *opt;
+        check_options(c.opt);
+        MG_REQUIRE((alloc == nullptr) == (free_fn == nullptr), MGMLMC_EINVAL, "alloc and free must both be given");
+        c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+        c.alloc = alloc;
+        c.free_fn = free_fn;
+        c.alloc_user = alloc_user;
+        int dev = 0;
+        MG_CUDA(cudaGetDevice(&dev));
+        c.hbuf_bytes = 4096;
+        MG_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c.hbuf), c.hbuf_bytes));
+    } catch (const Error& e) {
+        const int code = e.code;
+        if (c.hbuf) cudaFreeHost(c.hbuf);
+        delete h;
+        return code;
+    }
+    *out = h;
+    return MGMLMC_OK;
+}
+
+void mgmlmc_destroy(mgmlmc_ctx* h) {
+    if (!h) return;
+    h->c.release_all();
+    if (h->c.hbuf) cudaFreeHost(h->c.hbuf);
+    delete h;
+}
+
+const char* mgmlmc_last_error(const mgmlmc_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
+
+int mgmlmc_set_gauge(mgmlmc_ctx* h, int Lx, int Lt, const double* theta) {
+    API_BEGIN(h)
+    MG_REQUIRE(theta, MGMLMC_EINVAL, "set_gauge: theta is NULL");
+    MG_REQUIRE(Lx >= 2 && Lt >= 2 && Lx % 2 == 0 && Lt % 2 == 0 && (long long)Lx * Lt <= (1LL << 26), MGMLMC_EINVAL,
+               "set_gauge: Lx, Lt even, >= 2, Lx*Lt <= 2^26");
+    c.free_hierarchy();
+    c.have_gauge = false;
+    c.Lx = Lx;
+    c.Lt = Lt;
+    mg::upload_links(c, theta);
+    c.have_gauge = true;
+    API_END
+}
+
+int mgmlmc_set_mass(mgmlmc_ctx* h, double m0) {
+    API_BEGIN(h)
+    MG_REQUIRE(std::isfinite(m0), MGMLMC_ENAN, "set_mass: non-finite m0");
+    c.free_hierarchy();
+    c.m0 = m0;
+    c.have_mass = true;
+    API_END
+}
+
+int mgmlmc_set_hierarchy(mgmlmc_ctx* h, int nlevels, const int* agg_x, const int* agg_t, const int* nvec,
+                         int setup_iters, double setup_tol, const double* const* start_vectors) {
+    API_BEGIN(h)
+    MG_REQUIRE(setup_tol > 0 && setup_tol < 1, MGMLMC_EINVAL, "set_hierarchy: 0 < setup_tol < 1");
+    mg::build_hierarchy(c, nlevels, agg_x, agg_t, nvec, setup_iters, setup_tol, start_vectors);
+    API_END
+}
+
+int mgmlmc_set_terms(mgmlmc_ctx* h, int nskip, const int* skip) {
+    API_BEGIN(h)
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "set_terms: no hierarchy");
+    MG_REQUIRE(nskip >= 0 && (nskip == 0 || skip), MGMLMC_EINVAL, "set_terms: bad skip list");
+    std::vector<int> sk(skip, skip + nskip);
+    for (int s : sk)
+        MG_REQUIRE(s >= 2 && s <= c.L - 1, MGMLMC_EINVAL, "set_terms: only levels 2..L-1 can be skipped");
+    c.nterms = 0;
+    for (int l = 0; l < c.L; ++l)
+        if (std::find(sk.begin(), sk.end(), l + 1) == sk.end()) c.term_level[c.nterms++] = l;
+    c.skip = sk;
+    for (auto& s : c.stats) s = mg::TermStats();
+    API_END
+}
+
+int mgmlmc_num_terms(const mgmlmc_ctx* h, int* nterms, int* term_level) {
+    if (!h || !nterms) return MGMLMC_EINVAL;
+    const Ctx& c = h->c;
+    if (!c.have_hier) return MGMLMC_ESTATE;
+    *nterms = c.nterms;
+    if (term_level)
+        for (int t = 0; t < c.nterms; ++t) term_level[t] = c.term_level[t] + 1;
+    return MGMLMC_OK;
+}
+
+int mgmlmc_compute_deflation(mgmlmc_ctx* h, int k, double tol, int max_iters) {
+    API_BEGIN(h)
+    mg::compute_deflation(c, k, tol, max_iters);
+    API_END
+}
+
+int mgmlmc_get_deflation(mgmlmc_ctx* h, double* lambda, double* sigma, double* U, double* V, double* tau) {
+    API_BEGIN(h)
+    const int k = c.defl.k;
+    MG_REQUIRE(k > 0, MGMLMC_ESTATE, "get_deflation: no deflation computed");
+    const long long n = c.lev[c.L - 1].n;
+    for (int i = 0; i < k; ++i) {
+        if (lambda) lambda[i] = c.defl.lambda[i];
+        if (sigma) sigma[i] = std::fabs(c.defl.lambda[i]);
+    }
+    if (U) download_block(c, U, c.defl.Rv, n, k, "gd_tmp");
+    if (V) download_block(c, V, c.defl.Lv, n, k, "gd_tmp");
+    if (tau) {
+        tau[0] = c.defl.tau_re;
+        tau[1] = c.defl.tau_im;
+    }
+    API_END
+}
+
+int mgmlmc_estimate_level(mgmlmc_ctx* h, int term, int64_t first_sample, int nsamples, uint64_t seed,
+                          double* samples_out, mgmlmc_level_stats* stats) {
+    API_BEGIN(h)
+    MG_REQUIRE(first_sample >= 0, MGMLMC_EINVAL, "first_sample must be >= 0");
+    const TermLevels tl = term_levels(c, term);
+    const long long n = c.lev[tl.a].n;
+    estimate_term(c, term, nsamples, samples_out, stats, [&](int off, int Nb, double2* X) {
+        mg::launch_noise<double2>(X, n, Nb, seed, (uint64_t)(tl.a + 1), first_sample + off, c.stream);
+    });
+    API_END
+}
+
+int mgmlmc_estimate_level_probes(mgmlmc_ctx* h, int term, int nsamples, const int8_t* probes, double* samples_out,
+                                 mgmlmc_level_stats* stats) {
+    API_BEGIN(h)
+    MG_REQUIRE(probes || nsamples == 0, MGMLMC_EINVAL, "probes is NULL");
+    const TermLevels tl = term_levels(c, term);
+    const long long n = c.lev[tl.a].n;
+    const int blk = c.opt.max_block_rhs;
+    int8_t* dp = c.scratch<int8_t>("probes", (size_t)n * std::min(blk, std::max(nsamples, 1)));
+    estimate_term(c, term, nsamples, samples_out, stats, [&](int off, int Nb, double2* X) {
+        MG_CUDA(cudaMemcpyAsync(dp, probes + (size_t)off * n, (size_t)Nb * n, cudaMemcpyHostToDevice, c.stream));
+        mg::launch_probes<double2>(X, dp, n, Nb, c.stream);
+    });
+    API_END
+}
+
+int mgmlmc_get_stats(mgmlmc_ctx* h, int term, mgmlmc_level_stats* stats) {
+    API_BEGIN(h)
+    MG_REQUIRE(stats && term >= 0 && term < MGMLMC_MAX_LEVELS, MGMLMC_EINVAL, "get_stats: bad argument");
+    fill_stats(c.stats[term], stats);
+    API_END
+}
+
+int mgmlmc_reset_stats(mgmlmc_ctx* h) {
+    API_BEGIN(h)
+    for (auto& s : c.stats) s = mg::TermStats();
+    API_END
+}
+
+int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, uint64_t seed, const double* costs,
+                          mgmlmc_trace_result* out) {
+    API_BEGIN(h)
+    MG_REQUIRE(out && rel_tol > 0 && max_samples > 0, MGMLMC_EINVAL, "estimate_trace: bad argument");
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "estimate_trace: no hierarchy");
+    const int T = c.nterms;
+    for (auto& s : c.stats) s = mg::TermStats();
+    const int pilot = 16;
+    auto draw = [&](int t, long long first, long long count) {
+        while (count > 0) {
+            const int cnt = (int)std::min<long long>(count, 1 << 20);
+            const TermLevels tl = term_levels(c, t);
+            const long long n = c.lev[tl.a].n;
+            estimate_term(c, t, cnt, nullptr, nullptr, [&](int off, int Nb, double2* X) {
+                mg::launch_noise<double2>(X, n, Nb, seed, (uint64_t)(tl.a + 1), first + off, c.stream);
+            });
+            first += cnt;
+            count -= cnt;
+        }
+    };
+    for (int t = 0; t < T; ++t) draw(t, 0, pilot);
+    int rounds = 0;
+    double est_re = 0, est_im = 0, rel = 0;
+    bool converged = false;
+    for (;;) {
+        std::vector<double> N(T), V(T), C(T);
+        est_re = c.defl.k ? c.defl.tau_re : 0.0;
+        est_im = c.defl.k ? c.defl.tau_im : 0.0;
+        double err2 = 0;
+        long long total = 0;
+        for (int t = 0; t < T; ++t) {
+            const mg::TermStats& S = c.stats[t];
+            N[t] = (double)S.n;
+            const double mr = S.sum_re / S.n, mi = S.sum_im / S.n;
+            V[t] = std::max(0.0, (S.sum_abs2 - S.n * (mr * mr + mi * mi)) / (S.n - 1));
+            C[t] = costs ? costs[t] : std::max(S.seconds / S.n, 1e-12);
+            est_re += mr;
+            est_im += mi;
+            err2 += V[t] / N[t];
+            total += S.n;
+        }
+        const double mag = std::hypot(est_re, est_im);
+        rel = mag > 0 ? std::sqrt(err2) / mag : INFINITY;
+        if (rel <= rel_tol) {
+            converged = true;
+            break;
+        }
+        if (total >= max_samples) break;
+        // Giles-style allocation, growth capped at x2 per round
+        const double eps = rel_tol * mag;
+        double sum_vc = 0;
+        for (int t = 0; t < T; ++t) sum_vc += std::sqrt(V[t] * C[t]);
+        std::vector<long long> target(T);
+        bool grow = false;
+        for (int t = 0; t < T; ++t) {
+            const double want = std::ceil(std::sqrt(V[t] / C[t]) * sum_vc / (eps * eps));
+            long long nn = (long long)std::min(std::max(want, N[t]), 2 * N[t]);
+            target[t] = nn;
+            grow |= nn > (long long)N[t];
+        }
+        if (!grow) {
+            int worst = 0;
+            for (int t = 1; t < T; ++t)
+                if (V[t] / N[t] > V[worst] / N[worst]) worst = t;
+            target[worst] = 2 * (long long)N[worst];
+        }
+        for (int t = 0; t < T; ++t)
+            if (target[t] > (long long)N[t]) draw(t, (long long)N[t], target[t] - (long long)N[t]);
+        ++rounds;
+    }
+    out->trace_re = est_re;
+    out->trace_im = est_im;
+    out->rel_err = rel;
+    out->deflated_part = c.defl.k ? c.defl.tau_re : 0.0;
+    out->nterms = T;
+    out->converged = converged ? 1 : 0;
+    out->rounds = rounds;
+    for (int t = 0; t < MGMLMC_MAX_LEVELS; ++t) {
+        std::memset(&out->term[t], 0, sizeof(mgmlmc_level_stats));
+        if (t < T) fill_stats(c.stats[t], &out->term[t]);
+    }
+    API_END
+}
+
+int mgmlmc_apply(mgmlmc_ctx* h, int op, int level, int nrhs, const double* x, double* y) {
+    API_BEGIN(h)
+    require_level(c, level);
+    MG_REQUIRE(x && y && nrhs >= 1, MGMLMC_EINVAL, "apply: bad argument");
+    const int l = level - 1;
+    long long nin = c.lev[l].n, nout = c.lev[l].n;
+    if (op == MGMLMC_OP_PH || op == MGMLMC_OP_P) {
+        MG_REQUIRE(level < c.L, MGMLMC_EINVAL, "apply: P/P^H need level < L");
+        if (op == MGMLMC_OP_PH) nout = c.lev[l + 1].n;
+        else nin = c.lev[l + 1].n;
+    }
+    if (op == MGMLMC_OP_DINV_C) MG_REQUIRE(level == c.L, MGMLMC_EINVAL, "apply: DINV_C needs level == L");
+    MG_REQUIRE(op >= 0 && op <= 5, MGMLMC_EINVAL, "apply: unknown op");
+    double2* xt = upload_block(c, x, nin, nrhs, "ap_x");
+    double2* yt = c.scratch<double2>("ap_y", (size_t)nout * nrhs);
+    switch (op) {
+        case MGMLMC_OP_D: mg::apply_D<double2>(c, l, yt, xt, nullptr, nrhs, 0, nullptr); break;
+        case MGMLMC_OP_PH: mg::apply_restrict<double2>(c, l, yt, xt, nrhs); break;
+        case MGMLMC_OP_P: mg::apply_prolong<double2>(c, l, yt, xt, nrhs, false); break;
+        case MGMLMC_OP_G5: mg::launch_gamma5<double2>(yt, xt, c.lev[l].nsites, c.lev[l].d, nrhs, c.stream); break;
+        default:
+            if (c.opt.mg_precision == 64) {
+                mg::mg_cycle<double2>(c, l, yt, xt, nrhs);
+            } else {
+                float2* x32 = c.scratch<float2>("ap_x32", (size_t)nin * nrhs);
+                float2* y32 = c.scratch<float2>("ap_y32", (size_t)nout * nrhs);
+                mg::launch_convert<float2, double2>(x32, xt, nin * nrhs, c.stream);
+                mg::mg_cycle<float2>(c, l, y32, x32, nrhs);
+                mg::launch_convert<double2, float2>(yt, y32, nout * nrhs, c.stream);
+            }
+    }
+    download_block(c, y, yt, nout, nrhs, "ap_out");
+    API_END
+}
+
+int mgmlmc_solve(mgmlmc_ctx* h, int level, int nrhs, const double* b, double* x, int* iters) {
+    API_BEGIN(h)
+    require_level(c, level);
+    MG_REQUIRE(b && x && nrhs >= 1, MGMLMC_EINVAL, "solve: bad argument");
+    const int l = level - 1;
+    const long long n = c.lev[l].n;
+    double2* bt = upload_block(c, b, n, nrhs, "sv_b");
+    double2* xt = c.scratch<double2>("sv_x", (size_t)n * nrhs);
+    int ok = 0;
+    const long long it = mg::solve(c, l, bt, xt, nrhs, c.opt.solve_tol, &ok);
+    download_block(c, x, xt, n, nrhs, "sv_out");
+    if (iters) *iters = (int)it;
+    if (!ok) throw Error(MGMLMC_ENOTCONVERGED, "solve: max_iters reached");
+    API_END
+}
+
+int mgmlmc_noise(mgmlmc_ctx* h, int level, int64_t first_sample, int nsamples, uint64_t seed, double* x) {
+    API_BEGIN(h)
+    require_level(c, level);
+    MG_REQUIRE(x && nsamples >= 1 && first_sample >= 0, MGMLMC_EINVAL, "noise: bad argument");
+    const long long n = c.lev[level - 1].n;
+    double2* X = c.scratch<double2>("nz_X", (size_t)n * nsamples);
+    mg::launch_noise<double2>(X, n, nsamples, seed, (uint64_t)level, first_sample, c.stream);
+    std::vector<double> tmp((size_t)2 * n * nsamples);
+    download_block(c, tmp.data(), X, n, nsamples, "nz_out");
+    for (size_t i = 0; i < (size_t)n * nsamples; ++i) x[i] = tmp[2 * i];
+    API_END
+}
+
+int mgmlmc_get_test_vectors(mgmlmc_ctx* h, int level, double* v) {
+    API_BEGIN(h)
+    require_level(c, level);
+    MG_REQUIRE(level < c.L && v, MGMLMC_EINVAL, "get_test_vectors: level < L and v != NULL");
+    const mg::Level& L = c.lev[level - 1];
+    MG_CUDA(cudaMemcpyAsync(v, L.tv, sizeof(double2) * L.n * L.nvec, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    API_END
+}
+
+int mgmlmc_profile(mgmlmc_ctx* h, int enable, int reset) {
+    API_BEGIN(h)
+    c.sync();
+    c.prof.on = enable != 0;
+    if (reset) c.prof.clear();
+    API_END
+}
+
+int mgmlmc_profile_report(mgmlmc_ctx* h, char* buf, size_t cap, size_t* needed) {
+    API_BEGIN(h)
+    c.sync();
+    std::string js = "{";
+    bool first = true;
+    char tmp[256];
+    for (const auto& kv : c.prof.stats) {
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"count\": %lld, \"ms\": %.6f, \"bytes\": %.6e, \"flops\": %.6e}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.count, kv.second.ms, kv.second.bytes, kv.second.flops);
+        js += tmp;
+        first = false;
+    }
+    snprintf(tmp, sizeof(tmp), "%s\"__launches__\": {\"count\": %lld, \"ms\": 0, \"bytes\": 0, \"flops\": 0}",
+             first ? "" : ", ", mg::launch_counter() - c.prof.launch_base);
+    js += tmp;
+    js += "}";
+    if (needed) *needed = js.size();
+    if (buf && cap > 0) {
+        const size_t m = std::min(cap - 1, js.size());
+        memcpy(buf, js.data(), m);
+        buf[m] = 0;
+    }
+    API_END
+}
+
+int mgmlmc_level_info(const mgmlmc_ctx* h, int level, int* lx, int* lt, int* d, int64_t* n) {
+    if (!h) return MGMLMC_EINVAL;
+    const Ctx& c = h->c;
+    if (!c.have_hier) return MGMLMC_ESTATE;
+    if (level < 1 || level > c.L) return MGMLMC_EINVAL;
+    const mg::Level& L = c.lev[level - 1];
+    if (lx) *lx = L.lx;
+    if (lt) *lt = L.lt;
+    if (d) *d = L.d;
+    if (n) *n = L.n;
+    return MGMLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Context of the library: device-resident gauge field, multigrid hierarchy,
+// deflation space, per-term statistics and a named work-space pool.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct mgmlmc_ctx;
+
+namespace mg {
+
+struct Level {
+    int lx = 0, lt = 0, d = 0;       // sites per direction, dof per site
+    int nsites = 0;
+    long long n = 0;                 // nsites * d
+    // operator as 5-point block stencil [site][5][d][d] (level 0: d = 2, used by the
+    // Galerkin product; the fine solve uses the link-based Wilson kernel)
+    double2* A64 = nullptr;
+    float2* A32 = nullptr;
+    // prolongation to the next level: [site][d][nvec]
+    int ax = 0, at = 0, nvec = 0;
+    double2* P64 = nullptr;
+    float2* P32 = nullptr;
+    double2* tv = nullptr;           // test vectors [nvec][n]
+    // coarsest level: dense inverse [n][n]
+    double2* Dinv64 = nullptr;
+    float2* Dinv32 = nullptr;
+};
+
+struct Deflation {
+    int k = 0;
+    double2* Lv = nullptr;           // [n][k] left vectors of the traced operator (V)
+    double2* Rv = nullptr;           // [n][k] right vectors (U)
+    double* a = nullptr;             // [k] 1/sigma
+    std::vector<double> lambda;      // eigenvalues of Q_L
+    double tau_re = 0, tau_im = 0;   // tr(V Sigma^{-1} U^H)
+};
+
+struct TermStats {
+    long long n = 0;
+    double sum_re = 0, sum_im = 0, sum_abs2 = 0;
+    double seconds = 0;
+    long long iters = 0;
+};
+
+// CUDA-event timing of kernel classes with their algorithmic bytes and flops
+// per launch (the per-operation timing of Sect. 4.3: D_l, P_l, P_l^H,
+// deflations, axpy-type updates).
+struct ProfStat {
+    long long count = 0;
+    double ms = 0, bytes = 0, flops = 0;
+};
+struct Profiler {
+    bool on = false;
+    std::map<std::string, ProfStat> stats;
+    struct Pending {
+        std::string key;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    long long launch_base = 0;       // launch_counter() at the last reset
+    cudaEvent_t take();
+    void resolve();      // call after the stream is synchronised
+    void clear();
+    ~Profiler();
+};
+
+struct Ctx;
+// Brackets the launches issued during its lifetime with events (when enabled).
+struct ProfScope {
+    Ctx* c;
+    size_t idx;
+    bool active;
+    ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops);
+    ~ProfScope();
+};
+
+struct Ctx {
+    mgmlmc_options opt{};
+    Profiler prof;
+    cudaStream_t stream = nullptr;
+    mgmlmc_alloc_fn alloc = nullptr;
+    mgmlmc_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::string err;
+    double* hbuf = nullptr;          // pinned host scratch for scalar read-backs
+    size_t hbuf_bytes = 0;
+
+    int Lx = 0, Lt = 0;
+    bool have_gauge = false, have_mass = false, have_hier = false;
+    double m0 = 0;
+    double2* U64 = nullptr;          // links [site][2]
+    float2* U32 = nullptr;
+
+    int L = 0;
+    Level lev[MGMLMC_MAX_LEVELS];
+    int nterms = 0;
+    int term_level[MGMLMC_MAX_LEVELS + 1] = {0};   // 0-based fine level of each term
+    std::vector<int> skip;
+    Deflation defl;
+    TermStats stats[MGMLMC_MAX_LEVELS];
+    long long last_iters = 0;        // outer iterations of the last solve
+
+    // ---- memory
+    struct Buf { void* p = nullptr; size_t bytes = 0; };
+    std::map<std::string, Buf> ws;
+    std::vector<void*> owned;
+
+    void* dev_alloc(size_t bytes);
+    void dev_free(void* p);
+    template <typename T> T* alloc_n(size_t count) { return reinterpret_cast<T*>(dev_alloc(count * sizeof(T))); }
+    // Named scratch that grows on demand; contents are undefined after growth.
+    void* scratch_bytes(const std::string& name, size_t bytes);
+    template <typename T> T* scratch(const std::string& name, size_t count) {
+        return reinterpret_cast<T*>(scratch_bytes(name, count * sizeof(T)));
+    }
+    void release_all();
+    void free_hierarchy();
+    void free_deflation();
+    void sync();
+};
+
+// ---- solver layer (solver.cu)
+template <typename C> void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, double2* dots);
+template <typename C> void apply_restrict(Ctx& c, int l, C* xc, const C* x, int N);
+template <typename C> void apply_prolong(Ctx& c, int l, C* x, const C* xc, int N, bool accumulate);
+template <typename C> void mg_cycle(Ctx& c, int l, C* e, const C* r, int N);
+// FGMRES(m) in precision C on level l; x holds the initial guess (zero if x_zero).
+// At most max_cycles restart cycles.  Returns outer iterations; *ok = 1 if the
+// relative residual reached tol (or the cycle budget ended, for inner solves).
+template <typename C>
+long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long maxit, bool x_zero, int* ok,
+                 int max_cycles);
+// FP64-accurate solve D_l x = b (plain FP64 FGMRES, or mixed iterative refinement).
+long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok);
+
+// ---- setup (setup.cu)
+void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const int* nvec, int setup_iters,
+                     double setup_tol, const double* const* start_vectors);
+void compute_deflation(Ctx& c, int k, double tol, int max_iters);
+void upload_links(Ctx& c, const double* theta);
+
+}  // namespace mg
+
+struct mgmlmc_ctx {
+    mg::Ctx c;
+};

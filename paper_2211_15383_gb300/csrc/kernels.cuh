@@ -1,0 +1,133 @@
+// Host-side launchers of every kernel of the library.  Vectors are blocks of N
+// right-hand sides stored [row][rhs] (rhs fastest, row = site * d + dof), so a
+// warp reads 32 consecutive right-hand sides of one row: fully coalesced.
+// Per-rhs reductions are deterministic two-pass: each block writes partial
+// sums to a scratch array [group][...][N], a second kernel adds them in a fixed
+// order.
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+// ---------------------------------------------------------------- vectors
+// Z2 noise block: x[i][j] = +-1 (imag 0) for sample first+j, entry i (Sect. 1).
+template <typename C>
+void launch_noise(C* x, long long n, int N, uint64_t seed, uint64_t term, int64_t first, cudaStream_t s);
+// x[i][j] = probes[j][i] (host-supplied probe vectors already on the device).
+template <typename C>
+void launch_probes(C* x, const int8_t* probes, long long n, int N, cudaStream_t s);
+template <typename Cout, typename Cin>
+void launch_convert(Cout* y, const Cin* x, long long count, cudaStream_t s);
+// y[i][j] = scale[j] * x[i][j] (scale real, per rhs); scale may be inverted (1/scale, 0 if scale == 0)
+template <typename Cy, typename Cx_>
+void launch_scale_rhs(Cy* y, const Cx_* x, const double* scale, bool invert, long long n, int N, cudaStream_t s);
+// y[i][j] += sign * alpha[j] * x[i][j]  (alpha complex per rhs, optionally times real beta[j])
+template <typename Cy, typename Cx_>
+void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sign, const Cx_* x,
+                     long long n, int N, cudaStream_t s);
+template <typename C>
+void launch_zero(C* x, long long count, cudaStream_t s);
+// out[c][r] = in[r][c] (rows x cols complex, row-major)
+void launch_transpose(double2* out, const double2* in, long long rows, int cols, cudaStream_t s);
+
+// ------------------------------------------------------------- reductions
+// Number of row groups (partials) used by the reduction kernels for (n, N).
+int reduce_groups(long long n, int N);
+// out[j] = sum_i conj(x[i][j]) * y[i][j]  (double2), via scratch part[groups][N]
+template <typename Cx_, typename Cy>
+void launch_dot(double2* out, const Cx_* x, const Cy* y, long long n, int N, double2* part, cudaStream_t s);
+// out[j] = sum_i |x[i][j]|^2
+template <typename C>
+void launch_norm2(double* out, const C* x, long long n, int N, double* part, cudaStream_t s);
+// out[k][j] = <V_k, w>_j for k < m; V_k = V + k * n * N.  part: [groups][m][N].
+template <typename C>
+void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, int N, double2* part,
+                     cudaStream_t s);
+// w[i][j] += sign * sum_k coef[k][j] * V_k[i][j]
+template <typename C>
+void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
+                      cudaStream_t s);
+// Sum of partials: out[j] = sum_g part[g][j] (count = values per group).
+void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s);
+void launch_finalize(double* out, const double* part, int groups, int count, cudaStream_t s);
+
+// --------------------------------------------------------------- stencils
+// Fine Wilson-Schwinger operator (2 spins, U(1) links U[site][mu]).
+//  mode 0: y = D x;  mode 1: y = b - D x;
+//  mode 2: y = D x and part[g][0][j] = <y, x>_j, part[g][1][j] = <y, y>_j (MR smoother)
+template <typename C>
+void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N,
+                   int mode, double2* part, int groups, cudaStream_t s);
+// Coarse 5-point block stencil y_s = sum_dir A[s][dir] x_nbr(s,dir), d x d complex blocks,
+// dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t (periodic; boundary signs live in the blocks).
+template <typename C>
+void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N,
+                          int mode, double2* part, int groups, cudaStream_t s);
+int stencil_groups(int nsites, int N);
+// Restriction xc = P^H x and prolongation x (+)= P xc for aggregates ax x at,
+// P stored [fine site][d][nvec]; coarse dof (S, spin block, j).
+template <typename C>
+void launch_restrict(C* xc, const C* x, const C* P, int lx, int lt, int d, int ax, int at, int nvec,
+                     int N, cudaStream_t s);
+template <typename C>
+void launch_prolong(C* x, const C* xc, const C* P, int lx, int lt, int d, int ax, int at, int nvec,
+                    int N, bool accumulate, cudaStream_t s);
+// MR update: alpha_j = <p,r>/<p,p> from dots[2][N]; e += alpha r; r -= alpha p.
+template <typename C>
+void launch_mr_update(C* e, C* r, const C* p, const double2* dots, long long n, int N, bool e_is_zero,
+                      cudaStream_t s);
+// Gamma5 on a level with d dof per site: +1 on the first d/2 dof, -1 on the rest.
+template <typename C>
+void launch_gamma5(C* y, const C* x, long long nsites, int d, int N, cudaStream_t s);
+
+// ----------------------------------------------------------------- dense
+// C[M][Nc] = A[M][K] * B[K][Nc] (+ C if accumulate), complex, row-major.
+template <typename C>
+void launch_gemm_nn(C* Cm, const C* A, const C* B, int M, int K, int Nc, bool accumulate, cudaStream_t s);
+// C[ka][kb] = A^H B for A [n][ka], B [n][kb] (reduction over n, deterministic two-pass).
+template <typename C>
+void launch_gemm_hn(double2* Cm, const C* A, const C* B, long long n, int ka, int kb, double2* part,
+                    int groups, cudaStream_t s);
+int gemm_hn_groups(long long n, int ka, int kb);
+// In-place Gauss-Jordan inverse of a dense complex n x n matrix (partial pivoting).
+// work: n doubles + n ints + a few scalars.  Returns via *status_dev 0 ok, 1 singular.
+template <typename C>
+void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s);
+size_t gauss_jordan_work_bytes(int n);
+// Hermitian eigenproblem of a small b x b matrix (cyclic Jacobi, one CTA):
+// H is overwritten; W receives eigenvectors (columns), lam eigenvalues.
+void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s);
+// BF16 real embedding of a complex n x n matrix for the tensor-core coarsest solve.
+void launch_embed_bf16(__nv_bfloat16* E, const double2* A, int n, cudaStream_t s);
+// Y[n][N] = Dinv * X with the BF16 embedding (tcgen05 tensor cores), X, Y FP32 complex.
+void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N,
+                                void* scratch, cudaStream_t s);
+size_t coarse_inverse_bf16_scratch(int n, int N);
+
+// ----------------------------------------------------------------- setup
+// Block-stencil form of the fine Wilson operator: A[site][5][2][2].
+void launch_materialize_wilson(double2* A, const double2* U, double m0, int lx, int lt, cudaStream_t s);
+// Galerkin coarse blocks Ac[S][5][dc][dc] = P^H D P, D given as block stencil Af (d x d).
+void launch_galerkin(double2* Ac, const double2* Af, const double2* P, int lx, int lt, int d, int ax,
+                     int at, int nvec, cudaStream_t s);
+// P[site][d][nvec] from test vectors tv[nvec][n]: MGS per (aggregate, spin block).
+// status[0] set to 1 if a block is rank deficient.
+void launch_build_prolongator(double2* P, const double2* tv, int lx, int lt, int d, int ax, int at,
+                              int nvec, int* status, cudaStream_t s);
+// Small per-rhs FGMRES bookkeeping (one thread per rhs).
+void launch_arnoldi_column(double2* H, double* cs, double2* sn, double2* g, double* resid,
+                           const double2* h, const double* hnorm, int j, int m, int N, cudaStream_t s);
+void launch_back_substitute(double2* y, const double2* H, const double2* g, int j, int m, int N,
+                            cudaStream_t s);
+void launch_init_g(double2* g, const double* beta, int m, int N, cudaStream_t s);
+// max over rhs of resid[j] / bnorm[j] -> out (device scalar)
+void launch_max_ratio(double* out, const double* resid, const double* bnorm, int N, cudaStream_t s);
+// samples: s[j] = sign * <x, z>_j + s[j] (accumulate) helpers live in the estimator.
+void launch_deflation_correction(double2* s, const double2* A, const double2* B, const double* a, int k,
+                                 int N, cudaStream_t s_);
+void launch_sample_stats(double* acc, const double2* samples, int N, cudaStream_t s);
+// Dense [n][n] matrix of a 5-point block stencil (entries of coinciding neighbours add up).
+void launch_dense_from_blocks(double2* Dd, const double2* A, int lx, int lt, int d, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,343 @@
+// Stencil kernels: the fine Wilson-Schwinger operator D_1, the coarse 5-point
+// block stencils D_l (l >= 2), restriction P^H, prolongation P, Gamma5 and the
+// fused minimal-residual smoother update.
+//
+// The fine operator (the paper names the 2D Wilson-Schwinger discretisation,
+// Sect. 1; its form is the standard Wilson one):
+//   (D psi)(x) = (m0+2) psi(x) - 1/2 sum_mu [(1 - s_mu) U_mu(x) psi(x+mu)
+//                                          + (1 + s_mu) U_mu(x-mu)^* psi(x-mu)]
+// with s_0 = sigma_1, s_1 = sigma_2, antiperiodic in time.  Each hop needs a
+// single complex multiply: (1 -+ s_mu) projects the 2-spinor onto one
+// component (e.g. (1 - sigma_1) psi = (a, -a) with a = psi_0 - psi_1).
+#include "kernels.cuh"
+
+namespace mg {
+
+template <typename C, int MODE>
+__global__ void __launch_bounds__(256) k_wilson(C* __restrict__ y, const C* __restrict__ x, const C* __restrict__ b,
+                                                const C* __restrict__ U, re_t<C> mass, int lx, int lt, int N,
+                                                double2* __restrict__ part) {
+    using R = re_t<C>;
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    const int V = lx * lt;
+    const R half = (R)0.5;
+    C dyx = czero<C>();
+    R dyy = 0;
+    if (j < N) {
+        for (int site = blockIdx.y * kRowLanes + threadIdx.y; site < V; site += gridDim.y * kRowLanes) {
+            const int xx = site % lx, t = site / lx;
+            const int sxp = (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+            const int sxm = (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+            const int stp = xx + lx * (t + 1 == lt ? 0 : t + 1);
+            const int stm = xx + lx * (t == 0 ? lt - 1 : t - 1);
+            const R sgp = (t + 1 == lt) ? (R)-0.5 : half;   // antiperiodic time boundary, times 1/2
+            const R sgm = (t == 0) ? (R)-0.5 : half;
+            const C u0 = U[2 * site], u1 = U[2 * site + 1];
+            const C u0m = U[2 * sxm], u1m = U[2 * stm + 1];
+            const long long N2 = 2LL * N;
+            const C p0 = x[site * N2 + j], p1 = x[site * N2 + N + j];
+            C o0 = mk(mass * p0.x, mass * p0.y), o1 = mk(mass * p1.x, mass * p1.y);
+            {   // +x: (1 - sigma_1) psi = (a, -a), a = psi0 - psi1
+                const C q0 = x[sxp * N2 + j], q1 = x[sxp * N2 + N + j];
+                const C u = cscale(cmul(u0, csub(q0, q1)), half);
+                o0 = csub(o0, u);
+                o1 = cadd(o1, u);
+            }
+            {   // -x: (1 + sigma_1) psi = (c, c), c = psi0 + psi1
+                const C q0 = x[sxm * N2 + j], q1 = x[sxm * N2 + N + j];
+                const C u = cscale(cmulc(u0m, cadd(q0, q1)), half);
+                o0 = csub(o0, u);
+                o1 = csub(o1, u);
+            }
+            {   // +t: (1 - sigma_2) psi = (a, -i a), a = psi0 + i psi1
+                const C q0 = x[stp * N2 + j], q1 = x[stp * N2 + N + j];
+                const C u = cscale(cmul(u1, cadd(q0, ctimesi(q1))), sgp);
+                o0 = csub(o0, u);
+                o1 = cadd(o1, ctimesi(u));
+            }
+            {   // -t: (1 + sigma_2) psi = (c, i c), c = psi0 - i psi1
+                const C q0 = x[stm * N2 + j], q1 = x[stm * N2 + N + j];
+                const C u = cscale(cmulc(u1m, csub(q0, ctimesi(q1))), sgm);
+                o0 = csub(o0, u);
+                o1 = csub(o1, ctimesi(u));
+            }
+            if (MODE == 1) {
+                o0 = csub(b[site * N2 + j], o0);
+                o1 = csub(b[site * N2 + N + j], o1);
+            }
+            y[site * N2 + j] = o0;
+            y[site * N2 + N + j] = o1;
+            if (MODE == 2) {
+                cfmac(dyx, o0, p0);
+                cfmac(dyx, o1, p1);
+                dyy = fma(o0.x, o0.x, fma(o0.y, o0.y, fma(o1.x, o1.x, fma(o1.y, o1.y, dyy))));
+            }
+        }
+    }
+    if (MODE == 2) {
+        __shared__ double2 sh[2][kRowLanes][kRhsTile + 1];
+        sh[0][threadIdx.y][threadIdx.x] = to_d(dyx);
+        sh[1][threadIdx.y][threadIdx.x] = make_double2((double)dyy, 0.0);
+        __syncthreads();
+        if (threadIdx.y < 2 && j < N) {
+            double2 s = sh[threadIdx.y][0][threadIdx.x];
+            for (int r = 1; r < kRowLanes; ++r) s = cadd(s, sh[threadIdx.y][r][threadIdx.x]);
+            part[((long long)blockIdx.y * 2 + threadIdx.y) * N + j] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ int nbr_site(int site, int dir, int lx, int lt) {
+    const int xx = site % lx, t = site / lx;
+    switch (dir) {
+        case 1: return (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+        case 2: return (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+        case 3: return xx + lx * (t + 1 == lt ? 0 : t + 1);
+        case 4: return xx + lx * (t == 0 ? lt - 1 : t - 1);
+        default: return site;
+    }
+}
+
+// One block per coarse site (grid-stride): A[site] (5 d^2 complex) staged in
+// shared memory, each thread owns one rhs and RPT output rows.
+template <typename C, int RPT, int MODE>
+__global__ void __launch_bounds__(256) k_block_stencil(C* __restrict__ y, const C* __restrict__ x,
+                                                       const C* __restrict__ b, const C* __restrict__ A, int lx,
+                                                       int lt, int d, int N, double2* __restrict__ part) {
+    using R = re_t<C>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* As = reinterpret_cast<C*>(smem_raw);
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    const int V = lx * lt;
+    const int nA = 5 * d * d;
+    const int tid = threadIdx.y * kRhsTile + threadIdx.x;
+    C dyx = czero<C>();
+    R dyy = 0;
+    for (int site = blockIdx.y; site < V; site += gridDim.y) {
+        __syncthreads();
+        for (int e = tid; e < nA; e += kRhsTile * kRowLanes) As[e] = A[(long long)site * nA + e];
+        __syncthreads();
+        if (j < N) {
+            C acc[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) acc[r] = czero<C>();
+            for (int dir = 0; dir < 5; ++dir) {
+                const int nb = nbr_site(site, dir, lx, lt);
+                const C* xn = x + (long long)nb * d * N + j;
+                const C* Ad = As + dir * d * d;
+                for (int bc = 0; bc < d; ++bc) {
+                    const C xv = xn[(long long)bc * N];
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        const int c = threadIdx.y + kRowLanes * r;
+                        if (c < d) cfma(acc[r], Ad[c * d + bc], xv);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int c = threadIdx.y + kRowLanes * r;
+                if (c < d) {
+                    const long long idx = ((long long)site * d + c) * N + j;
+                    C o = acc[r];
+                    if (MODE == 1) o = csub(b[idx], o);
+                    y[idx] = o;
+                    if (MODE == 2) {
+                        cfmac(dyx, o, x[idx]);
+                        dyy = fma(o.x, o.x, fma(o.y, o.y, dyy));
+                    }
+                }
+            }
+        }
+    }
+    if (MODE == 2) {
+        __syncthreads();
+        double2* sh = reinterpret_cast<double2*>(smem_raw);   // reuse: [2][8][33]
+        sh[(0 * kRowLanes + threadIdx.y) * (kRhsTile + 1) + threadIdx.x] = to_d(dyx);
+        sh[(1 * kRowLanes + threadIdx.y) * (kRhsTile + 1) + threadIdx.x] = make_double2((double)dyy, 0.0);
+        __syncthreads();
+        if (threadIdx.y < 2 && j < N) {
+            double2 s = sh[(threadIdx.y * kRowLanes) * (kRhsTile + 1) + threadIdx.x];
+            for (int r = 1; r < kRowLanes; ++r)
+                s = cadd(s, sh[(threadIdx.y * kRowLanes + r) * (kRhsTile + 1) + threadIdx.x]);
+            part[((long long)blockIdx.y * 2 + threadIdx.y) * N + j] = s;
+        }
+    }
+}
+
+// xc[S][o] = sum_{site in S} sum_{a in spin block s(o)} conj(P[site][a][j(o)]) x[site][a]
+template <typename C>
+__global__ void k_restrict(C* __restrict__ xc, const C* __restrict__ x, const C* __restrict__ P, int lx, int lt,
+                           int d, int ax, int at, int nvec, int N) {
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    const int cx = lx / ax, ct = lt / at, dc = 2 * nvec, hd = d / 2;
+    for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
+        const int X = S % cx, T = S / cx;
+        for (int o = threadIdx.y; o < dc; o += kRowLanes) {
+            const int s = o / nvec, jv = o % nvec;
+            C acc = czero<C>();
+            for (int it = 0; it < at; ++it)
+                for (int ix = 0; ix < ax; ++ix) {
+                    const int site = (X * ax + ix) + lx * (T * at + it);
+                    for (int a = s * hd; a < (s + 1) * hd; ++a)
+                        cfmac(acc, P[((long long)site * d + a) * nvec + jv], x[((long long)site * d + a) * N + j]);
+                }
+            xc[((long long)S * dc + o) * N + j] = acc;
+        }
+    }
+}
+
+// x[site][a] (+)= sum_j P[site][a][j] xc[S(site)][s(a) nvec + j]
+template <typename C>
+__global__ void k_prolong(C* __restrict__ x, const C* __restrict__ xc, const C* __restrict__ P, int lx, int lt,
+                          int d, int ax, int at, int nvec, int N, bool accumulate) {
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    const int cx = lx / ax, dc = 2 * nvec, hd = d / 2;
+    const long long rows = (long long)lx * lt * d;
+    for (long long row = (long long)blockIdx.y * kRowLanes + threadIdx.y; row < rows;
+         row += (long long)gridDim.y * kRowLanes) {
+        const int site = (int)(row / d), a = (int)(row % d);
+        const int xx = site % lx, t = site / lx;
+        const int S = xx / ax + cx * (t / at);
+        const int s = a / hd;
+        C acc = accumulate ? x[row * N + j] : czero<C>();
+        const C* Pr = P + row * nvec;
+        const C* xcs = xc + ((long long)S * dc + s * nvec) * N + j;
+        for (int jv = 0; jv < nvec; ++jv) cfma(acc, Pr[jv], xcs[(long long)jv * N]);
+        x[row * N + j] = acc;
+    }
+}
+
+template <typename C>
+__global__ void k_mr_update(C* __restrict__ e, C* __restrict__ r, const C* __restrict__ p,
+                            const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
+    using R = re_t<C>;
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    const double2 pr = dots[j];
+    const double pp = dots[N + j].x;
+    const double2 al = (pp > 0.0) ? make_double2(pr.x / pp, pr.y / pp) : make_double2(0.0, 0.0);
+    const C a = mk((R)al.x, (R)al.y);
+    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
+         i += (long long)gridDim.y * kRowLanes) {
+        const long long idx = i * N + j;
+        const C rv = r[idx];
+        C ev = e_is_zero ? czero<C>() : e[idx];
+        cfma(ev, a, rv);
+        e[idx] = ev;
+        C rn = rv;
+        C ap = cmul(a, p[idx]);
+        r[idx] = csub(rn, ap);
+    }
+}
+
+template <typename C>
+__global__ void k_gamma5(C* __restrict__ y, const C* __restrict__ x, long long rows, int d, int N) {
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < rows;
+         i += (long long)gridDim.y * kRowLanes) {
+        const C v = x[i * N + j];
+        y[i * N + j] = ((int)(i % d) < d / 2) ? v : mk(-v.x, -v.y);
+    }
+}
+
+// --------------------------------------------------------------------- launchers
+static inline dim3 blk() { return dim3(kRhsTile, kRowLanes); }
+
+int stencil_groups(int nsites, int N) { return row_groups(nsites, N, 4); }
+
+template <typename C>
+void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N, int mode,
+                   double2* part, int groups, cudaStream_t s) {
+    using R = re_t<C>;
+    dim3 g(rhs_tiles(N), groups);
+    const R mass = (R)(m0 + 2.0);
+    switch (mode) {
+        case 0: k_wilson<C, 0><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+        case 1: k_wilson<C, 1><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+        default: k_wilson<C, 2><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+    }
+    MG_LAUNCHED();
+}
+
+template <typename C, int RPT>
+static void bs_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N, int mode,
+                        double2* part, int groups, cudaStream_t s) {
+    dim3 g(rhs_tiles(N), groups);
+    size_t sm = (size_t)5 * d * d * sizeof(C);
+    size_t smin = 2 * kRowLanes * (kRhsTile + 1) * sizeof(double2);
+    if (sm < smin) sm = smin;
+    if (sm > 48 * 1024) {
+        MG_CUDA(cudaFuncSetAttribute(k_block_stencil<C, RPT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MG_CUDA(cudaFuncSetAttribute(k_block_stencil<C, RPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MG_CUDA(cudaFuncSetAttribute(k_block_stencil<C, RPT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
+    switch (mode) {
+        case 0: k_block_stencil<C, RPT, 0><<<g, blk(), sm, s>>>(y, x, b, A, lx, lt, d, N, part); break;
+        case 1: k_block_stencil<C, RPT, 1><<<g, blk(), sm, s>>>(y, x, b, A, lx, lt, d, N, part); break;
+        default: k_block_stencil<C, RPT, 2><<<g, blk(), sm, s>>>(y, x, b, A, lx, lt, d, N, part); break;
+    }
+    MG_LAUNCHED();
+}
+
+template <typename C>
+void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N, int mode,
+                          double2* part, int groups, cudaStream_t s) {
+    MG_REQUIRE(d >= 2 && d <= 64, MGMLMC_EINVAL, "block stencil: 2 <= d <= 64");
+    if (d <= 8) bs_dispatch<C, 1>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
+    else if (d <= 16) bs_dispatch<C, 2>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
+    else if (d <= 32) bs_dispatch<C, 4>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
+    else bs_dispatch<C, 8>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
+}
+
+template <typename C>
+void launch_restrict(C* xc, const C* x, const C* P, int lx, int lt, int d, int ax, int at, int nvec, int N,
+                     cudaStream_t s) {
+    const int ncs = (lx / ax) * (lt / at);
+    int G = row_groups((long long)ncs * kRowLanes, N, 4);
+    k_restrict<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(xc, x, P, lx, lt, d, ax, at, nvec, N);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+void launch_prolong(C* x, const C* xc, const C* P, int lx, int lt, int d, int ax, int at, int nvec, int N,
+                    bool accumulate, cudaStream_t s) {
+    const long long rows = (long long)lx * lt * d;
+    k_prolong<C><<<dim3(rhs_tiles(N), row_groups(rows, N)), blk(), 0, s>>>(x, xc, P, lx, lt, d, ax, at, nvec, N,
+                                                                             accumulate);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+void launch_mr_update(C* e, C* r, const C* p, const double2* dots, long long n, int N, bool e_is_zero,
+                      cudaStream_t s) {
+    k_mr_update<C><<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, s>>>(e, r, p, dots, n, N, e_is_zero);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+void launch_gamma5(C* y, const C* x, long long nsites, int d, int N, cudaStream_t s) {
+    const long long rows = nsites * d;
+    k_gamma5<C><<<dim3(rhs_tiles(N), row_groups(rows, N)), blk(), 0, s>>>(y, x, rows, d, N);
+    MG_LAUNCHED();
+}
+
+#define INST(C)                                                                                        \
+    template void launch_wilson<C>(C*, const C*, const C*, const C*, double, int, int, int, int, double2*, \
+                                   int, cudaStream_t);                                                 \
+    template void launch_block_stencil<C>(C*, const C*, const C*, const C*, int, int, int, int, int,    \
+                                          double2*, int, cudaStream_t);                                 \
+    template void launch_restrict<C>(C*, const C*, const C*, int, int, int, int, int, int, int,         \
+                                     cudaStream_t);                                                     \
+    template void launch_prolong<C>(C*, const C*, const C*, int, int, int, int, int, int, int, bool,    \
+                                    cudaStream_t);                                                      \
+    template void launch_mr_update<C>(C*, C*, const C*, const double2*, long long, int, bool,           \
+                                      cudaStream_t);                                                    \
+    template void launch_gamma5<C>(C*, const C*, long long, int, int, cudaStream_t);
+INST(double2)
+INST(float2)
+
+}  // namespace mg

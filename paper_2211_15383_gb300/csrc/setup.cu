@@ -1,0 +1,421 @@
+// Context memory management, gauge upload, multigrid hierarchy setup
+// (Sect. 3.1, spin-preserving aggregation of Sect. 4.2) and the exact deflation
+// of the coarsest operator (Sect. 2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "context.h"
+
+namespace mg {
+
+// ------------------------------------------------------------------ memory
+void* Ctx::dev_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (alloc) {
+        p = alloc(alloc_user, bytes);
+        if (!p) throw Error(MGMLMC_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes refused");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(MGMLMC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        }
+    }
+    owned.push_back(p);
+    return p;
+}
+
+void Ctx::dev_free(void* p) {
+    if (!p) return;
+    auto it = std::find(owned.begin(), owned.end(), p);
+    if (it == owned.end()) return;
+    owned.erase(it);
+    if (free_fn) free_fn(alloc_user, p);
+    else cudaFree(p);
+}
+
+void* Ctx::scratch_bytes(const std::string& name, size_t bytes) {
+    Buf& b = ws[name];
+    if (b.p && b.bytes >= bytes) return b.p;
+    if (b.p) dev_free(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = ((bytes + 255) / 256) * 256;
+    b.p = dev_alloc(want);
+    b.bytes = want;
+    return b.p;
+}
+
+void Ctx::release_all() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : owned) {
+        if (free_fn) free_fn(alloc_user, p);
+        else cudaFree(p);
+    }
+    owned.clear();
+    ws.clear();
+    for (auto& L : lev) L = Level();
+    U64 = nullptr;
+    U32 = nullptr;
+    defl = Deflation();
+}
+
+void Ctx::free_deflation() {
+    dev_free(defl.Lv);
+    dev_free(defl.Rv);
+    dev_free(defl.a);
+    defl = Deflation();
+}
+
+void Ctx::free_hierarchy() {
+    sync();
+    for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) {
+        Level& L = lev[l];
+        dev_free(L.A64); dev_free(L.A32); dev_free(L.P64); dev_free(L.P32); dev_free(L.tv);
+        dev_free(L.Dinv64); dev_free(L.Dinv32);
+        L = Level();
+    }
+    free_deflation();
+    L = 0;
+    have_hier = false;
+    for (auto& s : stats) s = TermStats();
+}
+
+void Ctx::sync() {
+    MG_CUDA(cudaStreamSynchronize(stream));
+    if (!prof.pending.empty()) prof.resolve();
+}
+
+// ------------------------------------------------------------------ profiler
+long long& launch_counter() {
+    static long long n = 0;
+    return n;
+}
+
+cudaEvent_t Profiler::take() {
+    if (pool.empty()) {
+        cudaEvent_t e;
+        MG_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+}
+void Profiler::resolve() {
+    for (auto& p : pending) {
+        float ms = 0;
+        MG_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        ProfStat& s = stats[p.key];
+        s.count += 1;
+        s.ms += ms;
+        s.bytes += p.bytes;
+        s.flops += p.flops;
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+}
+void Profiler::clear() {
+    stats.clear();
+    launch_base = launch_counter();
+}
+Profiler::~Profiler() {
+    for (auto& p : pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+}
+ProfScope::ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops)
+    : c(&ctx), idx(0), active(ctx.prof.on) {
+    if (!active) return;
+    Profiler::Pending p{key, c->prof.take(), c->prof.take(), bytes, flops};
+    MG_CUDA(cudaEventRecord(p.a, c->stream));
+    c->prof.pending.push_back(p);
+    idx = c->prof.pending.size() - 1;
+}
+ProfScope::~ProfScope() {
+    if (active) cudaEventRecord(c->prof.pending[idx].b, c->stream);
+}
+
+// ------------------------------------------------------------------ gauge
+void upload_links(Ctx& c, const double* theta) {
+    const int V = c.Lx * c.Lt;
+    std::vector<double2> U((size_t)2 * V);
+    for (int i = 0; i < 2 * V; ++i) {
+        const double th = theta[i];
+        MG_REQUIRE(std::isfinite(th), MGMLMC_ENAN, "set_gauge: non-finite link angle");
+        U[i] = make_double2(std::cos(th), std::sin(th));
+    }
+    c.dev_free(c.U64);
+    c.dev_free(c.U32);
+    c.U64 = c.alloc_n<double2>((size_t)2 * V);
+    c.U32 = c.alloc_n<float2>((size_t)2 * V);
+    MG_CUDA(cudaMemcpyAsync(c.U64, U.data(), sizeof(double2) * 2 * V, cudaMemcpyHostToDevice, c.stream));
+    launch_convert<float2, double2>(c.U32, c.U64, 2LL * V, c.stream);
+    c.sync();
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void k_scale_cols_rsqrt(double2* W, const double* lam, int b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b * b) return;
+    const int col = e % b;
+    const double l = lam[col];
+    const double f = (l > 0.0) ? 1.0 / sqrt(l) : 0.0;
+    W[e] = make_double2(W[e].x * f, W[e].y * f);
+}
+__global__ void k_hermitize(double2* G, int b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b * b) return;
+    const int i = e / b, j = e % b;
+    if (i > j) return;
+    const double2 a = G[i * b + j], t = G[j * b + i];
+    const double2 h = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y - t.y));
+    G[i * b + j] = h;
+    G[j * b + i] = make_double2(h.x, -h.y);
+}
+__global__ void k_resid_cols(double2* R, const double2* QX, const double2* X, const double* lam, long long n, int b) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n * b) return;
+    const int col = (int)(e % b);
+    R[e] = make_double2(QX[e].x - lam[col] * X[e].x, QX[e].y - lam[col] * X[e].y);
+}
+__global__ void k_sign_cols(double2* Y, const double* lam, long long n, int b) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n * b) return;
+    if (lam[(int)(e % b)] < 0.0) Y[e] = make_double2(-Y[e].x, -Y[e].y);
+}
+__global__ void k_inv_abs(double* a, const double* lam, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) a[i] = 1.0 / fabs(lam[i]);
+}
+// tau = sum_i a_i t_i  (t_i = u_i^H v_i), fixed order, one thread.
+__global__ void k_weighted_sum(double2* out, const double2* t, const double* a, int k) {
+    if (threadIdx.x || blockIdx.x) return;
+    double2 s = make_double2(0, 0);
+    for (int i = 0; i < k; ++i) s = make_double2(s.x + a[i] * t[i].x, s.y + a[i] * t[i].y);
+    *out = s;
+}
+
+static void small_launch_check() { MG_LAUNCHED(); }
+
+void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);   // solver.cu
+
+// ------------------------------------------------------------------ hierarchy
+static void coarsest_inverse(Ctx& c) {
+    Level& L = c.lev[c.L - 1];
+    const long long n = L.n;
+    MG_REQUIRE(n <= 16384, MGMLMC_ENOTIMPL, "coarsest level above 16384 unknowns (dense inverse) not supported");
+    double2* Dd = c.scratch<double2>("dense_D", (size_t)n * n);
+    launch_dense_from_blocks(Dd, L.A64, L.lx, L.lt, L.d, c.stream);
+    void* work = c.scratch_bytes("gj_work", gauss_jordan_work_bytes((int)n));
+    int* status = reinterpret_cast<int*>(reinterpret_cast<double2*>(work) + n) + n;
+    if (c.opt.mg_precision == 64) {
+        if (!L.Dinv64) L.Dinv64 = c.alloc_n<double2>((size_t)n * n);
+        MG_CUDA(cudaMemcpyAsync(L.Dinv64, Dd, sizeof(double2) * n * n, cudaMemcpyDeviceToDevice, c.stream));
+        launch_gauss_jordan<double2>(L.Dinv64, (int)n, work, c.stream);
+    } else {
+        if (!L.Dinv32) L.Dinv32 = c.alloc_n<float2>((size_t)n * n);
+        launch_convert<float2, double2>(L.Dinv32, Dd, n * n, c.stream);
+        launch_gauss_jordan<float2>(L.Dinv32, (int)n, work, c.stream);
+    }
+    int hs = 0;
+    MG_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    MG_REQUIRE(hs == 0, MGMLMC_EINVAL, "coarsest operator is singular (zero pivot)");
+}
+
+static void rebuild_from(Ctx& c, int l0) {
+    int* status = c.scratch<int>("status", 4);
+    for (int l = l0; l < c.L - 1; ++l) {
+        Level& L = c.lev[l];
+        Level& Lc = c.lev[l + 1];
+        MG_CUDA(cudaMemsetAsync(status, 0, sizeof(int), c.stream));
+        launch_build_prolongator(L.P64, L.tv, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, status, c.stream);
+        int hs = 0;
+        MG_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        MG_REQUIRE(hs == 0, MGMLMC_EINVAL,
+                   "set_hierarchy: rank-deficient test vectors on an aggregate of level " + std::to_string(l + 1));
+        launch_convert<float2, double2>(L.P32, L.P64, L.n * L.nvec, c.stream);
+        launch_galerkin(Lc.A64, L.A64, L.P64, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, c.stream);
+        launch_convert<float2, double2>(Lc.A32, Lc.A64, (long long)Lc.nsites * 5 * Lc.d * Lc.d, c.stream);
+    }
+    coarsest_inverse(c);
+}
+
+void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* nvec, int setup_iters,
+                     double setup_tol, const double* const* sv) {
+    MG_REQUIRE(c.have_gauge && c.have_mass, MGMLMC_ESTATE, "set_hierarchy: gauge field and mass must be set first");
+    MG_REQUIRE(nlev >= 1 && nlev <= MGMLMC_MAX_LEVELS, MGMLMC_EINVAL, "set_hierarchy: 1 <= nlevels <= 6");
+    MG_REQUIRE(setup_iters >= 0 && setup_iters <= 100, MGMLMC_EINVAL, "set_hierarchy: 0 <= setup_iters <= 100");
+    MG_REQUIRE(nlev == 1 || (ax && at && nvec && sv), MGMLMC_EINVAL, "set_hierarchy: NULL argument");
+    int lx = c.Lx, lt = c.Lt, d = 2;
+    for (int l = 0; l < nlev - 1; ++l) {
+        MG_REQUIRE(ax[l] >= 1 && at[l] >= 1 && lx % ax[l] == 0 && lt % at[l] == 0, MGMLMC_EINVAL,
+                   "set_hierarchy: aggregate extents must divide the lattice of level " + std::to_string(l + 1));
+        MG_REQUIRE(nvec[l] >= 1 && nvec[l] <= 32, MGMLMC_EINVAL, "set_hierarchy: 1 <= nvec <= 32");
+        MG_REQUIRE(nvec[l] <= ax[l] * at[l] * d / 2, MGMLMC_EINVAL,
+                   "set_hierarchy: more test vectors than rows of an aggregate block on level " + std::to_string(l + 1));
+        MG_REQUIRE(sv[l] != nullptr, MGMLMC_EINVAL, "set_hierarchy: missing start vectors");
+        lx /= ax[l];
+        lt /= at[l];
+        d = 2 * nvec[l];
+    }
+    MG_REQUIRE((long long)lx * lt * d <= 16384, MGMLMC_ENOTIMPL,
+               "set_hierarchy: coarsest level above 16384 unknowns (dense inverse) not supported");
+    c.free_hierarchy();
+    c.L = nlev;
+    lx = c.Lx; lt = c.Lt; d = 2;
+    for (int l = 0; l < nlev; ++l) {
+        Level& L = c.lev[l];
+        L.lx = lx; L.lt = lt; L.d = d;
+        L.nsites = lx * lt;
+        L.n = (long long)L.nsites * d;
+        L.A64 = c.alloc_n<double2>((size_t)L.nsites * 5 * d * d);
+        if (l > 0) L.A32 = c.alloc_n<float2>((size_t)L.nsites * 5 * d * d);
+        if (l < nlev - 1) {
+            L.ax = ax[l]; L.at = at[l]; L.nvec = nvec[l];
+            L.P64 = c.alloc_n<double2>((size_t)L.n * L.nvec);
+            L.P32 = c.alloc_n<float2>((size_t)L.n * L.nvec);
+            L.tv = c.alloc_n<double2>((size_t)L.n * L.nvec);
+            MG_CUDA(cudaMemcpyAsync(L.tv, sv[l], sizeof(double2) * L.n * L.nvec, cudaMemcpyHostToDevice, c.stream));
+            lx /= ax[l]; lt /= at[l]; d = 2 * nvec[l];
+        }
+    }
+    launch_materialize_wilson(c.lev[0].A64, c.U64, c.m0, c.Lx, c.Lt, c.stream);
+    rebuild_from(c, 0);
+    for (int l = 0; l < nlev - 1; ++l) {
+        Level& L = c.lev[l];
+        for (int it = 0; it < setup_iters; ++it) {
+            const int nv = L.nvec;
+            double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
+            double2* X = c.scratch<double2>("setup_X", (size_t)L.n * nv);
+            double* nrm = c.scratch<double>("setup_nrm", nv);
+            launch_transpose(B, L.tv, nv, (int)L.n, c.stream);
+            int ok = 0;
+            solve(c, l, B, X, nv, setup_tol, &ok);
+            MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED,
+                       "set_hierarchy: inverse-iteration solve on level " + std::to_string(l + 1) + " did not converge");
+            column_norms(c, nrm, X, L.n, nv);
+            launch_scale_rhs<double2, double2>(X, X, nrm, true, L.n, nv, c.stream);
+            launch_transpose(L.tv, X, L.n, nv, c.stream);
+            rebuild_from(c, l);
+        }
+    }
+    c.sync();
+    c.have_hier = true;
+    c.nterms = nlev;
+    for (int t = 0; t < nlev; ++t) c.term_level[t] = t;
+    c.skip.clear();
+}
+
+// ------------------------------------------------------------------ deflation
+static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
+    double2* G = c.scratch<double2>("df_G", (size_t)b * b);
+    double2* W = c.scratch<double2>("df_W", (size_t)b * b);
+    double* lam = c.scratch<double>("df_lamG", b);
+    const int groups = gemm_hn_groups(n, b, b);
+    double2* part = c.scratch<double2>("df_part", (size_t)groups * b * b);
+    for (int pass = 0; pass < 2; ++pass) {   // Loewdin orthonormalisation, twice
+        launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
+        k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(G, b);
+        small_launch_check();
+        launch_jacobi_eig(G, W, lam, b, 40, c.stream);
+        k_scale_cols_rsqrt<<<(b * b + 127) / 128, 128, 0, c.stream>>>(W, lam, b);
+        small_launch_check();
+        launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
+        std::swap(X, Y);
+    }
+}
+
+void compute_deflation(Ctx& c, int k, double tol, int max_iters) {
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "compute_deflation: no hierarchy");
+    c.free_deflation();
+    if (k == 0) return;
+    const int l = c.L - 1;
+    const Level& L = c.lev[l];
+    const long long n = L.n;
+    MG_REQUIRE(k >= 1 && k <= n && k <= 512, MGMLMC_EINVAL, "compute_deflation: 0 <= k <= min(n_L, 512)");
+    MG_REQUIRE(tol > 0 && max_iters >= 1, MGMLMC_EINVAL, "compute_deflation: tol > 0 and max_iters >= 1");
+    const int b = (int)std::min<long long>(n, std::max(2 * k, k + 16));
+    double2* X = c.scratch<double2>("df_X", (size_t)n * b);
+    double2* Y = c.scratch<double2>("df_Y", (size_t)n * b);
+    double2* T = c.scratch<double2>("df_T", (size_t)n * b);
+    double2* T2 = c.scratch<double2>("df_T2", (size_t)n * b);
+    double2* H = c.scratch<double2>("df_H", (size_t)b * b);
+    double2* W = c.scratch<double2>("df_WR", (size_t)b * b);
+    double* lam = c.scratch<double>("df_lam", b);
+    double* res = c.scratch<double>("df_res", b);
+    const int groups = gemm_hn_groups(n, b, b);
+    double2* part = c.scratch<double2>("df_partR", (size_t)groups * b * b);
+    launch_noise<double2>(X, n, b, 0x2211153830ull, 77, 0, c.stream);
+    orthonormalize(c, X, Y, n, b);
+    std::vector<double> h_lam(b), h_res(b);
+    bool conv = false;
+    for (int it = 0; it < max_iters && !conv; ++it) {
+        // X <- Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves), then orthonormalise
+        launch_gamma5<double2>(T, X, L.nsites, L.d, b, c.stream);
+        int ok = 0;
+        solve(c, l, T, Y, b, c.opt.solve_tol, &ok);
+        MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "compute_deflation: coarsest solve did not converge");
+        std::swap(X, Y);
+        orthonormalize(c, X, Y, n, b);
+        // Rayleigh-Ritz with Q = Gamma5 D
+        apply_D<double2>(c, l, T, X, nullptr, b, 0, nullptr);
+        launch_gamma5<double2>(T, T, L.nsites, L.d, b, c.stream);
+        launch_gemm_hn<double2>(H, X, T, n, b, b, part, groups, c.stream);
+        k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(H, b);
+        small_launch_check();
+        launch_jacobi_eig(H, W, lam, b, 40, c.stream);
+        launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
+        launch_gemm_nn<double2>(T2, T, W, (int)n, b, b, false, c.stream);
+        std::swap(X, Y);
+        k_resid_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(T, T2, X, lam, n, b);
+        small_launch_check();
+        column_norms(c, res, T, n, b);
+        MG_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+        MG_CUDA(cudaMemcpyAsync(h_res.data(), res, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        double worst = 0;
+        for (int i = 0; i < k; ++i) worst = std::max(worst, h_res[i] / std::fabs(h_lam[i]));
+        if (c.opt.verbose) fprintf(stderr, "[mgmlmc] deflation it %d worst rel residual %.3e\n", it, worst);
+        conv = worst <= tol;
+    }
+    // store V = X_k, U = Gamma5 X_k sign(lambda), a = 1/|lambda|
+    c.defl.k = k;
+    c.defl.Lv = c.alloc_n<double2>((size_t)n * k);
+    c.defl.Rv = c.alloc_n<double2>((size_t)n * k);
+    c.defl.a = c.alloc_n<double>(k);
+    MG_CUDA(cudaMemcpy2DAsync(c.defl.Lv, sizeof(double2) * k, X, sizeof(double2) * b, sizeof(double2) * k, n,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    launch_gamma5<double2>(T, X, L.nsites, L.d, b, c.stream);
+    k_sign_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(T, lam, n, b);
+    small_launch_check();
+    MG_CUDA(cudaMemcpy2DAsync(c.defl.Rv, sizeof(double2) * k, T, sizeof(double2) * b, sizeof(double2) * k, n,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    k_inv_abs<<<(k + 127) / 128, 128, 0, c.stream>>>(c.defl.a, lam, k);
+    small_launch_check();
+    // tau = sum_i a_i u_i^H v_i  (Eq. small_trace_term), FP64 from the stored factors
+    double2* t = c.scratch<double2>("df_t", k);
+    double2* tau = c.scratch<double2>("df_tau", 1);
+    double2* dpart = c.scratch<double2>("df_dpart", (size_t)reduce_groups(n, k) * k);
+    launch_dot<double2, double2>(t, c.defl.Rv, c.defl.Lv, n, k, dpart, c.stream);
+    k_weighted_sum<<<1, 1, 0, c.stream>>>(tau, t, c.defl.a, k);
+    small_launch_check();
+    double2 htau;
+    MG_CUDA(cudaMemcpyAsync(&htau, tau, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    c.defl.tau_re = htau.x;
+    c.defl.tau_im = htau.y;
+    c.defl.lambda.assign(h_lam.begin(), h_lam.begin() + k);
+    if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "compute_deflation: eigensolver did not reach tol (results kept)");
+}
+
+}  // namespace mg

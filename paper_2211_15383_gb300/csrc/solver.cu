@@ -1,0 +1,307 @@
+// Solver layer: operator application per level, the multigrid cycle used as a
+// preconditioner (Sect. 3.1, Eq. two_level_mg_method applied recursively), the
+// multi-RHS flexible GMRES, and the FP64 outer solve (plain FP64 FGMRES, or
+// FP64 iterative refinement around an FP32 FGMRES for the mixed mode).
+//
+// The smoother S^(nu) is nu steps of minimal residual (GMRES(1)) per rhs: one
+// of the Krylov smoothers Sect. 3.1 lists; FGMRES tolerates its
+// non-linearity.  The coarsest level is solved by its stored dense inverse.
+#include <cmath>
+#include <cstdio>
+
+#include "context.h"
+
+namespace mg {
+
+template <typename C> static const C* links(Ctx& c);
+template <> const double2* links<double2>(Ctx& c) { return c.U64; }
+template <> const float2* links<float2>(Ctx& c) { return c.U32; }
+template <typename C> static const C* blocks(const Level& L);
+template <> const double2* blocks<double2>(const Level& L) { return L.A64; }
+template <> const float2* blocks<float2>(const Level& L) { return L.A32; }
+template <typename C> static const C* prol(const Level& L);
+template <> const double2* prol<double2>(const Level& L) { return L.P64; }
+template <> const float2* prol<float2>(const Level& L) { return L.P32; }
+
+static std::string nm(const char* base, int l, size_t sz) {
+    return std::string(base) + "_" + std::to_string(l) + "_" + std::to_string(sz);
+}
+
+static const char* prec_tag(size_t sz) { return sz == sizeof(double2) ? "f64" : "f32"; }
+
+static int bs_groups(int nsites, int N) {
+    int want = 8 * kNumSM / rhs_tiles(N);
+    if (want < 1) want = 1;
+    return nsites < want ? nsites : want;
+}
+
+template <typename C>
+void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, double2* dots) {
+    const Level& L = c.lev[l];
+    const int groups = (l == 0) ? stencil_groups(L.nsites, N) : bs_groups(L.nsites, N);
+    // algorithmic traffic: read x once, write y once (+ b for the residual form),
+    // operator data once; flops: 60 per fine site and rhs, 8 d^2 * 5 per coarse site and rhs
+    const double s = sizeof(C);
+    const double vec = (double)L.n * N * s;
+    const double bytes = vec * (mode == 1 ? 3 : 2) +
+                         (l == 0 ? 2.0 * L.nsites * s : 5.0 * L.nsites * L.d * L.d * s);
+    const double flops = (l == 0) ? 60.0 * L.nsites * N : 40.0 * L.d * L.d * (double)L.nsites * N;
+    ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), bytes, flops);
+    double2* part = nullptr;
+    if (mode == 2) part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
+    if (l == 0)
+        launch_wilson<C>(y, x, b, links<C>(c), c.m0, L.lx, L.lt, N, mode, part, groups, c.stream);
+    else
+        launch_block_stencil<C>(y, x, b, blocks<C>(L), L.lx, L.lt, L.d, N, mode, part, groups, c.stream);
+    if (mode == 2) launch_finalize(dots, part, groups, 2 * N, c.stream);
+}
+
+template <typename C>
+void apply_restrict(Ctx& c, int l, C* xc, const C* x, int N) {
+    const Level& L = c.lev[l];
+    const double s = sizeof(C);
+    ProfScope ps(c, "PH" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
+                 (double)L.n * N * s + (double)c.lev[l + 1].n * N * s + (double)L.n * L.nvec * s,
+                 8.0 * L.nvec * (double)L.n * N);
+    launch_restrict<C>(xc, x, prol<C>(L), L.lx, L.lt, L.d, L.ax, L.at, L.nvec, N, c.stream);
+}
+
+template <typename C>
+void apply_prolong(Ctx& c, int l, C* x, const C* xc, int N, bool accumulate) {
+    const Level& L = c.lev[l];
+    const double s = sizeof(C);
+    ProfScope ps(c, "P" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
+                 (double)L.n * N * s * (accumulate ? 2 : 1) + (double)c.lev[l + 1].n * N * s + (double)L.n * L.nvec * s,
+                 8.0 * L.nvec * (double)L.n * N);
+    launch_prolong<C>(x, xc, prol<C>(L), L.lx, L.lt, L.d, L.ax, L.at, L.nvec, N, accumulate, c.stream);
+}
+
+template <typename C> static void coarsest_apply(Ctx& c, C* e, const C* r, int N);
+static double dinv_bytes(const Level& L, int N, double s) { return (double)L.n * L.n * s + 2.0 * L.n * N * s; }
+static double dinv_flops(const Level& L, int N) { return 8.0 * (double)L.n * L.n * N; }
+template <> void coarsest_apply<double2>(Ctx& c, double2* e, const double2* r, int N) {
+    const Level& L = c.lev[c.L - 1];
+    ProfScope ps(c, "Dinv.f64", dinv_bytes(L, N, 16), dinv_flops(L, N));
+    launch_gemm_nn<double2>(e, L.Dinv64, r, (int)L.n, (int)L.n, N, false, c.stream);
+}
+template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int N) {
+    const Level& L = c.lev[c.L - 1];
+    ProfScope ps(c, "Dinv.f32", dinv_bytes(L, N, 8), dinv_flops(L, N));
+    launch_gemm_nn<float2>(e, L.Dinv32, r, (int)L.n, (int)L.n, N, false, c.stream);
+}
+
+// nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual
+// on entry and is overwritten.
+template <typename C>
+static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero) {
+    const Level& L = c.lev[l];
+    C* p = c.scratch<C>(nm("mr_p", l, sizeof(C)), (size_t)L.n * N);
+    double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(C)), 2 * (size_t)N);
+    for (int s = 0; s < nu; ++s) {
+        apply_D<C>(c, l, p, r, nullptr, N, 2, dots);
+        ProfScope ps(c, "mr" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), 5.0 * L.n * N * sizeof(C),
+                     16.0 * L.n * N);
+        launch_mr_update<C>(e, r, p, dots, L.n, N, e_zero && s == 0, c.stream);
+    }
+}
+
+template <typename C>
+void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
+    if (l == c.L - 1) {
+        coarsest_apply<C>(c, e, r, N);
+        return;
+    }
+    const Level& L = c.lev[l];
+    const Level& Lc = c.lev[l + 1];
+    C* res = c.scratch<C>(nm("cyc_res", l, sizeof(C)), (size_t)L.n * N);
+    C* rc = c.scratch<C>(nm("cyc_rc", l + 1, sizeof(C)), (size_t)Lc.n * N);
+    C* ec = c.scratch<C>(nm("cyc_ec", l + 1, sizeof(C)), (size_t)Lc.n * N);
+    bool e_zero = true;
+    if (c.opt.nu_pre > 0) {
+        MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C) * L.n * N, cudaMemcpyDeviceToDevice, c.stream));
+        mr_smooth<C>(c, l, e, res, N, c.opt.nu_pre, true);   // leaves res = r - D e
+        e_zero = false;
+        apply_restrict<C>(c, l, rc, res, N);
+    } else {
+        apply_restrict<C>(c, l, rc, r, N);
+    }
+    mg_cycle<C>(c, l + 1, ec, rc, N);
+    apply_prolong<C>(c, l, e, ec, N, !e_zero);
+    if (c.opt.nu_post > 0) {
+        apply_D<C>(c, l, res, e, r, N, 1, nullptr);
+        mr_smooth<C>(c, l, e, res, N, c.opt.nu_post, false);
+    }
+}
+
+static double read_scalar(Ctx& c, const double* dev) {
+    MG_CUDA(cudaMemcpyAsync(c.hbuf, dev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    return c.hbuf[0];
+}
+
+__global__ void k_sqrt_inplace(double* v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = sqrt(v[i]);
+}
+__global__ void k_add2(double2* a, const double2* b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
+}
+
+template <typename C>
+static void norms(Ctx& c, double* out, const C* x, long long n, int N) {
+    double* part = c.scratch<double>("part_nrm", (size_t)reduce_groups(n, N) * N);
+    launch_norm2<C>(out, x, n, N, part, c.stream);
+    k_sqrt_inplace<<<(N + 127) / 128, 128, 0, c.stream>>>(out, N);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long maxit, bool x_zero, int* ok,
+                 int max_cycles) {
+    const Level& L = c.lev[l];
+    const long long n = L.n;
+    const int m = c.opt.fgmres_restart;
+    const size_t nN = (size_t)n * N;
+    const size_t sz = sizeof(C);
+    C* V = c.scratch<C>(nm("fg_V", 0, sz), (size_t)(m + 1) * nN);
+    C* Z = c.scratch<C>(nm("fg_Z", 0, sz), (size_t)m * nN);
+    double* bnorm = c.scratch<double>(nm("fg_bn", 0, sz), N);
+    double* beta = c.scratch<double>(nm("fg_beta", 0, sz), N);
+    double* hnorm = c.scratch<double>(nm("fg_hn", 0, sz), N);
+    double* resid = c.scratch<double>(nm("fg_res", 0, sz), N);
+    double* maxr = c.scratch<double>(nm("fg_maxr", 0, sz), 1);
+    double2* h = c.scratch<double2>(nm("fg_h", 0, sz), (size_t)(m + 1) * N);
+    double2* h2 = c.scratch<double2>(nm("fg_h2", 0, sz), (size_t)(m + 1) * N);
+    double2* y = c.scratch<double2>(nm("fg_y", 0, sz), (size_t)(m + 1) * N);
+    double2* H = c.scratch<double2>(nm("fg_H", 0, sz), (size_t)N * (m + 1) * m);
+    double* cs = c.scratch<double>(nm("fg_cs", 0, sz), (size_t)N * m);
+    double2* sn = c.scratch<double2>(nm("fg_sn", 0, sz), (size_t)N * m);
+    double2* g = c.scratch<double2>(nm("fg_g", 0, sz), (size_t)N * (m + 1));
+    double2* part = c.scratch<double2>("part_md", (size_t)reduce_groups(n, N) * (m + 1) * N);
+
+    norms<C>(c, bnorm, b, n, N);
+    if (x_zero) launch_zero<C>(x, (long long)nN, c.stream);
+    long long it = 0;
+    int cycles = 0;
+    *ok = 0;
+    for (;;) {
+        if (x_zero && it == 0)
+            MG_CUDA(cudaMemcpyAsync(V, b, sz * nN, cudaMemcpyDeviceToDevice, c.stream));
+        else
+            apply_D<C>(c, l, V, x, b, N, 1, nullptr);
+        norms<C>(c, beta, V, n, N);
+        launch_max_ratio(maxr, beta, bnorm, N, c.stream);
+        const double ratio = read_scalar(c, maxr);
+        if (ratio != ratio) throw Error(MGMLMC_ENAN, "FGMRES: NaN residual");
+        if (c.opt.verbose)
+            fprintf(stderr, "[mgmlmc] fgmres level %d prec %zu it %lld true rel res %.3e\n", l + 1, sz * 4, it,
+                    ratio);
+        if (ratio <= tol) {
+            *ok = 1;
+            break;
+        }
+        if (it >= maxit) break;
+        launch_scale_rhs<C, C>(V, V, beta, true, n, N, c.stream);
+        launch_init_g(g, beta, m, N, c.stream);
+        int j_end = -1;
+        for (int j = 0; j < m; ++j) {
+            C* Vj = V + (size_t)j * nN;
+            C* Vn = V + (size_t)(j + 1) * nN;
+            C* Zj = Z + (size_t)j * nN;
+            mg_cycle<C>(c, l, Zj, Vj, N);
+            apply_D<C>(c, l, Vn, Zj, nullptr, N, 0, nullptr);
+            // classical Gram-Schmidt, twice
+            {
+                ProfScope ps(c, "orth." + std::string(prec_tag(sz)), 2.0 * (2 * j + 5) * (double)nN * sz,
+                             4.0 * 8.0 * (j + 1) * (double)nN);
+                launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
+                launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream);
+                launch_multidot<C>(h2, V, j + 1, Vn, n, N, part, c.stream);
+                launch_multiaxpy<C>(Vn, h2, j + 1, V, -1.0, n, N, c.stream);
+            }
+            k_add2<<<((j + 1) * N + 127) / 128, 128, 0, c.stream>>>(h, h2, (j + 1) * N);
+            MG_LAUNCHED();
+            norms<C>(c, hnorm, Vn, n, N);
+            launch_scale_rhs<C, C>(Vn, Vn, hnorm, true, n, N, c.stream);
+            launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, m, N, c.stream);
+            ++it;
+            j_end = j;
+            launch_max_ratio(maxr, resid, bnorm, N, c.stream);
+            const double est = read_scalar(c, maxr);
+            if (est != est) throw Error(MGMLMC_ENAN, "FGMRES: NaN in Arnoldi");
+            if (est <= tol || it >= maxit) break;
+        }
+        launch_back_substitute(y, H, g, j_end, m, N, c.stream);
+        launch_multiaxpy<C>(x, y, j_end + 1, Z, 1.0, n, N, c.stream);
+        x_zero = false;
+        if (++cycles >= max_cycles) {
+            // the caller checks the residual itself (inner solve of the refinement loop)
+            *ok = 1;
+            break;
+        }
+    }
+    return it;
+}
+
+long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok) {
+    const long long maxit = c.opt.max_iters;
+    if (c.opt.mg_precision == 64) {
+        const long long it = fgmres<double2>(c, l, b, x, N, tol, maxit, true, ok, 1 << 30);
+        c.last_iters = it;
+        return it;
+    }
+    // Mixed: FP64 iterative refinement, FP32 FGMRES + FP32 multigrid inside.
+    const Level& L = c.lev[l];
+    const long long n = L.n;
+    const size_t nN = (size_t)n * N;
+    double2* r = c.scratch<double2>("ir_r", nN);
+    float2* r32 = c.scratch<float2>("ir_r32", nN);
+    float2* e32 = c.scratch<float2>("ir_e32", nN);
+    double* bnorm = c.scratch<double>("ir_bn", N);
+    double* rnorm = c.scratch<double>("ir_rn", N);
+    double* maxr = c.scratch<double>("ir_maxr", 1);
+    const double inner_tol = 1e-6;
+    norms<double2>(c, bnorm, b, n, N);
+    launch_zero<double2>(x, (long long)nN, c.stream);
+    MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * nN, cudaMemcpyDeviceToDevice, c.stream));
+    long long it = 0;
+    *ok = 0;
+    for (int cycle = 0; cycle < 40; ++cycle) {
+        norms<double2>(c, rnorm, r, n, N);
+        launch_max_ratio(maxr, rnorm, bnorm, N, c.stream);
+        const double ratio = read_scalar(c, maxr);
+        if (ratio != ratio) throw Error(MGMLMC_ENAN, "refinement: NaN residual");
+        if (c.opt.verbose)
+            fprintf(stderr, "[mgmlmc] refine level %d cycle %d it %lld rel res %.3e\n", l + 1, cycle, it, ratio);
+        if (ratio <= tol) {
+            *ok = 1;
+            break;
+        }
+        if (it >= maxit) break;
+        launch_scale_rhs<float2, double2>(r32, r, rnorm, true, n, N, c.stream);
+        int iok = 0;
+        // one FGMRES cycle in FP32: its own FP32 residual cannot certify more than
+        // ~1e-6 relative, so the FP64 residual of this loop decides on restarts
+        it += fgmres<float2>(c, l, r32, e32, N, inner_tol, maxit - it, true, &iok, 1);
+        launch_axpy_rhs<double2, float2>(x, nullptr, rnorm, 1.0, e32, n, N, c.stream);
+        apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
+    }
+    c.last_iters = it;
+    return it;
+}
+
+#define INST(C)                                                                                           \
+    template void apply_D<C>(Ctx&, int, C*, const C*, const C*, int, int, double2*);                        \
+    template void apply_restrict<C>(Ctx&, int, C*, const C*, int);                                          \
+    template void apply_prolong<C>(Ctx&, int, C*, const C*, int, bool);                                     \
+    template void mg_cycle<C>(Ctx&, int, C*, const C*, int);                                                \
+    template long long fgmres<C>(Ctx&, int, const C*, C*, int, double, long long, bool, int*, int);
+INST(double2)
+INST(float2)
+
+}  // namespace mg
+
+namespace mg {
+void column_norms(Ctx& c, double* out, const double2* x, long long n, int N) { norms<double2>(c, out, x, n, N); }
+}  // namespace mg

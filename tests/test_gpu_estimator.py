@@ -1,0 +1,117 @@
+"""Per-sample parity of the GPU estimator with the oracle on identical seeded
+noise (FP64 bar 1e-9 relative), deflation triplets, ragged blocks, the
+probe-vector entry, mixed precision, skip-a-level terms and the MLMC loop."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import deflation as odefl
+from oracle import estimator as oest
+from oracle import hierarchy as ohier
+
+from gpu_common import make_ctx, rel_sample_error, require_gpu, small_problem
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """The 16x16 workload: 2 levels, 4x4 aggregates, 4 test vectors per spin, k = 16."""
+    w = inputs.workload("schwinger-16x16")
+    theta = w.gauge()
+    sv = w.start_vectors()
+    H = ohier.build_hierarchy(theta, w.m0, w.agg, w.nvec, sv, w.setup_iters)
+    defl = odefl.coarsest_deflation(H.D[-1], H.g5[-1], w.k)
+    return w, theta, sv, H, defl
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_c1_samples_match_oracle(pkg, c1, prec):
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=prec) as ctx:
+        # test vectors after the setup iteration agree with the oracle's exact inverse iteration
+        tv = ctx.get_test_vectors(1, w.nvec[0])
+        assert np.abs(tv - H.test_vectors[0]).max() < 1e-9
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        lam, sig, U, V, tau = ctx.get_deflation(w.k, 2)
+        assert np.abs(sig - 1.0 / defl.a).max() < 1e-10 * sig.max()
+        assert abs(tau - defl.trace_term()) < 1e-9 * abs(defl.trace_term())
+        Pg = V.T @ V.conj()
+        Po = defl.L @ defl.L.conj().T
+        assert np.abs(Pg - Po).max() < 1e-8
+        for t, term in enumerate(oest.term_list(2)):
+            got, st = ctx.estimate_level(t, 0, w.nrhs, w.noise_seed)
+            ref = oest.noise_samples(H, term, w.noise_seed, 0, w.nrhs, solvers,
+                                     defl if term[1] is None else None)
+            assert rel_sample_error(got, ref) < TOL64, (prec, term)
+            assert st["nsamples"] == w.nrhs
+            assert abs(st["mean_re"] - ref.mean().real) < 1e-9 * max(1, abs(ref.mean()))
+
+
+def test_ragged_blocks_and_probes(pkg, c1):
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, max_block_rhs=16) as ctx:
+        got, _ = ctx.estimate_level(0, 7, 37, 99)
+        ref = oest.noise_samples(H, (1, 2), 99, 7, 37, solvers)
+        assert rel_sample_error(got, ref) < TOL64
+        # caller-supplied probes: random signs from the shared input generator
+        n = H.D[0].shape[0]
+        probes = np.where(inputs.uniform(4, 4, 5 * n).reshape(5, n) < 0.5, 1, -1).astype(np.int8)
+        gp, _ = ctx.estimate_level_probes(0, probes)
+        rp = oest.term_samples(H, (1, 2), probes.astype(float), solvers)
+        assert rel_sample_error(gp, rp) < TOL64
+
+
+def test_setup_without_iterations_and_single_rhs(pkg):
+    theta, sv = small_problem(agg=((2, 2), (2, 2)), nvec=(2, 2))
+    H = ohier.build_hierarchy(theta, 0.05, ((2, 2), (2, 2)), (2, 2), sv, 0)
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, 0.05, ((2, 2), (2, 2)), (2, 2), sv, 0) as ctx:
+        for t, term in enumerate(oest.term_list(3)):
+            got, _ = ctx.estimate_level(t, 3, 1, 5)
+            ref = oest.noise_samples(H, term, 5, 3, 1, solvers)
+            assert rel_sample_error(got, ref) < TOL64
+
+
+def test_skip_level_terms(pkg):
+    agg, nvec = ((2, 2), (2, 1), (1, 2)), (2, 2, 2)
+    theta, sv = small_problem(agg=agg, nvec=nvec)
+    H = ohier.build_hierarchy(theta, 0.05, agg, nvec, sv, 1)
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, 0.05, agg, nvec, sv, 1) as ctx:
+        ctx.set_terms([2])
+        nt, levels = ctx.num_terms()
+        assert (nt, levels) == (3, [1, 3, 4])
+        for t, term in enumerate(oest.term_list(4, skip=(2,))):
+            got, _ = ctx.estimate_level(t, 0, 20, 11)
+            ref = oest.noise_samples(H, term, 11, 0, 20, solvers)
+            assert rel_sample_error(got, ref) < TOL64, term
+
+
+def test_mlmc_loop_matches_oracle_rule(pkg, c1):
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    costs = [1.0, 0.1]
+    terms = oest.term_list(2)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters) as ctx:
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        res = ctx.estimate_trace(2e-2, 200000, 31, costs)
+
+    def fn(t, first, count):
+        term = terms[t]
+        return oest.noise_samples(H, term, 31, first, count, solvers, defl if term[1] is None else None)
+
+    ref = oest.mlmc_estimate(fn, 2, 2e-2, 200000, costs, tau=defl.trace_term())
+    assert res["converged"] == 1 and ref["converged"]
+    assert [t["nsamples"] for t in res["terms"]] == ref["N"]
+    assert abs(res["trace"] - ref["estimate"]) < 1e-9 * abs(ref["estimate"])
+    exact = np.trace(np.linalg.inv(H.D[0].toarray()))
+    assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)

@@ -1,0 +1,107 @@
+"""GPU operator parity against the oracle: D_l, P^H, P, Gamma5, the coarsest
+inverse and the Z2 noise, on seeded inputs of several sizes (ragged rhs counts)."""
+import numpy as np
+import pytest
+
+from oracle import hierarchy as ohier
+from oracle import noise as onoise
+from oracle import wilson as owilson
+
+from gpu_common import make_ctx, rand_complex, require_gpu, small_problem
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (Lx, Lt, agg, nvec)
+    (8, 8, ((2, 2), (2, 2)), (2, 2)),
+    (16, 16, ((4, 4),), (4,)),
+    (12, 8, ((2, 4), (3, 1)), (2, 3)),
+]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("Lx,Lt,agg,nvec", CASES)
+@pytest.mark.parametrize("nrhs", [1, 3, 37])
+def test_operators_match_oracle(pkg, Lx, Lt, agg, nvec, nrhs):
+    m0 = 0.05
+    theta, sv = small_problem(Lx, Lt, agg=agg, nvec=nvec)
+    H = ohier.build_hierarchy(theta, m0, agg, nvec, sv, 0)
+    rng = np.random.default_rng(Lx * 100 + nrhs)
+    with make_ctx(pkg, theta, m0, agg, nvec, sv, 0) as ctx:
+        for lev in range(1, H.nlevels + 1):
+            n = H.D[lev - 1].shape[0]
+            x = rand_complex(rng, (nrhs, n))
+            y = ctx.apply(pkg.OP_D, lev, x, n)
+            ref = (H.D[lev - 1] @ x.T).T
+            assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max(), f"D_{lev}"
+            g = ctx.apply(pkg.OP_G5, lev, x, n)
+            assert np.array_equal(g, H.g5[lev - 1][None, :] * x)
+            if lev < H.nlevels:
+                P = H.P[lev - 1]
+                nc = P.shape[1]
+                yc = ctx.apply(pkg.OP_PH, lev, x, nc)
+                refc = (P.conj().T @ x.T).T
+                assert np.abs(yc - refc).max() < 1e-13 * np.abs(refc).max(), f"P^H_{lev}"
+                xc = rand_complex(rng, (nrhs, nc))
+                yf = ctx.apply(pkg.OP_P, lev, xc, n)
+                reff = (P @ xc.T).T
+                assert np.abs(yf - reff).max() < 1e-13 * np.abs(reff).max(), f"P_{lev}"
+        # the coarsest level's stored inverse
+        L = H.nlevels
+        n = H.D[-1].shape[0]
+        b = rand_complex(rng, (nrhs, n))
+        z = ctx.apply(pkg.OP_DINV_C, L, b, n)
+        ref = np.linalg.solve(H.D[-1].toarray(), b.T).T
+        assert np.abs(z - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_free_field_fine_operator(pkg):
+    # theta = 0: the fine operator against the oracle at a non-square size
+    Lx, Lt, m0 = 6, 10, 0.3
+    theta = np.zeros((Lt, Lx, 2))
+    _, sv = small_problem(Lx, Lt, agg=((3, 5),), nvec=(1,))
+    with make_ctx(pkg, theta, m0, ((3, 5),), (1,), sv, 0) as ctx:
+        D = owilson.wilson_dirac(theta, m0)
+        x = rand_complex(np.random.default_rng(1), (5, D.shape[0]))
+        y = ctx.apply(pkg.OP_D, 1, x, D.shape[0])
+        assert np.abs(y - (D @ x.T).T).max() < 1e-13
+
+
+@pytest.mark.parametrize("first,ns", [(0, 1), (5, 33), (1000, 70)])
+def test_noise_bit_exact(pkg, first, ns):
+    theta, sv = small_problem()
+    with make_ctx(pkg, theta, 0.05, ((2, 2), (2, 2)), (2, 2), sv, 0) as ctx:
+        for lev in (1, 2, 3):
+            n = ctx.level_info(lev)[3]
+            x = ctx.noise(lev, first, ns, 0xABCDEF0123)
+            ref = onoise.z2_noise(0xABCDEF0123, lev, first, ns, n)
+            assert np.array_equal(x, ref)
+
+
+def test_rank_deficient_test_vectors_rejected(pkg):
+    theta, sv = small_problem(agg=((2, 2),), nvec=(2,))
+    sv = [np.stack([sv[0][0], 2.0 * sv[0][0]])]            # second vector parallel to the first
+    with pkg.Context() as ctx:
+        ctx.set_gauge(theta)
+        ctx.set_mass(0.05)
+        with pytest.raises(pkg.MgmlmcError) as e:
+            ctx.set_hierarchy(((2, 2),), (2,), sv, setup_iters=0)
+        assert e.value.code == -1
+
+
+def test_state_errors(pkg):
+    with pkg.Context() as ctx:
+        with pytest.raises(pkg.MgmlmcError) as e:
+            ctx.estimate_level(0, 0, 4, 1)
+        assert e.value.code == -8
+        with pytest.raises(pkg.MgmlmcError):
+            ctx.set_gauge(np.zeros((3, 4, 2)))          # odd Lt
+        bad = np.zeros((4, 4, 2))
+        bad[0, 0, 0] = np.nan
+        with pytest.raises(pkg.MgmlmcError) as e:
+            ctx.set_gauge(bad)
+        assert e.value.code == -7
