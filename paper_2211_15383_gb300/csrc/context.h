@@ -28,6 +28,7 @@ struct Level {
     // coarsest level: dense inverse [n][n]
     double2* Dinv64 = nullptr;
     float2* Dinv32 = nullptr;
+    __nv_bfloat16* Dinv16 = nullptr;  // [Re | Im] BF16 embedding for the tensor-core solve
 };
 
 struct Deflation {
@@ -89,6 +90,7 @@ struct Ctx {
     void* alloc_user = nullptr;
     std::string err;
     double* hbuf = nullptr;          // pinned host scratch for scalar read-backs
+    int* dev_err = nullptr;          // device error flag of kernels with bounded waits
     size_t hbuf_bytes = 0;
 
     int Lx = 0, Lt = 0;
@@ -138,6 +140,11 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
                  int max_cycles);
 // FP64-accurate solve D_l x = b (plain FP64 FGMRES, or mixed iterative refinement).
 long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok);
+// One FGMRES cycle (restart length m) in the multigrid precision: x ~ D_l^{-1} b.
+void approx_inverse(Ctx& c, int l, const double2* b, double2* x, int N);
+void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);
+// Throws MGMLMC_ETIMEOUT if a kernel with bounded waits recorded a timeout.
+void check_device_error(Ctx& c);
 
 // ---- setup (setup.cu)
 void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const int* nvec, int setup_iters,

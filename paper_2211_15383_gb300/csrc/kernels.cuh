@@ -98,11 +98,14 @@ size_t gauss_jordan_work_bytes(int n);
 // Hermitian eigenproblem of a small b x b matrix (cyclic Jacobi, one CTA):
 // H is overwritten; W receives eigenvectors (columns), lam eigenvalues.
 void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s);
-// BF16 real embedding of a complex n x n matrix for the tensor-core coarsest solve.
-void launch_embed_bf16(__nv_bfloat16* E, const double2* A, int n, cudaStream_t s);
-// Y[n][N] = Dinv * X with the BF16 embedding (tcgen05 tensor cores), X, Y FP32 complex.
+// BF16 real embedding [Re A | Im A] (n x 2n) of a complex FP32 n x n matrix for the
+// tensor-core coarsest solve.
+void launch_embed_bf16(__nv_bfloat16* E, const float2* A, int n, cudaStream_t s);
+bool tc_coarse_supported(int n);
+// Y[n][N] = A * X with the BF16 embedding E of A (tcgen05 tensor cores, FP32 accumulation);
+// X, Y FP32 complex [n][N].  *err set to 1 if a bounded wait gave up.
 void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N,
-                                void* scratch, cudaStream_t s);
+                                void* scratch, int* err, cudaStream_t s);
 size_t coarse_inverse_bf16_scratch(int n, int N);
 
 // ----------------------------------------------------------------- setup

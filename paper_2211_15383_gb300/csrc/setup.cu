@@ -58,6 +58,7 @@ void Ctx::release_all() {
     }
     owned.clear();
     ws.clear();
+    dev_err = nullptr;
     for (auto& L : lev) L = Level();
     U64 = nullptr;
     U32 = nullptr;
@@ -76,7 +77,7 @@ void Ctx::free_hierarchy() {
     for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) {
         Level& L = lev[l];
         dev_free(L.A64); dev_free(L.A32); dev_free(L.P64); dev_free(L.P32); dev_free(L.tv);
-        dev_free(L.Dinv64); dev_free(L.Dinv32);
+        dev_free(L.Dinv64); dev_free(L.Dinv32); dev_free(L.Dinv16);
         L = Level();
     }
     free_deflation();
@@ -206,6 +207,7 @@ __global__ void k_weighted_sum(double2* out, const double2* t, const double* a, 
 static void small_launch_check() { MG_LAUNCHED(); }
 
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);   // solver.cu
+constexpr int kBootstrapRounds = 2;
 
 // ------------------------------------------------------------------ hierarchy
 static void coarsest_inverse(Ctx& c) {
@@ -224,6 +226,10 @@ static void coarsest_inverse(Ctx& c) {
         if (!L.Dinv32) L.Dinv32 = c.alloc_n<float2>((size_t)n * n);
         launch_convert<float2, double2>(L.Dinv32, Dd, n * n, c.stream);
         launch_gauss_jordan<float2>(L.Dinv32, (int)n, work, c.stream);
+        if (tc_coarse_supported((int)n)) {
+            if (!L.Dinv16) L.Dinv16 = c.alloc_n<__nv_bfloat16>((size_t)n * 2 * n);
+            launch_embed_bf16(L.Dinv16, L.Dinv32, (int)n, c.stream);
+        }
     }
     int hs = 0;
     MG_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
@@ -291,21 +297,54 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
     }
     launch_materialize_wilson(c.lev[0].A64, c.U64, c.m0, c.Lx, c.Lt, c.stream);
     rebuild_from(c, 0);
-    for (int l = 0; l < nlev - 1; ++l) {
-        Level& L = c.lev[l];
-        for (int it = 0; it < setup_iters; ++it) {
+    if (setup_iters > 0) {
+        // Keep the start vectors: the test vectors are defined by exact inverse
+        // iteration from them.
+        std::vector<double2*> raw(nlev - 1);
+        for (int l = 0; l < nlev - 1; ++l) {
+            const Level& L = c.lev[l];
+            raw[l] = c.scratch<double2>("setup_raw" + std::to_string(l), (size_t)L.n * L.nvec);
+            MG_CUDA(cudaMemcpyAsync(raw[l], L.tv, sizeof(double2) * L.n * L.nvec, cudaMemcpyDeviceToDevice,
+                                    c.stream));
+        }
+        // Preconditioner bootstrap: a hierarchy built from random vectors is too weak
+        // for the near-critical solves of the inverse iteration, so first improve every
+        // level's vectors by a few rounds of approximate inverse iteration (one FGMRES
+        // cycle each).  This only shapes the preconditioner of the setup solves; the
+        // final test vectors come from the exact iteration below.
+        for (int round = 0; round < kBootstrapRounds; ++round)
+            for (int l = 0; l < nlev - 1; ++l) {
+                Level& L = c.lev[l];
+                const int nv = L.nvec;
+                double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
+                double2* X = c.scratch<double2>("setup_X", (size_t)L.n * nv);
+                double* nrm = c.scratch<double>("setup_nrm", nv);
+                launch_transpose(B, L.tv, nv, (int)L.n, c.stream);
+                approx_inverse(c, l, B, X, nv);
+                column_norms(c, nrm, X, L.n, nv);
+                launch_scale_rhs<double2, double2>(X, X, nrm, true, L.n, nv, c.stream);
+                launch_transpose(L.tv, X, L.n, nv, c.stream);
+                rebuild_from(c, l);
+            }
+        // Inverse iteration v <- D_l^{-1} v / ||.|| from the start vectors, level by
+        // level top-down, each solve to setup_tol.
+        for (int l = 0; l < nlev - 1; ++l) {
+            Level& L = c.lev[l];
             const int nv = L.nvec;
             double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
             double2* X = c.scratch<double2>("setup_X", (size_t)L.n * nv);
             double* nrm = c.scratch<double>("setup_nrm", nv);
-            launch_transpose(B, L.tv, nv, (int)L.n, c.stream);
-            int ok = 0;
-            solve(c, l, B, X, nv, setup_tol, &ok);
-            MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED,
-                       "set_hierarchy: inverse-iteration solve on level " + std::to_string(l + 1) + " did not converge");
-            column_norms(c, nrm, X, L.n, nv);
-            launch_scale_rhs<double2, double2>(X, X, nrm, true, L.n, nv, c.stream);
-            launch_transpose(L.tv, X, L.n, nv, c.stream);
+            launch_transpose(B, raw[l], nv, (int)L.n, c.stream);
+            for (int it = 0; it < setup_iters; ++it) {
+                int ok = 0;
+                solve(c, l, B, X, nv, setup_tol, &ok);
+                MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED,
+                           "set_hierarchy: inverse-iteration solve on level " + std::to_string(l + 1) +
+                               " did not converge");
+                column_norms(c, nrm, X, L.n, nv);
+                launch_scale_rhs<double2, double2>(B, X, nrm, true, L.n, nv, c.stream);
+            }
+            launch_transpose(L.tv, B, L.n, nv, c.stream);
             rebuild_from(c, l);
         }
     }

@@ -86,6 +86,17 @@ template <> void coarsest_apply<double2>(Ctx& c, double2* e, const double2* r, i
 }
 template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int N) {
     const Level& L = c.lev[c.L - 1];
+    if (L.Dinv16) {
+        // BF16 inverse on the tensor cores; algorithmic bytes: the BF16 matrix once + FP32 in/out
+        ProfScope ps(c, "Dinv.bf16", (double)L.n * 2 * L.n * 2 + 2.0 * L.n * N * 8, dinv_flops(L, N));
+        void* scr = c.scratch_bytes("tc_scratch", coarse_inverse_bf16_scratch((int)L.n, N));
+        if (!c.dev_err) {
+            c.dev_err = c.scratch<int>("dev_err", 1);
+            MG_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
+        }
+        launch_coarse_inverse_bf16(e, r, L.Dinv16, (int)L.n, N, scr, c.dev_err, c.stream);
+        return;
+    }
     ProfScope ps(c, "Dinv.f32", dinv_bytes(L, N, 8), dinv_flops(L, N));
     launch_gemm_nn<float2>(e, L.Dinv32, r, (int)L.n, (int)L.n, N, false, c.stream);
 }
@@ -288,7 +299,19 @@ long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, 
         apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
     }
     c.last_iters = it;
+    check_device_error(c);
     return it;
+}
+
+void check_device_error(Ctx& c) {
+    if (!c.dev_err) return;
+    int h = 0;
+    MG_CUDA(cudaMemcpyAsync(&h, c.dev_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (h) {
+        MG_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
+        throw Error(MGMLMC_ETIMEOUT, "a tensor-core kernel gave up waiting on an mbarrier (bounded wait)");
+    }
 }
 
 #define INST(C)                                                                                           \
@@ -304,4 +327,18 @@ INST(float2)
 
 namespace mg {
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N) { norms<double2>(c, out, x, n, N); }
+
+void approx_inverse(Ctx& c, int l, const double2* b, double2* x, int N) {
+    int ok = 0;
+    if (c.opt.mg_precision == 64) {
+        fgmres<double2>(c, l, b, x, N, 1e-14, c.opt.fgmres_restart, true, &ok, 1);
+        return;
+    }
+    const size_t nN = (size_t)c.lev[l].n * N;
+    float2* b32 = c.scratch<float2>("ai_b32", nN);
+    float2* x32 = c.scratch<float2>("ai_x32", nN);
+    launch_convert<float2, double2>(b32, b, (long long)nN, c.stream);
+    fgmres<float2>(c, l, b32, x32, N, 1e-6, c.opt.fgmres_restart, true, &ok, 1);
+    launch_convert<double2, float2>(x, x32, (long long)nN, c.stream);
+}
 }  // namespace mg

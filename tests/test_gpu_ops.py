@@ -105,3 +105,26 @@ def test_state_errors(pkg):
         with pytest.raises(pkg.MgmlmcError) as e:
             ctx.set_gauge(bad)
         assert e.value.code == -7
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 37, 64, 130, 256])
+def test_tensor_core_coarsest_solve(pkg, nrhs):
+    # mixed mode: the coarsest inverse is rounded to BF16 and applied with tcgen05 MMAs
+    # (FP32 accumulation); compare with the exact solve at BF16 accuracy
+    import inputs
+    w = inputs.workload("schwinger-16x16")
+    theta, sv = w.gauge(), w.start_vectors()
+    H = ohier.build_hierarchy(theta, w.m0, w.agg, w.nvec, sv, 0)
+    n = H.D[-1].shape[0]
+    assert n % 128 == 0
+    rng = np.random.default_rng(nrhs)
+    b = rand_complex(rng, (nrhs, n))
+    ref = np.linalg.solve(H.D[-1].toarray(), b.T).T
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, 0, mg_precision=32) as ctx:
+        z = ctx.apply(pkg.OP_DINV_C, 2, b, n)
+        z2 = ctx.apply(pkg.OP_DINV_C, 2, b, n)
+    assert np.array_equal(z, z2)                                   # deterministic
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) < 2e-2
+    # per rhs as well (no column is left unwritten or mixed up)
+    err = np.linalg.norm(z - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() < 3e-2
