@@ -85,6 +85,7 @@ SIGNATURES = [
     ("mgmlmc_profile", C.c_int, [_P, C.c_int, C.c_int]),
     ("mgmlmc_profile_report", C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("mgmlmc_fma_peak", C.c_int, [C.c_int, _D]),
+    ("mgmlmc_coarse_inverse_noalloc", C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 _lib = None
@@ -313,6 +314,11 @@ class Context:
         buf = C.create_string_buffer(need.value + 1)
         self._check(self.lib.mgmlmc_profile_report(self.h, buf, need.value + 1, C.byref(need)))
         return json.loads(buf.value.decode())
+
+    def coarse_inverse_noalloc(self, nrhs: int, x_ptr: int, y_ptr: int, stream: int = 0):
+        """y = D_L^{-1} x for caller-owned device buffers (FP32 complex [n_L][nrhs]); allocates nothing."""
+        self._check(self.lib.mgmlmc_coarse_inverse_noalloc(self.h, int(nrhs), C.c_void_p(x_ptr), C.c_void_p(y_ptr),
+                                                           C.c_void_p(stream)))
 
     def get_test_vectors(self, level: int, nvec: int):
         n = self.level_info(level)[3]

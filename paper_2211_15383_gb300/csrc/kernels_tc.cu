@@ -304,3 +304,85 @@ void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16*
 }
 
 }  // namespace mg
+
+// ------------------------------------------------------------------------------
+// Allocation-free variant of the coarsest solve.  The packed operand B' lives in
+// a file-scope device array instead of context work space, so the call itself
+// never allocates.  Its address is looked up once per device with
+// cudaGetSymbolAddress (host code must not use the symbol as a device pointer).
+#include <mutex>
+
+#include "context.h"
+
+namespace mg {
+namespace tc {
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB: B' for n_L * nrhs <= 2^20
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ int g_noalloc_err;
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[kMaxDevices];
+static int* g_noalloc_err_ptr[kMaxDevices];
+
+// Device addresses of the static scratch and error flag for the current device.
+static void noalloc_symbols(void** scratch, int** err) {
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    MG_REQUIRE(dev >= 0 && dev < kMaxDevices, MGMLMC_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        void* e = nullptr;
+        MG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        MG_CUDA(cudaGetSymbolAddress(&e, g_noalloc_err));
+        g_noalloc_err_ptr[dev] = reinterpret_cast<int*>(e);
+        g_noalloc_ptr[dev] = p;
+    }
+    *scratch = g_noalloc_ptr[dev];
+    *err = g_noalloc_err_ptr[dev];
+}
+}  // namespace tc
+}  // namespace mg
+
+extern "C" int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* h, int nrhs, const float* x, float* y, void* stream) {
+    if (!h) return MGMLMC_EINVAL;
+    mg::Ctx& c = h->c;
+    c.err.clear();
+    try {
+        MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "coarse_inverse_noalloc: no hierarchy");
+        const mg::Level& L = c.lev[c.L - 1];
+        MG_REQUIRE(L.Dinv16 != nullptr, MGMLMC_ESTATE,
+                   "coarse_inverse_noalloc: needs mg_precision = 32 and a coarsest level with n_L % 128 == 0");
+        MG_REQUIRE(x && y && x != y, MGMLMC_EINVAL, "coarse_inverse_noalloc: x, y must be distinct device pointers");
+        MG_REQUIRE(nrhs >= 32 && nrhs % 32 == 0, MGMLMC_EINVAL, "coarse_inverse_noalloc: nrhs must be a multiple of 32");
+        const int n = (int)L.n;
+        const size_t need = (size_t)2 * nrhs * 2 * n * sizeof(__nv_bfloat16);
+        MG_REQUIRE(need <= mg::tc::kNoAllocScratchBytes, MGMLMC_EINVAL,
+                   "coarse_inverse_noalloc: n_L * nrhs above 2^20 (static scratch of 8 MiB)");
+        void* scratch = nullptr;
+        int* err = nullptr;
+        mg::tc::noalloc_symbols(&scratch, &err);
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        const int Ncols = 2 * nrhs;
+        MG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        {
+            dim3 g((Ncols / 2 + 31) / 32, (n + 31) / 32);
+            mg::tc::k_pack_bt<<<g, dim3(32, 8), 0, s>>>(reinterpret_cast<__nv_bfloat16*>(scratch),
+                                                       reinterpret_cast<const float2*>(x), n, nrhs, Ncols);
+            MG_LAUNCHED();
+        }
+        const __nv_bfloat16* Bt = reinterpret_cast<const __nv_bfloat16*>(scratch);
+        if (Ncols % 256 == 0) mg::launch_tc<256>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
+        else if (Ncols % 128 == 0) mg::launch_tc<128>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
+        else mg::launch_tc<64>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
+        int herr = 0;
+        MG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        MG_REQUIRE(herr == 0, MGMLMC_ETIMEOUT, "coarse_inverse_noalloc: a bounded mbarrier wait gave up");
+    } catch (const mg::Error& e) {
+        c.err = e.what();
+        return e.code;
+    }
+    return MGMLMC_OK;
+}
