@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--ttt-tol", type=float, default=1e-2,
                     help="relative error of the time-to-trace run (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--block-rhs", type=int, default=0,
+                    help="override the workload's right-hand sides per block (smaller ncu captures)")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="mark the timed regions with NVTX ranges timed_f64 / timed_mixed / timed_e2e")
     return ap.parse_args()
 
 
@@ -168,23 +172,34 @@ def ncu_traffic(kclass):
 
 
 def roofline(report, peaks, fp64_peak, fp32_peak):
-    """Roofline of the kernel class with the largest device time."""
+    """Roofline of the kernel class with the largest device time.
+
+    The bound follows the class's precision and arithmetic intensity: BF16 classes
+    run on the tensor cores (peak: measured sustained cuBLAS BF16, the kernel runs
+    inside a long step); FP64 and FP32 classes are ALU-bound when their
+    intensity exceeds the ridge point (FMA peak / HBM bandwidth), else HBM-bound.
+    """
     cls, st = max(report.items(), key=lambda kv: kv[1]["ms"])
     per_launch_s = st["ms"] * 1e-3 / st["count"]
     prec = cls.split(".")[-1]
     bytes_l = st["bytes"] / st["count"]
     flops_l = st["flops"] / st["count"]
-    if prec == "f64":
-        # FP64 kernels on GB300 are bound by the FP64 pipe (~1/64 of the FP32 rate),
-        # far below their HBM time: ALU roofline against the measured FMA peak.
+    hbm = peaks["hbm_gbs"] * 1e9
+    if prec == "bf16":
+        peak = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
         ach = flops_l / per_launch_s / 1e12
-        peak = fp64_peak / 1e12
-        out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-               "peak_source": "measured FP64 FMA throughput (mgmlmc_fma_peak)"}
+        out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": f"{peaks['source']} cuBLAS BF16 sustained"}
     else:
-        ach = bytes_l / per_launch_s / 1e9
-        out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-               "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+        alu = fp64_peak if prec == "f64" else fp32_peak
+        if flops_l / max(bytes_l, 1.0) > alu / hbm:
+            ach = flops_l / per_launch_s / 1e12
+            out = {"bound": "alu", "achieved": ach, "peak": alu / 1e12, "unit": "TFLOP/s", "frac": ach * 1e12 / alu,
+                   "peak_source": f"measured {prec.upper()} FMA throughput (mgmlmc_fma_peak)"}
+        else:
+            ach = bytes_l / per_launch_s / 1e9
+            out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
     out.update({"kernel": cls, "launches": st["count"], "avg_launch_us": per_launch_s * 1e6,
                 "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                 "traffic": ncu_traffic(cls), "share_of_profiled_time":
@@ -221,15 +236,19 @@ def run_steps(ctx, w, nterms, first_step, K, seed):
             ctx.estimate_level(t, (first_step + k) * w.nrhs, w.nrhs, seed, samples=False)
 
 
-def timed_region(torch, ws, fn):
+def timed_region(torch, ws, fn, name=None):
     barrier(ws)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if name:
+        torch.cuda.nvtx.range_push(name)
     e0.record(s)
     fn()
     e1.record(s)
     torch.cuda.synchronize()
+    if name:
+        torch.cuda.nvtx.range_pop()
     barrier(ws)
     return max_over_ranks(e0.elapsed_time(e1) * 1e-3, ws)
 
@@ -242,6 +261,9 @@ def gpu_arm(args, rank, ws, local):
     import paper_2211_15383_gb300 as pkg
 
     w = inputs.workload(args.workload)
+    if args.block_rhs:
+        import dataclasses
+        w = dataclasses.replace(w, nrhs=args.block_rhs)
     peaks = measured_peaks()
     fp64_peak = pkg.fma_peak(64)
     fp32_peak = pkg.fma_peak(32)
@@ -253,7 +275,8 @@ def gpu_arm(args, rank, ws, local):
     ctx.profile(True, reset=True)
     clk = Clocks(local)
     clk.start()
-    sec = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W, K, seed))
+    tag = "timed_f64" if args.precision == 64 else "timed_mixed"
+    sec = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W, K, seed), tag if args.nvtx else None)
     clocks = clk.stop()
     ctx.profile(False)
     report = ctx.profile_report()
@@ -302,7 +325,7 @@ def gpu_arm(args, rank, ws, local):
                     o = outs[t].numpy().view(np.complex128).reshape(-1)
                     ctx.estimate_level_probes(t, probes[k][t].numpy(), out=o)
 
-        sec_e2e = timed_region(torch, ws, e2e_steps)
+        sec_e2e = timed_region(torch, ws, e2e_steps, "timed_e2e" if args.nvtx else None)
         out["e2e"] = {"value": samples / sec_e2e, "unit": UNIT,
                       "h2d_bytes_per_step": int(sum(w.nrhs * n for n in n_of)),
                       "d2h_bytes_per_step": int(nterms * w.nrhs * 16),
@@ -328,7 +351,8 @@ def gpu_arm(args, rank, ws, local):
                 for g, r in zip(got, ref)]
         run_steps(mctx, w, nterms, 0, W, seed)
         mctx.profile(True, reset=True)
-        msec = timed_region(torch, ws, lambda: run_steps(mctx, w, nterms, W, K, seed))
+        msec = timed_region(torch, ws, lambda: run_steps(mctx, w, nterms, W, K, seed),
+                            "timed_mixed" if args.nvtx else None)
         mctx.profile(False)
         mrep = mctx.profile_report()
         mrep.pop("__launches__", None)

@@ -65,6 +65,9 @@ template <typename C>
 void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N,
                           int mode, double2* part, int groups, cudaStream_t s);
 int stencil_groups(int nsites, int N);
+// Row groups (grid.y) the block-stencil launcher expects for (nsites, d, N); the MR
+// partials array holds groups * 2 * N values.
+int block_stencil_groups(int nsites, int d, int N);
 // Restriction xc = P^H x and prolongation x (+)= P xc for aggregates ax x at,
 // P stored [fine site][d][nvec]; coarse dof (S, spin block, j).
 template <typename C>
@@ -111,9 +114,11 @@ size_t coarse_inverse_bf16_scratch(int n, int N);
 // ----------------------------------------------------------------- setup
 // Block-stencil form of the fine Wilson operator: A[site][5][2][2].
 void launch_materialize_wilson(double2* A, const double2* U, double m0, int lx, int lt, cudaStream_t s);
-// Galerkin coarse blocks Ac[S][5][dc][dc] = P^H D P, D given as block stencil Af (d x d).
+// Galerkin coarse blocks Ac[S][5][dc][dc] = P^H D P, D given as block stencil Af (d x d);
+// T: scratch of galerkin_scratch_count(...) complex values.
 void launch_galerkin(double2* Ac, const double2* Af, const double2* P, int lx, int lt, int d, int ax,
-                     int at, int nvec, cudaStream_t s);
+                     int at, int nvec, double2* T, cudaStream_t s);
+size_t galerkin_scratch_count(int lx, int lt, int d, int nvec);
 // P[site][d][nvec] from test vectors tv[nvec][n]: MGS per (aggregate, spin block).
 // status[0] set to 1 if a block is rank deficient.
 void launch_build_prolongator(double2* P, const double2* tv, int lx, int lt, int d, int ax, int at,

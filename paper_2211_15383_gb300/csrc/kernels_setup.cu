@@ -39,12 +39,40 @@ void launch_materialize_wilson(double2* A, const double2* U, double m0, int lx, 
     MG_LAUNCHED();
 }
 
-// Coarse block Ac[S][dir][o][o'] = sum over fine sites x of aggregate S and
-// fine hops x -> y that leave S through side dir (dir 0: stay inside) of
-// conj(P[x][a][j]) Af[x][fdir][a][b] P[y][b][j'], o = (s, j), o' = (s', j'),
-// a in spin block s, b in spin block s'.  One thread per output entry.
-__global__ void k_galerkin(double2* Ac, const double2* Af, const double2* P, int lx, int lt, int d, int ax, int at,
-                           int nvec) {
+// Galerkin coarse operator D_{l+1} = P^H D_l P in two stages.
+// Stage 1: T[x][fdir][a][o'] = sum_{b in spin block s'} Af[x][fdir][a][b] P[y][b][j'],
+//          y the fine neighbour of x in direction fdir, o' = (s', j').
+// Stage 2: Ac[S][dir][o][o'] = sum over fine sites x of aggregate S and fine hops x -> y
+//          that leave S through side dir (dir 0: stay inside) of
+//          sum_{a in spin block s} conj(P[x][a][j]) T[x][fdir][a][o'],  o = (s, j).
+__device__ __forceinline__ int fine_nbr(int xx, int t, int fdir, int lx, int lt) {
+    switch (fdir) {
+        case 1: return (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+        case 2: return (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+        case 3: return xx + lx * (t + 1 == lt ? 0 : t + 1);
+        case 4: return xx + lx * (t == 0 ? lt - 1 : t - 1);
+        default: return xx + lx * t;
+    }
+}
+
+__global__ void k_galerkin_t(double2* T, const double2* Af, const double2* P, int lx, int lt, int d, int nvec) {
+    const int dc = 2 * nvec, hd = d / 2;
+    const long long total = (long long)lx * lt * 5 * d * dc;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int op = (int)(e % dc), a = (int)((e / dc) % d), fdir = (int)((e / ((long long)dc * d)) % 5);
+    const int site = (int)(e / (5LL * d * dc));
+    const int xx = site % lx, t = site / lx;
+    const int ysite = fine_nbr(xx, t, fdir, lx, lt);
+    const int sp = op / nvec, jp = op % nvec;
+    const double2* Ab = Af + ((long long)site * 5 + fdir) * d * d + (long long)a * d;
+    double2 acc = make_double2(0, 0);
+    for (int b = sp * hd; b < (sp + 1) * hd; ++b) cfma(acc, Ab[b], P[((long long)ysite * d + b) * nvec + jp]);
+    T[e] = acc;
+}
+
+__global__ void k_galerkin_c(double2* Ac, const double2* T, const double2* P, int lx, int lt, int d, int ax, int at,
+                             int nvec) {
     const int dc = 2 * nvec, hd = d / 2;
     const int cx = lx / ax, ct = lt / at;
     const long long total = (long long)cx * ct * 5 * dc * dc;
@@ -52,40 +80,39 @@ __global__ void k_galerkin(double2* Ac, const double2* Af, const double2* P, int
     if (e >= total) return;
     const int op = (int)(e % dc), o = (int)((e / dc) % dc), dir = (int)((e / (dc * dc)) % 5);
     const int S = (int)(e / (5LL * dc * dc));
-    const int X = S % cx, T = S / cx;
-    const int s = o / nvec, jj = o % nvec, sp = op / nvec, jp = op % nvec;
+    const int X = S % cx, TT = S / cx;
+    const int s = o / nvec, jj = o % nvec;
     double2 acc = make_double2(0, 0);
     for (int it = 0; it < at; ++it)
         for (int ix = 0; ix < ax; ++ix) {
-            const int xx = X * ax + ix, t = T * at + it;
-            const int site = xx + lx * t;
+            const int site = (X * ax + ix) + lx * (TT * at + it);
             for (int fdir = 0; fdir < 5; ++fdir) {
-                int cdir, ysite;
+                int cdir;
                 switch (fdir) {
-                    case 1: cdir = (ix == ax - 1) ? 1 : 0; ysite = (xx + 1 == lx ? 0 : xx + 1) + lx * t; break;
-                    case 2: cdir = (ix == 0) ? 2 : 0; ysite = (xx == 0 ? lx - 1 : xx - 1) + lx * t; break;
-                    case 3: cdir = (it == at - 1) ? 3 : 0; ysite = xx + lx * (t + 1 == lt ? 0 : t + 1); break;
-                    case 4: cdir = (it == 0) ? 4 : 0; ysite = xx + lx * (t == 0 ? lt - 1 : t - 1); break;
-                    default: cdir = 0; ysite = site;
+                    case 1: cdir = (ix == ax - 1) ? 1 : 0; break;
+                    case 2: cdir = (ix == 0) ? 2 : 0; break;
+                    case 3: cdir = (it == at - 1) ? 3 : 0; break;
+                    case 4: cdir = (it == 0) ? 4 : 0; break;
+                    default: cdir = 0;
                 }
                 if (cdir != dir) continue;
-                const double2* Ab = Af + ((long long)site * 5 + fdir) * d * d;
-                for (int a = s * hd; a < (s + 1) * hd; ++a) {
-                    const double2 pa = P[((long long)site * d + a) * nvec + jj];
-                    double2 row = make_double2(0, 0);
-                    for (int b = sp * hd; b < (sp + 1) * hd; ++b)
-                        cfma(row, Ab[a * d + b], P[((long long)ysite * d + b) * nvec + jp]);
-                    cfmac(acc, pa, row);
-                }
+                const double2* Tr = T + (((long long)site * 5 + fdir) * d) * dc + op;
+                for (int a = s * hd; a < (s + 1) * hd; ++a)
+                    cfmac(acc, P[((long long)site * d + a) * nvec + jj], Tr[(long long)a * dc]);
             }
         }
     Ac[e] = acc;
 }
 
+size_t galerkin_scratch_count(int lx, int lt, int d, int nvec) { return (size_t)lx * lt * 5 * d * 2 * nvec; }
+
 void launch_galerkin(double2* Ac, const double2* Af, const double2* P, int lx, int lt, int d, int ax, int at,
-                     int nvec, cudaStream_t s) {
+                     int nvec, double2* T, cudaStream_t s) {
+    const long long t1 = (long long)lx * lt * 5 * d * 2 * nvec;
+    k_galerkin_t<<<(unsigned)((t1 + 127) / 128), 128, 0, s>>>(T, Af, P, lx, lt, d, nvec);
+    MG_LAUNCHED();
     const long long total = (long long)(lx / ax) * (lt / at) * 5 * (2 * nvec) * (2 * nvec);
-    k_galerkin<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ac, Af, P, lx, lt, d, ax, at, nvec);
+    k_galerkin_c<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ac, T, P, lx, lt, d, ax, at, nvec);
     MG_LAUNCHED();
 }
 

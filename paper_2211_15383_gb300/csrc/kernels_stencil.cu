@@ -165,6 +165,66 @@ __global__ void __launch_bounds__(256) k_block_stencil(C* __restrict__ y, const 
     }
 }
 
+// Site-per-thread-row variant for compile-time d: block = 128 rhs, each thread
+// computes all d outputs of one site for its rhs, so every input value loaded
+// is used d times.  The blocks are staged transposed, At[dir][b][c], so the
+// inner loop over output rows reads consecutive shared-memory words (broadcast
+// to the whole warp).
+template <typename C, int D, int MODE>
+__global__ void __launch_bounds__(128) k_block_stencil_d(C* __restrict__ y, const C* __restrict__ x,
+                                                         const C* __restrict__ b, const C* __restrict__ A, int lx,
+                                                         int lt, int N, double2* __restrict__ part) {
+    using R = re_t<C>;
+    __shared__ C At[5 * D * D];
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int V = lx * lt;
+    C dyx = czero<C>();
+    R dyy = 0;
+    for (int site = blockIdx.y; site < V; site += gridDim.y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 5 * D * D; e += 128) {
+            const int dir = e / (D * D), r = e % (D * D), c = r / D, bb = r % D;
+            At[(dir * D + bb) * D + c] = A[(long long)site * 5 * D * D + e];
+        }
+        __syncthreads();
+        if (j < N) {
+            C acc[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] = czero<C>();
+#pragma unroll 1
+            for (int dir = 0; dir < 5; ++dir) {
+                const int nb = nbr_site(site, dir, lx, lt);
+                const C* xn = x + (long long)nb * D * N + j;
+                const C* Ad = At + dir * D * D;
+#pragma unroll 4
+                for (int bc = 0; bc < D; ++bc) {
+                    const C xv = xn[(long long)bc * N];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) cfma(acc[c], Ad[bc * D + c], xv);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const long long idx = ((long long)site * D + c) * N + j;
+                C o = acc[c];
+                if (MODE == 1) o = csub(b[idx], o);
+                y[idx] = o;
+                if (MODE == 2) {
+                    cfmac(dyx, o, x[idx]);
+                    dyy = fma(o.x, o.x, fma(o.y, o.y, dyy));
+                }
+            }
+        }
+    }
+    if (MODE == 2) {
+        // per-rhs partials: one thread per rhs, no cross-thread reduction needed
+        if (j < N) {
+            part[((long long)blockIdx.y * 2 + 0) * N + j] = to_d(dyx);
+            part[((long long)blockIdx.y * 2 + 1) * N + j] = make_double2((double)dyy, 0.0);
+        }
+    }
+}
+
 // xc[S][o] = sum_{site in S} sum_{a in spin block s(o)} conj(P[site][a][j(o)]) x[site][a]
 template <typename C>
 __global__ void k_restrict(C* __restrict__ xc, const C* __restrict__ x, const C* __restrict__ P, int lx, int lt,
@@ -283,10 +343,36 @@ static void bs_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt
     MG_LAUNCHED();
 }
 
+template <typename C, int D>
+static void bsd_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt, int N, int mode, double2* part,
+                         int groups, cudaStream_t s) {
+    dim3 g((N + 127) / 128, groups);
+    switch (mode) {
+        case 0: k_block_stencil_d<C, D, 0><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 1: k_block_stencil_d<C, D, 1><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        default: k_block_stencil_d<C, D, 2><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+    }
+    MG_LAUNCHED();
+}
+
+int block_stencil_groups(int nsites, int d, int N) {
+    if (d == 8 || d == 16) {
+        const int tiles = (N + 127) / 128;
+        int want = 16 * kNumSM / tiles;
+        if (want < 1) want = 1;
+        return nsites < want ? nsites : want;
+    }
+    int want = 8 * kNumSM / rhs_tiles(N);
+    if (want < 1) want = 1;
+    return nsites < want ? nsites : want;
+}
+
 template <typename C>
 void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N, int mode,
                           double2* part, int groups, cudaStream_t s) {
     MG_REQUIRE(d >= 2 && d <= 64, MGMLMC_EINVAL, "block stencil: 2 <= d <= 64");
+    if (d == 16) return bsd_dispatch<C, 16>(y, x, b, A, lx, lt, N, mode, part, groups, s);
+    if (d == 8) return bsd_dispatch<C, 8>(y, x, b, A, lx, lt, N, mode, part, groups, s);
     if (d <= 8) bs_dispatch<C, 1>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
     else if (d <= 16) bs_dispatch<C, 2>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
     else if (d <= 32) bs_dispatch<C, 4>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);

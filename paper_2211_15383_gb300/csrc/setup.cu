@@ -250,7 +250,8 @@ static void rebuild_from(Ctx& c, int l0) {
         MG_REQUIRE(hs == 0, MGMLMC_EINVAL,
                    "set_hierarchy: rank-deficient test vectors on an aggregate of level " + std::to_string(l + 1));
         launch_convert<float2, double2>(L.P32, L.P64, L.n * L.nvec, c.stream);
-        launch_galerkin(Lc.A64, L.A64, L.P64, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, c.stream);
+        double2* T = c.scratch<double2>("galerkin_T", galerkin_scratch_count(L.lx, L.lt, L.d, L.nvec));
+        launch_galerkin(Lc.A64, L.A64, L.P64, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, T, c.stream);
         launch_convert<float2, double2>(Lc.A32, Lc.A64, (long long)Lc.nsites * 5 * Lc.d * Lc.d, c.stream);
     }
     coarsest_inverse(c);
