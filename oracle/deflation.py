@@ -62,3 +62,35 @@ def coarsest_deflation(D, g5: np.ndarray, k: int) -> Deflation:
     """Deflation of the traced operator D^{-1} by D's k smallest triplets."""
     sigma, U, V, lam = smallest_triplets(D, g5, k)
     return Deflation(L=V, R=U, a=1.0 / sigma, lam=lam)
+
+
+def hermitian_difference_operator(hier, term) -> np.ndarray:
+    """J = M Gamma5^a = Q_a^{-1} - P Q_b^{-1} P^H for the term (a, b) (Sect. 4.2).
+
+    M = D_a^{-1} - P D_b^{-1} P^H with P = P_{a->b}; Gamma5^a P = P Gamma5^b and
+    Q_l = Gamma5^l D_l Hermitian make J Hermitian.  Dense; small lattices only.
+    """
+    a, b = term
+    g_a, g_b = hier.g5[a - 1], hier.g5[b - 1]
+    Qa = g_a[:, None] * hier.D[a - 1].toarray()
+    Qb = g_b[:, None] * hier.D[b - 1].toarray()
+    P = hier.prolongator(a, b).toarray()
+    J = np.linalg.inv(Qa) - P @ np.linalg.inv(Qb) @ P.conj().T
+    return 0.5 * (J + J.conj().T)
+
+
+def difference_deflation(hier, term, k: int) -> Deflation:
+    """Exact deflation of the difference-level operator M by its k largest
+    singular triplets, from the eigenpairs of J (Eq. hermitian_diff_lev_op):
+    J = X Lambda X^H gives M = U S V^H with U = X sign(Lambda), S = |Lambda|,
+    V = Gamma5^a X.  For the traced operator A = M: L = U, R = V, a = S.
+    Ordered by decreasing |lambda|; dense Hermitian eigensolver (numpy eigh).
+    """
+    J = hermitian_difference_operator(hier, term)
+    lam, X = np.linalg.eigh(J)
+    order = np.argsort(-np.abs(lam), kind="stable")[:k]
+    lam, X = lam[order], X[:, order]
+    g = hier.g5[term[0] - 1]
+    U = X * np.sign(lam)[None, :]
+    V = g[:, None] * X
+    return Deflation(L=U, R=V, a=np.abs(lam), lam=lam)

@@ -52,3 +52,50 @@ def test_deflation_lowers_variance():
     v0 = estimator.z2_variance(Dinv)
     v1 = estimator.z2_variance(estimator.deflated_operator(Dinv, deflation.coarsest_deflation(D, g5, 8)))
     assert v1 < v0
+
+
+def _three_level(seed=31):
+    from oracle import hierarchy
+    th = inputs.metropolis_u1(8, 8, 2.0, 10, seed)
+    sv = [inputs.start_vectors(seed, 1, 128, 2), inputs.start_vectors(seed, 2, 64, 2)]
+    return hierarchy.build_hierarchy(th, 0.05, ((2, 2), (2, 2)), (2, 2), sv, 1)
+
+
+def test_difference_operator_hermitian_and_svd():
+    # J = M Gamma5 is Hermitian and |eig(J)| are the singular values of M (Sect. 4.2)
+    H = _three_level()
+    for term in [(1, 2), (2, 3), (1, 3)]:
+        J = deflation.hermitian_difference_operator(H, term)
+        g = H.g5[term[0] - 1]
+        M = estimator.term_operator(H, term)
+        assert np.abs(M * g[None, :] - J).max() < 1e-11 * np.abs(J).max()
+        sv = np.sort(np.linalg.svd(M, compute_uv=False))[::-1]
+        ev = np.sort(np.abs(np.linalg.eigvalsh(J)))[::-1]
+        assert np.abs(sv - ev).max() < 1e-10 * sv[0]
+
+
+def test_difference_deflation_triplets_and_trace():
+    H = _three_level()
+    term = (1, 2)
+    M = estimator.term_operator(H, term)
+    k = 12
+    d = deflation.difference_deflation(H, term, k)
+    # M R = L diag(a)  (M V = U S), and the deflated trace term equals tr(U S V^H)
+    assert np.abs(M @ d.R - d.L * d.a[None, :]).max() < 1e-10 * d.a.max()
+    sv = np.sort(np.linalg.svd(M, compute_uv=False))[::-1][:k]
+    assert np.abs(np.sort(d.a)[::-1] - sv).max() < 1e-10 * sv[0]
+    low = (d.L * d.a[None, :]) @ d.R.conj().T
+    assert abs(d.trace_term() - np.trace(low)) < 1e-10 * max(1.0, abs(np.trace(low)))
+    # deflation removes the largest singular values: the Frobenius norm drops accordingly
+    rest = M - low
+    assert abs(np.linalg.norm(rest) ** 2 - (np.linalg.norm(M) ** 2 - np.sum(d.a ** 2))) < 1e-8 * np.linalg.norm(M) ** 2
+
+
+def test_full_difference_deflation_is_exact():
+    H = _three_level()
+    term = (2, 3)
+    n = H.D[1].shape[0]
+    d = deflation.difference_deflation(H, term, n)
+    M = estimator.term_operator(H, term)
+    assert np.abs(estimator.deflated_operator(M, d)).max() < 1e-10 * np.abs(M).max()
+    assert abs(d.trace_term() - np.trace(M)) < 1e-10 * max(1.0, abs(np.trace(M)))

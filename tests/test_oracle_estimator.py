@@ -130,3 +130,18 @@ def test_mlmc_allocation_and_stopping():
     new = estimator.mlmc_allocation([1.0, 1.0], [1.0, 1.0], [10, 10], 1e-3)
     assert list(new) == [20, 20]
     del rng
+
+
+def test_brute_force_deflated_difference_term():
+    # all 2^16 Z2 vectors on a 2x4 lattice: deflated difference samples average to
+    # tr(M) - tr(L a R^H), and adding the deflated trace term gives tr(M) exactly
+    H = build(2, 4, 0.1, ((1, 2),), (1,))
+    solvers = estimator.DirectSolvers(H)
+    term = (1, 2)
+    d = deflation.difference_deflation(H, term, 3)
+    X = all_z2(H.D[0].shape[0])
+    s = estimator.term_samples(H, term, X, solvers, d)
+    M = estimator.term_operator(H, term)
+    assert abs(s.mean() + d.trace_term() - np.trace(M)) < 1e-11 * max(1.0, abs(np.trace(M)))
+    var_pop = float(np.mean(np.abs(s - s.mean()) ** 2))
+    assert abs(var_pop - estimator.z2_variance(estimator.deflated_operator(M, d))) < 1e-9 * max(1.0, var_pop)
