@@ -139,7 +139,8 @@ int mgmlmc_set_hierarchy(mgmlmc_ctx* ctx, int nlevels, const int* agg_x, const i
                          const double* const* start_vectors);
 
 /* Terms of the telescoping sum (Eq. mgmlmc).  nskip levels listed in skip
- * (2..L-1) are left out of the sum, giving Eq. skip_level for skip = {2}:
+ * (2..L) are left out of the sum, giving Eq. skip_level for skip = {2}, and
+ * plain (deflated) Hutchinson on D_1 (Sect. 2) for skip = {2..L}:
  * tr(D^{-1}) = tr(D_1^{-1} - P_1 P_2 D_3^{-1} P_2^H P_1^H) + ... .  nskip = 0
  * restores the plain sum.  Term t (0-based) then has fine level
  * term_level[t] and coarse level term_level[t+1] (none for the last term). */
@@ -159,6 +160,43 @@ int mgmlmc_compute_deflation(mgmlmc_ctx* ctx, int k, double tol, int max_iters);
  * complex, tau (2 doubles).  Any pointer may be NULL. */
 int mgmlmc_get_deflation(mgmlmc_ctx* ctx, double* lambda, double* sigma, double* U,
                          double* V, double* tau);
+
+/* Exact deflation of term t (0-based).  For the last (coarsest) term this is
+ * mgmlmc_compute_deflation.  For a difference term with fine level a and coarse
+ * level b (Sect. 4.2, exact deflation on difference levels): the k largest
+ * singular triplets of M = D_a^{-1} - P D_b^{-1} P^H (P = P_a ... P_{b-1}) from the
+ * eigenpairs of the Hermitian J = M Gamma5^a = Q_a^{-1} - P Q_b^{-1} P^H,
+ * J = X Lambda X^H -> U = X sign(Lambda), S = |Lambda|, V = Gamma5^a X (Eq.
+ * hermitian_diff_lev_op), by subspace iteration on J (two FP64-accurate solves
+ * per application) with Rayleigh-Ritz until ||J x - lambda x|| <= tol |lambda|
+ * for the k wanted pairs (Sect. 4.3 uses 1e-9), at most max_iters iterations.
+ * The term's samples then subtract x^H U S V^H x and the estimate adds
+ * tr(U S V^H) = sum_i lambda_i x_i^H Gamma5 x_i.  k = 0 removes it.  A later
+ * mgmlmc_set_terms that changes the term's coarse level disables it. */
+int mgmlmc_compute_term_deflation(mgmlmc_ctx* ctx, int term, int k, double tol, int max_iters);
+
+/* Inexact deflation of term t (Sect. 3.2/4.3: loosely converged vectors, the
+ * paper uses eigensolver tolerance 1e-1 and inner solves at 1e-3): the same
+ * eigensolver as mgmlmc_compute_term_deflation run to eig_tol with its solves at
+ * inner_tol gives approximate vectors V (Gamma5 X); the term is then deflated by
+ * the orthogonal projector V V^H with the deflated part computed from V by k
+ * extra solves at opt.solve_tol ("the computation of tr(D^{-1} Pi) requires k
+ * extra inversions"): samples subtract x^H (A V) V^H x, the estimate adds
+ * tr(V^H A V), A the term's traced operator.  Unbiased for any V. */
+int mgmlmc_compute_term_deflation_inexact(mgmlmc_ctx* ctx, int term, int k, double eig_tol, double inner_tol,
+                                          int max_iters);
+
+/* Deflation of term t by caller-supplied vectors V (host, [k][n_a] complex; the
+ * projector V V^H is orthogonal when V has orthonormal columns): the library
+ * computes A V with k FP64-accurate solves, as in the inexact deflation. */
+int mgmlmc_set_term_deflation_vectors(mgmlmc_ctx* ctx, int term, int k, const double* V);
+
+/* Host copies of term t's deflation: *k, lambda[k] (eigenvalues of the Hermitian
+ * operator), the traced operator's left vectors L and right vectors R as [k][n_a]
+ * complex (L = V, R = U for the coarsest term; L = U, R = V for a difference
+ * term), tau (2 doubles) = its deflated trace part.  Pointers may be NULL. */
+int mgmlmc_get_term_deflation(mgmlmc_ctx* ctx, int term, int* k, double* lambda, double* L, double* R,
+                              double* tau);
 
 /* nsamples Hutchinson samples of term t (0-based; Sect. 3.2):
  *   s_j = x_j^H D_a^{-1} x_j - (P^H x_j)^H D_b^{-1} (P^H x_j)   (difference term)

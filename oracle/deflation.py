@@ -94,3 +94,22 @@ def difference_deflation(hier, term, k: int) -> Deflation:
     U = X * np.sign(lam)[None, :]
     V = g[:, None] * X
     return Deflation(L=U, R=V, a=np.abs(lam), lam=lam)
+
+
+def vector_deflation(hier, term, V: np.ndarray, solvers=None) -> Deflation:
+    """Deflation of a term by given vectors V (n_a x k): the orthogonal projector
+    V V^H (Sect. 2's Pi, Sect. 3.2's inexact deflation with approximate vectors),
+    whose deflated part A V V^H needs the k extra applications A V of the traced
+    operator A (D_a^{-1}, or D_a^{-1} - P D_b^{-1} P^H).  L = A V, R = V, a = 1:
+    samples subtract x^H (A V)(V^H x), the estimate adds tr(V^H A V).  The
+    estimator stays unbiased for any V.
+    """
+    from .estimator import DirectSolvers
+    a, b = term
+    S = solvers if solvers is not None else DirectSolvers(hier)
+    V = np.asarray(V, dtype=np.complex128)
+    W = S.solve(a, V)
+    if b is not None:
+        P = hier.prolongator(a, b)
+        W = W - P @ S.solve(b, P.conj().T @ V)
+    return Deflation(L=W, R=V, a=np.ones(V.shape[1]), lam=np.zeros(V.shape[1]))

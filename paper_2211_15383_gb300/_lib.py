@@ -71,6 +71,10 @@ SIGNATURES = [
     ("mgmlmc_num_terms", C.c_int, [_P, _I, _I]),
     ("mgmlmc_compute_deflation", C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     ("mgmlmc_get_deflation", C.c_int, [_P, _D, _D, _D, _D, _D]),
+    ("mgmlmc_compute_term_deflation", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int]),
+    ("mgmlmc_get_term_deflation", C.c_int, [_P, C.c_int, _I, _D, _D, _D, _D]),
+    ("mgmlmc_compute_term_deflation_inexact", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int]),
+    ("mgmlmc_set_term_deflation_vectors", C.c_int, [_P, C.c_int, C.c_int, _D]),
     ("mgmlmc_estimate_level", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D, C.POINTER(LevelStats)]),
     ("mgmlmc_estimate_level_probes", C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int8), _D,
                                                C.POINTER(LevelStats)]),
@@ -240,6 +244,30 @@ class Context:
         self._check(self.lib.mgmlmc_get_deflation(self.h, _dptr(lam), _dptr(sig), U.ctypes.data_as(_D),
                                                   V.ctypes.data_as(_D), _dptr(tau)))
         return lam, sig, U, V, complex(tau[0], tau[1])
+
+    def compute_term_deflation(self, term: int, k: int, tol: float = 1e-9, max_iters: int = 200):
+        self._check(self.lib.mgmlmc_compute_term_deflation(self.h, int(term), int(k), float(tol), int(max_iters)))
+
+    def compute_term_deflation_inexact(self, term: int, k: int, eig_tol: float = 1e-1, inner_tol: float = 1e-3,
+                                       max_iters: int = 200):
+        self._check(self.lib.mgmlmc_compute_term_deflation_inexact(self.h, int(term), int(k), float(eig_tol),
+                                                                   float(inner_tol), int(max_iters)))
+
+    def set_term_deflation_vectors(self, term: int, V: np.ndarray):
+        v = _cplx(np.atleast_2d(V))
+        self._check(self.lib.mgmlmc_set_term_deflation_vectors(self.h, int(term), v.shape[0], v.ctypes.data_as(_D)))
+
+    def get_term_deflation(self, term: int, k: int):
+        _, levels = self.num_terms()
+        n = self.level_info(levels[term])[3]
+        kk = C.c_int()
+        lam = np.zeros(k)
+        L = np.zeros((k, n), np.complex128)
+        R = np.zeros((k, n), np.complex128)
+        tau = np.zeros(2)
+        self._check(self.lib.mgmlmc_get_term_deflation(self.h, int(term), C.byref(kk), _dptr(lam),
+                                                       L.ctypes.data_as(_D), R.ctypes.data_as(_D), _dptr(tau)))
+        return lam, L, R, complex(tau[0], tau[1])
 
     # ---------------------------------------------------------------- estimation
     def estimate_level(self, term: int, first: int, nsamples: int, seed: int, samples: bool = True):

@@ -52,7 +52,7 @@ void require_level(const Ctx& c, int level) {
 
 struct TermLevels {
     int a, b;          // 0-based fine / coarse level; b = -1 for the last term
-    bool deflated;
+    const mg::Deflation* defl;   // exact deflation of this term, if computed
 };
 
 TermLevels term_levels(const Ctx& c, int t) {
@@ -61,7 +61,7 @@ TermLevels term_levels(const Ctx& c, int t) {
     TermLevels tl;
     tl.a = c.term_level[t];
     tl.b = (t + 1 < c.nterms) ? c.term_level[t + 1] : -1;
-    tl.deflated = (tl.b < 0 && c.defl.k > 0 && tl.a == c.L - 1);
+    tl.defl = mg::term_deflation(c, tl.a, tl.b);
     return tl;
 }
 
@@ -92,16 +92,17 @@ bool run_term_block(Ctx& c, const TermLevels& tl, const double2* X, int Nb, doub
         mg::launch_dot<double2, double2>(s2, Ycur, W, Lb.n, Nb, part2, c.stream);
         mg::launch_axpy_rhs<double2, double2>(smp, nullptr, nullptr, -1.0, s2, 1, Nb, c.stream);
     }
-    if (tl.deflated) {
-        const int k = c.defl.k;
+    if (tl.defl) {
+        const mg::Deflation& D = *tl.defl;
+        const int k = D.k;
         double2* A = c.scratch<double2>("est_A", (size_t)k * Nb);
         double2* B = c.scratch<double2>("est_B", (size_t)k * Nb);
         const int groups = mg::gemm_hn_groups(La.n, k, Nb);
         double2* part3 = c.scratch<double2>("est_part3", (size_t)groups * k * Nb);
         mg::ProfScope ps(c, "defl.f64", 2.0 * La.n * k * 16 + (double)La.n * Nb * 16, 2.0 * 8.0 * La.n * k * Nb);
-        mg::launch_gemm_hn<double2>(A, c.defl.Rv, X, La.n, k, Nb, part3, groups, c.stream);
-        mg::launch_gemm_hn<double2>(B, c.defl.Lv, X, La.n, k, Nb, part3, groups, c.stream);
-        mg::launch_deflation_correction(smp, A, B, c.defl.a, k, Nb, c.stream);
+        mg::launch_gemm_hn<double2>(A, D.Rv, X, La.n, k, Nb, part3, groups, c.stream);
+        mg::launch_gemm_hn<double2>(B, D.Lv, X, La.n, k, Nb, part3, groups, c.stream);
+        mg::launch_deflation_correction(smp, A, B, D.a, k, Nb, c.stream);
     }
     return all_ok;
 }
@@ -282,7 +283,7 @@ int mgmlmc_set_terms(mgmlmc_ctx* h, int nskip, const int* skip) {
     MG_REQUIRE(nskip >= 0 && (nskip == 0 || skip), MGMLMC_EINVAL, "set_terms: bad skip list");
     std::vector<int> sk(skip, skip + nskip);
     for (int s : sk)
-        MG_REQUIRE(s >= 2 && s <= c.L - 1, MGMLMC_EINVAL, "set_terms: only levels 2..L-1 can be skipped");
+        MG_REQUIRE(s >= 2 && s <= c.L, MGMLMC_EINVAL, "set_terms: only levels 2..L can be skipped");
     c.nterms = 0;
     for (int l = 0; l < c.L; ++l)
         if (std::find(sk.begin(), sk.end(), l + 1) == sk.end()) c.term_level[c.nterms++] = l;
@@ -303,7 +304,56 @@ int mgmlmc_num_terms(const mgmlmc_ctx* h, int* nterms, int* term_level) {
 
 int mgmlmc_compute_deflation(mgmlmc_ctx* h, int k, double tol, int max_iters) {
     API_BEGIN(h)
-    mg::compute_deflation(c, k, tol, max_iters);
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "compute_deflation: no hierarchy");
+    mg::compute_deflation(c, c.term_level[c.nterms - 1], k, tol, max_iters);
+    API_END
+}
+
+int mgmlmc_compute_term_deflation(mgmlmc_ctx* h, int term, int k, double tol, int max_iters) {
+    API_BEGIN(h)
+    const TermLevels tl = term_levels(c, term);
+    if (tl.b < 0) mg::compute_deflation(c, tl.a, k, tol, max_iters);
+    else mg::compute_difference_deflation(c, tl.a, tl.b, k, tol, max_iters);
+    API_END
+}
+
+int mgmlmc_compute_term_deflation_inexact(mgmlmc_ctx* h, int term, int k, double eig_tol, double inner_tol,
+                                          int max_iters) {
+    API_BEGIN(h)
+    MG_REQUIRE(inner_tol > 0 && inner_tol < 1, MGMLMC_EINVAL, "inexact deflation: 0 < inner_tol < 1");
+    const TermLevels tl = term_levels(c, term);
+    // eigensolver solves at inner_tol; the k extra solves of the deflated part at solve_tol
+    if (tl.b < 0) mg::compute_deflation(c, tl.a, k, eig_tol, max_iters, true, inner_tol);
+    else mg::compute_difference_deflation(c, tl.a, tl.b, k, eig_tol, max_iters, true, inner_tol);
+    API_END
+}
+
+int mgmlmc_set_term_deflation_vectors(mgmlmc_ctx* h, int term, int k, const double* V) {
+    API_BEGIN(h)
+    MG_REQUIRE(V, MGMLMC_EINVAL, "set_term_deflation_vectors: V is NULL");
+    const TermLevels tl = term_levels(c, term);
+    const long long n = c.lev[tl.a].n;
+    MG_REQUIRE(k >= 1 && k <= n, MGMLMC_EINVAL, "set_term_deflation_vectors: 1 <= k <= n_a");
+    double2* R = upload_block(c, V, n, k, "stdv_R");
+    mg::set_deflation_vectors(c, tl.a, tl.b, R, k);
+    API_END
+}
+
+int mgmlmc_get_term_deflation(mgmlmc_ctx* h, int term, int* k, double* lambda, double* L, double* R, double* tau) {
+    API_BEGIN(h)
+    const TermLevels tl = term_levels(c, term);
+    MG_REQUIRE(tl.defl, MGMLMC_ESTATE, "get_term_deflation: this term has no deflation");
+    const mg::Deflation& D = *tl.defl;
+    const long long n = c.lev[tl.a].n;
+    if (k) *k = D.k;
+    if (lambda)
+        for (int i = 0; i < D.k; ++i) lambda[i] = D.lambda[i];
+    if (L) download_block(c, L, D.Lv, n, D.k, "gd_tmp");
+    if (R) download_block(c, R, D.Rv, n, D.k, "gd_tmp");
+    if (tau) {
+        tau[0] = D.tau_re;
+        tau[1] = D.tau_im;
+    }
     API_END
 }
 
@@ -391,8 +441,15 @@ int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, ui
     bool converged = false;
     for (;;) {
         std::vector<double> N(T), V(T), C(T);
-        est_re = c.defl.k ? c.defl.tau_re : 0.0;
-        est_im = c.defl.k ? c.defl.tau_im : 0.0;
+        est_re = 0.0;
+        est_im = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const TermLevels tl = term_levels(c, t);
+            if (tl.defl) {
+                est_re += tl.defl->tau_re;
+                est_im += tl.defl->tau_im;
+            }
+        }
         double err2 = 0;
         long long total = 0;
         for (int t = 0; t < T; ++t) {
@@ -438,7 +495,11 @@ int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, ui
     out->trace_re = est_re;
     out->trace_im = est_im;
     out->rel_err = rel;
-    out->deflated_part = c.defl.k ? c.defl.tau_re : 0.0;
+    out->deflated_part = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const TermLevels tl = term_levels(c, t);
+        if (tl.defl) out->deflated_part += tl.defl->tau_re;
+    }
     out->nterms = T;
     out->converged = converged ? 1 : 0;
     out->rounds = rounds;

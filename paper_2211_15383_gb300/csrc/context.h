@@ -33,6 +33,9 @@ struct Level {
 
 struct Deflation {
     int k = 0;
+    int fine = -1;                   // fine level (0-based) of the term it belongs to
+    int coarse = -1;                 // coarse level of that term (-1: last term)
+    bool inexact = false;            // vectors from a loose eigensolve, L = A R computed
     double2* Lv = nullptr;           // [n][k] left vectors of the traced operator (V)
     double2* Rv = nullptr;           // [n][k] right vectors (U)
     double* a = nullptr;             // [k] 1/sigma
@@ -104,7 +107,8 @@ struct Ctx {
     int nterms = 0;
     int term_level[MGMLMC_MAX_LEVELS + 1] = {0};   // 0-based fine level of each term
     std::vector<int> skip;
-    Deflation defl;
+    Deflation defl;                  // coarsest term: k smallest triplets of D_L (Sect. 2)
+    Deflation ddefl[MGMLMC_MAX_LEVELS];   // difference terms, by fine level: largest triplets of M_l (Sect. 4.2)
     TermStats stats[MGMLMC_MAX_LEVELS];
     long long last_iters = 0;        // outer iterations of the last solve
 
@@ -149,7 +153,21 @@ void check_device_error(Ctx& c);
 // ---- setup (setup.cu)
 void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const int* nvec, int setup_iters,
                      double setup_tol, const double* const* start_vectors);
-void compute_deflation(Ctx& c, int k, double tol, int max_iters);
+// Exact deflation of the last term (fine level a): k smallest triplets of D_a.
+// With inexact, the vectors come from the eigensolver as they are and the
+// deflated part is recomputed from them (see store_deflation).
+// eig_solve_tol: tolerance of the eigensolver's solves (0: the context's solve_tol).
+void compute_deflation(Ctx& c, int a, int k, double tol, int max_iters, bool inexact = false,
+                       double eig_solve_tol = 0);
+// Exact deflation of the difference term with fine level a and coarse level b
+// (0-based): k largest singular triplets of M from eigenpairs of J = M Gamma5^a.
+void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int max_iters, bool inexact = false,
+                                  double eig_solve_tol = 0);
+// Deflation of term (a, b) by given right vectors R [n_a][k] (device): L = A R with
+// A the term's traced operator (FP64-accurate solves), a_i = 1.
+void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k);
+// The deflation that applies to the term (a, b), or nullptr.
+const Deflation* term_deflation(const Ctx& c, int a, int b);
 void upload_links(Ctx& c, const double* theta);
 
 }  // namespace mg

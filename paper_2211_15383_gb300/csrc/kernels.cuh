@@ -100,7 +100,8 @@ void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s);
 size_t gauss_jordan_work_bytes(int n);
 // Hermitian eigenproblem of a small b x b matrix (cyclic Jacobi, one CTA):
 // H is overwritten; W receives eigenvectors (columns), lam eigenvalues.
-void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s);
+void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s,
+                       bool descending = false);
 // BF16 real embedding [Re A | Im A] (n x 2n) of a complex FP32 n x n matrix for the
 // tensor-core coarsest solve.
 void launch_embed_bf16(__nv_bfloat16* E, const float2* A, int n, cudaStream_t s);

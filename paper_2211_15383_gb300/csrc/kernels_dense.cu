@@ -247,9 +247,10 @@ void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s) {
 // rotation G = diag(1, e^{-i phi}) [[c, s], [-s, c]] removes H[p][q] = |h| e^{i phi}
 // with (c, s) from the symmetric 2x2 Schur decomposition (tau = (h_qq - h_pp)/(2|h|),
 // t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c).
-// Eigenvalues are returned sorted by increasing |lambda|, eigenvectors in the
-// matching columns of W.
-__global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double* lam, int b, int sweeps) {
+// Eigenvalues are returned sorted by increasing |lambda| (decreasing with
+// descending = 1), eigenvectors in the matching columns of W.
+__global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double* lam, int b, int sweeps,
+                                                int descending) {
     extern __shared__ double sm_jac[];
     const int bp = b + (b & 1);                  // padded to even
     int* order = reinterpret_cast<int*>(sm_jac);               // bp
@@ -346,10 +347,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double*
     for (int e = tid; e < b * b; e += nt) H[e] = W[e];
     __syncthreads();
     for (int i = tid; i < b; i += nt) {
-        const double li = fabs(lam[i]);
+        const double li = descending ? -fabs(lam[i]) : fabs(lam[i]);
         int rank = 0;
         for (int j2 = 0; j2 < b; ++j2) {
-            const double lj = fabs(lam[j2]);
+            const double lj = descending ? -fabs(lam[j2]) : fabs(lam[j2]);
             if (lj < li || (lj == li && j2 < i)) ++rank;
         }
         order[i] = rank;
@@ -365,12 +366,12 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double*
     for (int i = tid; i < b; i += nt) lam[i] = lcopy[i];
 }
 
-void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s) {
+void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s, bool descending) {
     MG_REQUIRE(b >= 1 && b <= 1024, MGMLMC_EINVAL, "jacobi: 1 <= b <= 1024");
     const int bp = b + (b & 1);
     size_t sm = (size_t)((bp + 1) / 2 + 1) * sizeof(double) + 4 * (size_t)(bp / 2) * sizeof(double) + 64;
     if (sm < (size_t)(bp + 1) * sizeof(int)) sm = (bp + 1) * sizeof(int);
-    k_jacobi<<<1, 1024, sm, s>>>(H, W, lam, b, sweeps);
+    k_jacobi<<<1, 1024, sm, s>>>(H, W, lam, b, sweeps, descending ? 1 : 0);
     MG_LAUNCHED();
 }
 

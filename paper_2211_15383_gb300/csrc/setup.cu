@@ -70,6 +70,18 @@ void Ctx::free_deflation() {
     dev_free(defl.Rv);
     dev_free(defl.a);
     defl = Deflation();
+    for (auto& d : ddefl) {
+        dev_free(d.Lv);
+        dev_free(d.Rv);
+        dev_free(d.a);
+        d = Deflation();
+    }
+}
+
+const Deflation* term_deflation(const Ctx& c, int a, int b) {
+    if (b < 0) return (c.defl.k > 0 && c.defl.fine == a) ? &c.defl : nullptr;
+    const Deflation& d = c.ddefl[a];
+    return (d.k > 0 && d.coarse == b) ? &d : nullptr;
 }
 
 void Ctx::free_hierarchy() {
@@ -195,6 +207,10 @@ __global__ void k_sign_cols(double2* Y, const double* lam, long long n, int b) {
 __global__ void k_inv_abs(double* a, const double* lam, int k) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < k) a[i] = 1.0 / fabs(lam[i]);
+}
+__global__ void k_abs(double* a, const double* lam, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) a[i] = fabs(lam[i]);
 }
 // tau = sum_i a_i t_i  (t_i = u_i^H v_i), fixed order, one thread.
 __global__ void k_weighted_sum(double2* out, const double2* t, const double* a, int k) {
@@ -375,11 +391,15 @@ static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b)
     }
 }
 
-void compute_deflation(Ctx& c, int k, double tol, int max_iters) {
+void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool inexact, double eig_solve_tol) {
+    if (eig_solve_tol <= 0) eig_solve_tol = c.opt.solve_tol;
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "compute_deflation: no hierarchy");
-    c.free_deflation();
+    MG_REQUIRE(l >= 0 && l < c.L, MGMLMC_EINVAL, "compute_deflation: bad level");
+    c.dev_free(c.defl.Lv);
+    c.dev_free(c.defl.Rv);
+    c.dev_free(c.defl.a);
+    c.defl = Deflation();
     if (k == 0) return;
-    const int l = c.L - 1;
     const Level& L = c.lev[l];
     const long long n = L.n;
     MG_REQUIRE(k >= 1 && k <= n && k <= 512, MGMLMC_EINVAL, "compute_deflation: 0 <= k <= min(n_L, 512)");
@@ -403,7 +423,7 @@ void compute_deflation(Ctx& c, int k, double tol, int max_iters) {
         // X <- Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves), then orthonormalise
         launch_gamma5<double2>(T, X, L.nsites, L.d, b, c.stream);
         int ok = 0;
-        solve(c, l, T, Y, b, c.opt.solve_tol, &ok);
+        solve(c, l, T, Y, b, eig_solve_tol, &ok);
         MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "compute_deflation: coarsest solve did not converge");
         std::swap(X, Y);
         orthonormalize(c, X, Y, n, b);
@@ -428,8 +448,22 @@ void compute_deflation(Ctx& c, int k, double tol, int max_iters) {
         if (c.opt.verbose) fprintf(stderr, "[mgmlmc] deflation it %d worst rel residual %.3e\n", it, worst);
         conv = worst <= tol;
     }
+    if (inexact) {
+        // orthogonal projector on U = Gamma5 X (Sect. 2's Pi = U U^H) with the deflated
+        // part recomputed from the approximate vectors by k extra solves
+        double2* R = c.scratch<double2>("df_Rin", (size_t)n * k);
+        launch_gamma5<double2>(T, X, L.nsites, L.d, b, c.stream);
+        MG_CUDA(cudaMemcpy2DAsync(R, sizeof(double2) * k, T, sizeof(double2) * b, sizeof(double2) * k, n,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+        set_deflation_vectors(c, l, -1, R, k);
+        c.defl.lambda.assign(h_lam.begin(), h_lam.begin() + k);
+        c.defl.inexact = true;
+        if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "compute_deflation: eigensolver did not reach tol (results kept)");
+        return;
+    }
     // store V = X_k, U = Gamma5 X_k sign(lambda), a = 1/|lambda|
     c.defl.k = k;
+    c.defl.fine = l;
     c.defl.Lv = c.alloc_n<double2>((size_t)n * k);
     c.defl.Rv = c.alloc_n<double2>((size_t)n * k);
     c.defl.a = c.alloc_n<double>(k);
@@ -456,6 +490,221 @@ void compute_deflation(Ctx& c, int k, double tol, int max_iters) {
     c.defl.tau_im = htau.y;
     c.defl.lambda.assign(h_lam.begin(), h_lam.begin() + k);
     if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "compute_deflation: eigensolver did not reach tol (results kept)");
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// Y = J X = D_a^{-1} Gamma5^a X - P D_b^{-1} Gamma5^b P^H X  (FP64-accurate solves)
+static void apply_J(Ctx& c, int a, int b, const double2* X, double2* Y, int nb, double tol) {
+    const Level& La = c.lev[a];
+    double2* T = c.scratch<double2>("dd_T", (size_t)La.n * nb);
+    int ok = 0;
+    launch_gamma5<double2>(T, X, La.nsites, La.d, nb, c.stream);
+    solve(c, a, T, Y, nb, tol, &ok);
+    MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "difference deflation: solve on the fine level did not converge");
+    const double2* cur = X;
+    for (int l = a; l < b; ++l) {
+        double2* nx = c.scratch<double2>("dd_R" + std::to_string(l + 1), (size_t)c.lev[l + 1].n * nb);
+        apply_restrict<double2>(c, l, nx, cur, nb);
+        cur = nx;
+    }
+    const Level& Lb = c.lev[b];
+    double2* Tb = c.scratch<double2>("dd_Tb", (size_t)Lb.n * nb);
+    double2* Zb = c.scratch<double2>("dd_Zb", (size_t)Lb.n * nb);
+    launch_gamma5<double2>(Tb, cur, Lb.nsites, Lb.d, nb, c.stream);
+    solve(c, b, Tb, Zb, nb, tol, &ok);
+    MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "difference deflation: solve on the coarse level did not converge");
+    // prolongate back to level a and subtract
+    const double2* up = Zb;
+    for (int l = b - 1; l >= a; --l) {
+        double2* px = c.scratch<double2>("dd_P" + std::to_string(l), (size_t)c.lev[l].n * nb);
+        apply_prolong<double2>(c, l, px, up, nb, false);
+        up = px;
+    }
+    launch_axpy_rhs<double2, double2>(Y, nullptr, nullptr, -1.0, up, La.n, nb, c.stream);
+}
+
+void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int max_iters, bool inexact,
+                                  double eig_solve_tol) {
+    if (eig_solve_tol <= 0) eig_solve_tol = c.opt.solve_tol;
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "difference deflation: no hierarchy");
+    MG_REQUIRE(a >= 0 && b > a && b < c.L, MGMLMC_EINVAL, "difference deflation: bad term");
+    Deflation& D = c.ddefl[a];
+    c.dev_free(D.Lv);
+    c.dev_free(D.Rv);
+    c.dev_free(D.a);
+    D = Deflation();
+    if (k == 0) return;
+    const Level& La = c.lev[a];
+    const long long n = La.n;
+    MG_REQUIRE(k >= 1 && k <= n && k <= 512, MGMLMC_EINVAL, "difference deflation: 0 <= k <= min(n_a, 512)");
+    MG_REQUIRE(tol > 0 && max_iters >= 1, MGMLMC_EINVAL, "difference deflation: tol > 0 and max_iters >= 1");
+    const int nb = (int)std::min<long long>(n, std::max(2 * k, k + 16));
+    double2* X = c.scratch<double2>("dd_X", (size_t)n * nb);
+    double2* Y = c.scratch<double2>("dd_Y", (size_t)n * nb);
+    double2* Xr = c.scratch<double2>("dd_Xr", (size_t)n * nb);
+    double2* Yr = c.scratch<double2>("dd_Yr", (size_t)n * nb);
+    double2* H = c.scratch<double2>("dd_H", (size_t)nb * nb);
+    double2* W = c.scratch<double2>("dd_W", (size_t)nb * nb);
+    double* lam = c.scratch<double>("dd_lam", nb);
+    double* res = c.scratch<double>("dd_res", nb);
+    const int groups = gemm_hn_groups(n, nb, nb);
+    double2* part = c.scratch<double2>("dd_part", (size_t)groups * nb * nb);
+    launch_noise<double2>(X, n, nb, 0x2211153831ull, 78 + a, 0, c.stream);
+    orthonormalize(c, X, Y, n, nb);
+    std::vector<double> h_lam(nb), h_res(nb);
+    bool conv = false;
+    for (int it = 0; it < max_iters && !conv; ++it) {
+        apply_J(c, a, b, X, Y, nb, eig_solve_tol);
+        // Rayleigh-Ritz on span(X): H = X^H J X, largest |lambda| first
+        launch_gemm_hn<double2>(H, X, Y, n, nb, nb, part, groups, c.stream);
+        k_hermitize<<<(nb * nb + 127) / 128, 128, 0, c.stream>>>(H, nb);
+        small_launch_check();
+        launch_jacobi_eig(H, W, lam, nb, 40, c.stream, true);
+        launch_gemm_nn<double2>(Xr, X, W, (int)n, nb, nb, false, c.stream);
+        launch_gemm_nn<double2>(Yr, Y, W, (int)n, nb, nb, false, c.stream);
+        k_resid_cols<<<(unsigned)((n * nb + 255) / 256), 256, 0, c.stream>>>(Y, Yr, Xr, lam, n, nb);
+        small_launch_check();
+        column_norms(c, res, Y, n, nb);
+        MG_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.stream));
+        MG_CUDA(cudaMemcpyAsync(h_res.data(), res, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        double worst = 0;
+        for (int i = 0; i < k; ++i) worst = std::max(worst, h_res[i] / std::fabs(h_lam[i]));
+        if (c.opt.verbose) fprintf(stderr, "[mgmlmc] difference deflation level %d it %d worst rel residual %.3e\n",
+                                   a + 1, it, worst);
+        conv = worst <= tol;
+        if (conv) {
+            std::swap(X, Xr);          // X = Ritz vectors
+            break;
+        }
+        // next iterate: J applied to the Ritz vectors, orthonormalised
+        std::swap(X, Yr);
+        orthonormalize(c, X, Y, n, nb);
+    }
+    if (!conv) {
+        // the last Ritz vectors are the best available
+        std::swap(X, Xr);
+    }
+    if (inexact) {
+        // orthogonal projector on V = Gamma5^a X, deflated part recomputed from the
+        // approximate vectors by k extra applications of M
+        double2* R = c.scratch<double2>("dd_Rin", (size_t)n * k);
+        double2* T0 = c.scratch<double2>("dd_T2", (size_t)n * nb);
+        launch_gamma5<double2>(T0, X, La.nsites, La.d, nb, c.stream);
+        MG_CUDA(cudaMemcpy2DAsync(R, sizeof(double2) * k, T0, sizeof(double2) * nb, sizeof(double2) * k, n,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+        set_deflation_vectors(c, a, b, R, k);
+        c.ddefl[a].lambda.assign(h_lam.begin(), h_lam.begin() + k);
+        c.ddefl[a].inexact = true;
+        if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "difference deflation: eigensolver did not reach tol (results kept)");
+        return;
+    }
+    // U = X sign(lambda) (left, L), V = Gamma5^a X (right, R), a = |lambda|
+    D.k = k;
+    D.fine = a;
+    D.coarse = b;
+    D.Lv = c.alloc_n<double2>((size_t)n * k);
+    D.Rv = c.alloc_n<double2>((size_t)n * k);
+    D.a = c.alloc_n<double>(k);
+    double2* T = c.scratch<double2>("dd_T2", (size_t)n * nb);
+    MG_CUDA(cudaMemcpyAsync(T, X, sizeof(double2) * n * nb, cudaMemcpyDeviceToDevice, c.stream));
+    k_sign_cols<<<(unsigned)((n * nb + 255) / 256), 256, 0, c.stream>>>(T, lam, n, nb);
+    small_launch_check();
+    MG_CUDA(cudaMemcpy2DAsync(D.Lv, sizeof(double2) * k, T, sizeof(double2) * nb, sizeof(double2) * k, n,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    launch_gamma5<double2>(T, X, La.nsites, La.d, nb, c.stream);
+    MG_CUDA(cudaMemcpy2DAsync(D.Rv, sizeof(double2) * k, T, sizeof(double2) * nb, sizeof(double2) * k, n,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    k_abs<<<(k + 127) / 128, 128, 0, c.stream>>>(D.a, lam, k);
+    small_launch_check();
+    double2* t = c.scratch<double2>("dd_t", k);
+    double2* tau = c.scratch<double2>("dd_tau", 1);
+    double2* dpart = c.scratch<double2>("dd_dpart", (size_t)reduce_groups(n, k) * k);
+    launch_dot<double2, double2>(t, D.Rv, D.Lv, n, k, dpart, c.stream);
+    k_weighted_sum<<<1, 1, 0, c.stream>>>(tau, t, D.a, k);
+    small_launch_check();
+    double2 htau;
+    MG_CUDA(cudaMemcpyAsync(&htau, tau, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    D.tau_re = htau.x;
+    D.tau_im = htau.y;
+    D.lambda.assign(h_lam.begin(), h_lam.begin() + k);
+    if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "difference deflation: eigensolver did not reach tol (results kept)");
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// Y = A X for the traced operator of term (a, b): D_a^{-1} X - P D_b^{-1} P^H X,
+// or D_a^{-1} X for the last term (b < 0).  FP64-accurate solves.
+static void apply_traced(Ctx& c, int a, int b, const double2* X, double2* Y, int nb) {
+    int ok = 0;
+    solve(c, a, X, Y, nb, c.opt.solve_tol, &ok);
+    MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "deflation: solve on the fine level did not converge");
+    if (b < 0) return;
+    const double2* cur = X;
+    for (int l = a; l < b; ++l) {
+        double2* nx = c.scratch<double2>("at_R" + std::to_string(l + 1), (size_t)c.lev[l + 1].n * nb);
+        apply_restrict<double2>(c, l, nx, cur, nb);
+        cur = nx;
+    }
+    double2* Zb = c.scratch<double2>("at_Zb", (size_t)c.lev[b].n * nb);
+    solve(c, b, cur, Zb, nb, c.opt.solve_tol, &ok);
+    MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "deflation: solve on the coarse level did not converge");
+    const double2* up = Zb;
+    for (int l = b - 1; l >= a; --l) {
+        double2* px = c.scratch<double2>("at_P" + std::to_string(l), (size_t)c.lev[l].n * nb);
+        apply_prolong<double2>(c, l, px, up, nb, false);
+        up = px;
+    }
+    launch_axpy_rhs<double2, double2>(Y, nullptr, nullptr, -1.0, up, c.lev[a].n, nb, c.stream);
+}
+
+__global__ void k_fill(double* a, double v, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) a[i] = v;
+}
+
+void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k) {
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "deflation: no hierarchy");
+    MG_REQUIRE(a >= 0 && a < c.L && (b < 0 || (b > a && b < c.L)), MGMLMC_EINVAL, "deflation: bad term");
+    const long long n = c.lev[a].n;
+    MG_REQUIRE(k >= 1 && k <= n && k <= 4096, MGMLMC_EINVAL, "deflation: 1 <= k <= min(n_a, 4096)");
+    Deflation& D = (b < 0) ? c.defl : c.ddefl[a];
+    // R may live in scratch that apply_traced reuses: keep a private copy first
+    double2* Rv = c.alloc_n<double2>((size_t)n * k);
+    MG_CUDA(cudaMemcpyAsync(Rv, R, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, c.stream));
+    double2* Lv = c.alloc_n<double2>((size_t)n * k);
+    apply_traced(c, a, b, Rv, Lv, k);
+    c.dev_free(D.Lv);
+    c.dev_free(D.Rv);
+    c.dev_free(D.a);
+    D = Deflation();
+    D.k = k;
+    D.fine = a;
+    D.coarse = b;
+    D.Lv = Lv;
+    D.Rv = Rv;
+    D.a = c.alloc_n<double>(k);
+    k_fill<<<(k + 127) / 128, 128, 0, c.stream>>>(D.a, 1.0, k);
+    small_launch_check();
+    // tau = sum_i r_i^H l_i = tr(R^H A R)
+    double2* t = c.scratch<double2>("sv_t", k);
+    double2* tau = c.scratch<double2>("sv_tau", 1);
+    double2* dpart = c.scratch<double2>("sv_dpart", (size_t)reduce_groups(n, k) * k);
+    launch_dot<double2, double2>(t, D.Rv, D.Lv, n, k, dpart, c.stream);
+    k_weighted_sum<<<1, 1, 0, c.stream>>>(tau, t, D.a, k);
+    small_launch_check();
+    double2 htau;
+    MG_CUDA(cudaMemcpyAsync(&htau, tau, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    D.tau_re = htau.x;
+    D.tau_im = htau.y;
+    D.inexact = true;
 }
 
 }  // namespace mg

@@ -115,3 +115,81 @@ def test_mlmc_loop_matches_oracle_rule(pkg, c1):
     assert abs(res["trace"] - ref["estimate"]) < 1e-9 * abs(ref["estimate"])
     exact = np.trace(np.linalg.inv(H.D[0].toarray()))
     assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_difference_level_deflation(pkg, c1, prec):
+    # exact deflation on the difference level (Sect. 4.2): k = 5 largest singular
+    # triplets of M_1 (a spectral gap follows the 5th), then deflated samples
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    k = 5
+    dref = odefl.difference_deflation(H, (1, 2), k)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=prec) as ctx:
+        ctx.compute_term_deflation(0, k, 1e-10, 2000)
+        lam, L, R, tau = ctx.get_term_deflation(0, k)
+        assert np.abs(np.abs(lam) - dref.a).max() < 1e-9 * dref.a.max()
+        assert abs(tau - dref.trace_term()) < 1e-9 * max(1.0, abs(dref.trace_term()))
+        Pg = L.T @ L.conj()
+        Po = dref.L @ dref.L.conj().T
+        assert np.abs(Pg - Po).max() < 1e-8
+        got, _ = ctx.estimate_level(0, 0, w.nrhs, w.noise_seed)
+        ref = oest.noise_samples(H, (1, 2), w.noise_seed, 0, w.nrhs, solvers, dref)
+        assert rel_sample_error(got, ref) < TOL64
+        # the coarsest term is unaffected; with both deflations the MLMC estimate adds both traces
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        res = ctx.estimate_trace(5e-2, 100000, 3, [1.0, 0.1])
+        exact = np.trace(np.linalg.inv(H.D[0].toarray()))
+        assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
+        assert abs(res["deflated_part"] - (dref.trace_term() + defl.trace_term()).real) < 1e-8 * abs(exact)
+
+
+def test_deflation_by_given_vectors(pkg, c1):
+    # inexact-style deflation with the same seeded orthonormal vectors on both sides
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    n = H.D[0].shape[0]
+    V, _ = np.linalg.qr(inputs.gaussian_complex(17, 3, (n, 6)))
+    dref = odefl.vector_deflation(H, (1, 2), V, solvers)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters) as ctx:
+        ctx.set_term_deflation_vectors(0, V.T)
+        _, L, R, tau = ctx.get_term_deflation(0, 6)
+        assert np.abs(R.T - V).max() < 1e-15
+        assert abs(tau - dref.trace_term()) < 1e-9 * max(1.0, abs(dref.trace_term()))
+        got, _ = ctx.estimate_level(0, 0, 40, 8)
+        ref = oest.noise_samples(H, (1, 2), 8, 0, 40, solvers, dref)
+        assert rel_sample_error(got, ref) < TOL64
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_inexact_deflation_keeps_estimate_unbiased(pkg, c1, prec):
+    # loosely converged vectors (eigensolver 1e-1, inner solves 1e-3, as in the paper's
+    # inexact runs): the trace estimate stays consistent with the exact trace
+    w, theta, sv, H, defl = c1
+    exact = np.trace(np.linalg.inv(H.D[0].toarray()))
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=prec) as ctx:
+        ctx.compute_term_deflation_inexact(0, 8, 1e-1, 1e-3, 500)
+        ctx.compute_term_deflation_inexact(1, w.k, 1e-1, 1e-3, 500)
+        _, L, R, _ = ctx.get_term_deflation(0, 8)
+        assert np.abs(R.conj() @ R.T - np.eye(8)).max() < 1e-10          # orthonormal V
+        res = ctx.estimate_trace(3e-2, 100000, 5, [1.0, 0.1])
+        assert res["converged"] == 1
+        assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
+
+
+def test_deflated_hutchinson_on_the_fine_operator(pkg, c1):
+    # skip every coarse level: one term tr(D_1^{-1}) (Sect. 2's deflated Hutchinson),
+    # deflated by the 16 smallest triplets of D_1; MG still preconditions the solves
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    dref = odefl.coarsest_deflation(H.D[0], H.g5[0], 16)
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters) as ctx:
+        ctx.set_terms([2])
+        assert ctx.num_terms() == (1, [1])
+        ctx.compute_term_deflation(0, 16, 1e-10, 2000)
+        lam, L, R, tau = ctx.get_term_deflation(0, 16)
+        assert np.abs(np.abs(lam) - 1.0 / dref.a).max() < 1e-10 * np.abs(lam).max()
+        assert abs(tau - dref.trace_term()) < 1e-9 * abs(dref.trace_term())
+        got, _ = ctx.estimate_level(0, 0, 48, 12)
+        ref = oest.noise_samples(H, (1, None), 12, 0, 48, solvers, dref)
+        assert rel_sample_error(got, ref) < TOL64

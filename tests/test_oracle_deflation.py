@@ -99,3 +99,24 @@ def test_full_difference_deflation_is_exact():
     M = estimator.term_operator(H, term)
     assert np.abs(estimator.deflated_operator(M, d)).max() < 1e-10 * np.abs(M).max()
     assert abs(d.trace_term() - np.trace(M)) < 1e-10 * max(1.0, abs(np.trace(M)))
+
+
+def test_vector_deflation_unbiased_and_exact_limit():
+    # any V: mean over all Z2 vectors + tr(V^H A V) = tr(A); V = exact right singular
+    # vectors: identical to exact deflation
+    import itertools
+    from oracle import hierarchy
+    th = inputs.metropolis_u1(2, 4, 2.0, 10, 3)
+    sv = [inputs.start_vectors(3, 1, 16, 1)]
+    H = hierarchy.build_hierarchy(th, 0.1, ((1, 2),), (1,), sv, 1)
+    solvers = estimator.DirectSolvers(H)
+    X = np.array(list(itertools.product([1.0, -1.0], repeat=16)))
+    term = (1, 2)
+    A = estimator.term_operator(H, term)
+    V, _ = np.linalg.qr(inputs.gaussian_complex(5, 5, (16, 3)))
+    d = deflation.vector_deflation(H, term, V, solvers)
+    s = estimator.term_samples(H, term, X, solvers, d)
+    assert abs(s.mean() + d.trace_term() - np.trace(A)) < 1e-11 * max(1.0, abs(np.trace(A)))
+    ex = deflation.difference_deflation(H, term, 3)
+    dv = deflation.vector_deflation(H, term, ex.R, solvers)
+    assert np.abs(estimator.deflated_operator(A, dv) - estimator.deflated_operator(A, ex)).max() < 1e-10 * np.abs(A).max()
