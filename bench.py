@@ -150,25 +150,21 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def kernel_sources_sha():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2211_15383_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
-    return h.hexdigest()[:16]
+def source_sha(fn):
+    path = os.path.join(ROOT, "paper_2211_15383_gb300", "csrc", fn)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if os.path.exists(path) else None
 
 
 def ncu_traffic(kclass):
     """DRAM bytes per launch of a kernel class from a committed ncu summary, if the
-    kernels have not changed since it was taken."""
+    kernel's source file has not changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("kernel_sources_sha") != kernel_sources_sha():
+    e = json.load(open(p)).get("classes", {}).get(kclass)
+    if e is None or source_sha(e.get("source", "")) != e.get("source_sha"):
         return None
-    e = d.get("classes", {}).get(kclass)
-    return None if e is None else e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_launch")
 
 
 def roofline(report, peaks, fp64_peak, fp32_peak):

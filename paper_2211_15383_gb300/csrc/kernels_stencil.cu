@@ -270,6 +270,95 @@ __global__ void k_prolong(C* __restrict__ x, const C* __restrict__ xc, const C* 
     }
 }
 
+// Aggregate-per-block restriction / prolongation for compile-time nvec: block =
+// 128 rhs, one coarse site S per block iteration; P restricted to S (ax*at*d*nvec
+// values) staged in shared memory; each thread reads every fine value of its rhs
+// once and keeps the 2 nvec coarse values in registers.
+template <typename C, int NV>
+__global__ void __launch_bounds__(128) k_restrict_nv(C* __restrict__ xc, const C* __restrict__ x,
+                                                     const C* __restrict__ P, int lx, int lt, int d, int ax, int at,
+                                                     int N) {
+    extern __shared__ __align__(16) unsigned char smem_rp[];
+    C* Ps = reinterpret_cast<C*>(smem_rp);
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int cx = lx / ax, ct = lt / at, hd = d / 2, na = ax * at;
+    const int nP = na * d * NV;
+    for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
+        const int X = S % cx, T = S / cx;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nP; e += 128) {
+            const int q = e / (d * NV), r = e % (d * NV);
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            Ps[e] = P[(long long)site * d * NV + r];
+        }
+        __syncthreads();
+        if (j >= N) continue;
+        C acc[2 * NV];
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) acc[o] = czero<C>();
+        for (int q = 0; q < na; ++q) {
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            const C* xs = x + (long long)site * d * N + j;
+            const C* Pq = Ps + q * d * NV;
+            for (int a = 0; a < d; ++a) {
+                const C xv = xs[(long long)a * N];
+                const C* Pa = Pq + a * NV;
+                if (a < hd) {
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfmac(acc[jv], Pa[jv], xv);
+                } else {
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfmac(acc[NV + jv], Pa[jv], xv);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) xc[((long long)S * 2 * NV + o) * N + j] = acc[o];
+    }
+}
+
+template <typename C, int NV>
+__global__ void __launch_bounds__(128) k_prolong_nv(C* __restrict__ x, const C* __restrict__ xc,
+                                                    const C* __restrict__ P, int lx, int lt, int d, int ax, int at,
+                                                    int N, bool accumulate) {
+    extern __shared__ __align__(16) unsigned char smem_rp[];
+    C* Ps = reinterpret_cast<C*>(smem_rp);
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int cx = lx / ax, ct = lt / at, hd = d / 2, na = ax * at;
+    const int nP = na * d * NV;
+    for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
+        const int X = S % cx, T = S / cx;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nP; e += 128) {
+            const int q = e / (d * NV), r = e % (d * NV);
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            Ps[e] = P[(long long)site * d * NV + r];
+        }
+        __syncthreads();
+        if (j >= N) continue;
+        C cv[2 * NV];
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) cv[o] = xc[((long long)S * 2 * NV + o) * N + j];
+        for (int q = 0; q < na; ++q) {
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            C* xs = x + (long long)site * d * N + j;
+            const C* Pq = Ps + q * d * NV;
+            for (int a = 0; a < d; ++a) {
+                const C* Pa = Pq + a * NV;
+                C acc = accumulate ? xs[(long long)a * N] : czero<C>();
+                if (a < hd) {
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfma(acc, Pa[jv], cv[jv]);
+                } else {
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfma(acc, Pa[jv], cv[NV + jv]);
+                }
+                xs[(long long)a * N] = acc;
+            }
+        }
+    }
+}
+
 template <typename C>
 __global__ void k_mr_update(C* __restrict__ e, C* __restrict__ r, const C* __restrict__ p,
                             const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
@@ -379,9 +468,38 @@ void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int 
     else bs_dispatch<C, 8>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
 }
 
+template <typename C, int NV>
+static void rp_launch(bool restrict_op, C* xc_or_x, const C* in, const C* P, int lx, int lt, int d, int ax, int at,
+                      int N, bool accumulate, cudaStream_t s) {
+    const int ncs = (lx / ax) * (lt / at);
+    const int tiles = (N + 127) / 128;
+    int G = 16 * kNumSM / tiles;
+    if (G > ncs) G = ncs;
+    if (G < 1) G = 1;
+    const size_t sm = (size_t)ax * at * d * NV * sizeof(C);
+    if (restrict_op)
+        k_restrict_nv<C, NV><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N);
+    else
+        k_prolong_nv<C, NV><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N, accumulate);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+static bool rp_fast(bool restrict_op, C* out, const C* in, const C* P, int lx, int lt, int d, int ax, int at,
+                    int nvec, int N, bool accumulate, cudaStream_t s) {
+    if ((size_t)ax * at * d * nvec * sizeof(C) > 48 * 1024) return false;
+    switch (nvec) {
+        case 2: rp_launch<C, 2>(restrict_op, out, in, P, lx, lt, d, ax, at, N, accumulate, s); return true;
+        case 4: rp_launch<C, 4>(restrict_op, out, in, P, lx, lt, d, ax, at, N, accumulate, s); return true;
+        case 8: rp_launch<C, 8>(restrict_op, out, in, P, lx, lt, d, ax, at, N, accumulate, s); return true;
+        default: return false;
+    }
+}
+
 template <typename C>
 void launch_restrict(C* xc, const C* x, const C* P, int lx, int lt, int d, int ax, int at, int nvec, int N,
                      cudaStream_t s) {
+    if (rp_fast<C>(true, xc, x, P, lx, lt, d, ax, at, nvec, N, false, s)) return;
     const int ncs = (lx / ax) * (lt / at);
     int G = row_groups((long long)ncs * kRowLanes, N, 4);
     k_restrict<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(xc, x, P, lx, lt, d, ax, at, nvec, N);
@@ -391,6 +509,7 @@ void launch_restrict(C* xc, const C* x, const C* P, int lx, int lt, int d, int a
 template <typename C>
 void launch_prolong(C* x, const C* xc, const C* P, int lx, int lt, int d, int ax, int at, int nvec, int N,
                     bool accumulate, cudaStream_t s) {
+    if (rp_fast<C>(false, x, xc, P, lx, lt, d, ax, at, nvec, N, accumulate, s)) return;
     const long long rows = (long long)lx * lt * d;
     k_prolong<C><<<dim3(rhs_tiles(N), row_groups(rows, N)), blk(), 0, s>>>(x, xc, P, lx, lt, d, ax, at, nvec, N,
                                                                              accumulate);
