@@ -9,12 +9,14 @@
 // setup; B' is packed per call, K-major (transposed), so both operands are
 // K-major BF16 in the canonical no-swizzle shared-memory layout.
 //
-// Kernel: one CTA (4 warps) per 128 x NT output tile.  A 4-stage cp.async
-// pipeline stages 128x64 (A) and NTx64 (B) tiles; thread 0 issues 4
-// tcgen05.mma (K = 16 each) per stage and commits them to the stage's
-// mbarrier; the accumulator lives in TMEM (NT columns) and is read back with
-// tcgen05.ld.  Every mbarrier wait is bounded: on timeout the CTA records an
-// error flag, drains its copies, frees TMEM and returns.
+// Kernel: one CTA (4 warps) per 128 x NT output tile and K split.  Thread 0
+// streams 128x64 (A) and NTx64 (B) stages with 1-D bulk copies into a ring of
+// shared-memory stages (full/empty mbarrier pairs); thread 32 issues 4
+// tcgen05.mma (K = 16 each) per stage and commits the stage back; the
+// accumulator lives in TMEM (NT columns) and is read back with tcgen05.ld.
+// Split-K partials are added in a fixed order by a second kernel.  Every
+// mbarrier wait is bounded: on timeout the CTA records an error flag, frees TMEM
+// and returns.
 #include "kernels.cuh"
 
 namespace mg {
@@ -23,7 +25,6 @@ namespace tc {
 
 constexpr int BM = 128;         // rows per tile (TMEM lanes)
 constexpr int BK = 64;          // K per stage (4 MMAs of K = 16)
-constexpr int STAGES = 4;
 constexpr unsigned kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -66,34 +67,56 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     return false;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // Canonical K-major layout of a rows x 64 BF16 tile: 8-row groups of 1024 B
 // (eight 128-byte core matrices along K), rows 16 B apart inside a core matrix.
-__device__ __forceinline__ uint32_t tile_off(int row, int kchunk) {
-    return (uint32_t)((row >> 3) * 1024 + kchunk * 128 + (row & 7) * 16);
+// Operands are stored pre-tiled in global memory: a 128 x 64 tile of A' (16 KB) or
+// an NT x 64 tile of B' (NT * 128 B) is contiguous and already in the canonical
+// layout above, so one 1-D bulk copy (cp.async.bulk, completing on an mbarrier)
+// moves a whole stage operand.
+__host__ __device__ __forceinline__ size_t tiled_off(int row, int k, int rows_per_tile, int ktiles) {
+    const int tile_r = row / rows_per_tile, r = row % rows_per_tile;
+    const int tile_k = k / 64, kk = k % 64;
+    return ((size_t)tile_r * ktiles + tile_k) * (size_t)rows_per_tile * 128 +
+           (size_t)((r >> 3) * 1024 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2);
 }
 
-template <int NT>
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Warp-specialised main loop: thread 0 (warp 0) streams stages with bulk copies,
+// thread 32 (warp 1) issues tcgen05.mma and commits each stage back to its empty
+// barrier and the last one to `done`; then all four warps read TMEM (one lane
+// quarter each) and store their rows.  K range: split blockIdx.z of gridDim.z.
+template <int NT, int ST>
 __global__ void __launch_bounds__(128, 1)
-    k_tc_gemm_bf16(float* __restrict__ Y, const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Bt,
+    k_tc_gemm_bf16(float* __restrict__ Y, const __nv_bfloat16* __restrict__ At, const __nv_bfloat16* __restrict__ Bt,
                    int M, int K, int Ncols, int* __restrict__ err) {
     constexpr int A_BYTES = BM * BK * 2;
     constexpr int B_BYTES = NT * BK * 2;
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[STAGES];
+    __shared__ __align__(8) uint64_t full[ST], empty[ST], done;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * NT;
-    const int nk = K / BK;
+    const int mt = blockIdx.y, nt = blockIdx.x;
+    const int ktiles = K / BK;
+    const int per = (ktiles + gridDim.z - 1) / gridDim.z;
+    const int k_begin = blockIdx.z * per;
+    const int k_end = min(ktiles, k_begin + per);
+    const int nk = max(0, k_end - k_begin);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
@@ -101,7 +124,11 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -109,48 +136,34 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
+    const uint8_t* a_base = reinterpret_cast<const uint8_t*>(At) + (size_t)mt * ktiles * A_BYTES;
+    const uint8_t* b_base = reinterpret_cast<const uint8_t*>(Bt) + (size_t)nt * ktiles * B_BYTES;
 
-    auto load_stage = [&](int kt, int s) {
-        uint8_t* sa = smem + s * STAGE_BYTES;
-        uint8_t* sb = sa + A_BYTES;
-        const int k0 = kt * BK;
-        for (int c = tid; c < BM * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7;
-            cp_async16(sa + tile_off(r, kc), A + (size_t)(m0 + r) * K + k0 + kc * 8);
-        }
-        for (int c = tid; c < NT * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7;
-            cp_async16(sb + tile_off(r, kc), Bt + (size_t)(n0 + r) * K + k0 + kc * 8);
-        }
-    };
-
-    constexpr uint32_t IDESC = instr_desc(BM, NT);
-    bool ok = true;
-    // prologue: stages 0 .. STAGES-2
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nk) load_stage(s, s);
-        cp_async_commit();
-    }
-    for (int kt = 0; kt < nk && ok; ++kt) {
-        const int s = kt % STAGES;
-        // refill the stage consumed STAGES-1 iterations ago, once its MMAs are done
-        const int kn = kt + STAGES - 1;
-        if (kn < nk) {
-            const int sn = kn % STAGES;
-            if (kn >= STAGES) {
-                if (!mbar_wait(&mbar[sn], (unsigned)((kn / STAGES - 1) & 1))) {
-                    ok = false;
-                    atomicExch(&abort_flag, 1);
-                }
+    if (tid == 0) {
+        // producer
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % ST, u = i / ST;
+            if (u > 0 && !mbar_wait(&empty[s], (unsigned)((u - 1) & 1))) {
+                atomicExch(&abort_flag, 1);
+                break;
             }
-            if (ok) load_stage(kn, sn);
+            if (abort_flag) break;
+            uint8_t* sa = smem + s * STAGE_BYTES;
+            const int kt = k_begin + i;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            bulk_g2s(sa, a_base + (size_t)kt * A_BYTES, A_BYTES, &full[s]);
+            bulk_g2s(sa + A_BYTES, b_base + (size_t)kt * B_BYTES, B_BYTES, &full[s]);
         }
-        cp_async_commit();
-        cp_async_wait<STAGES - 1>();             // tile kt has landed (this thread's part)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (abort_flag) { ok = false; break; }
-        if (tid == 0) {
+    } else if (tid == 32) {
+        // MMA issuer
+        constexpr uint32_t IDESC = instr_desc(BM, NT);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % ST, u = i / ST;
+            if (!mbar_wait(&full[s], (unsigned)(u & 1))) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (abort_flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t sb = sa + A_BYTES;
@@ -158,28 +171,34 @@ __global__ void __launch_bounds__(128, 1)
             for (int ks = 0; ks < BK / 16; ++ks) {
                 const uint64_t ad = smem_desc(sa + ks * 256, 128, 1024);
                 const uint64_t bd = smem_desc(sb + ks * 256, 128, 1024);
-                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                     "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar[s])));
+                smem_u32(&empty[s])));
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done)));
     }
-    cp_async_wait<0>();
-    if (ok && nk > 0) {
-        const int last = nk - 1;
-        if (!mbar_wait(&mbar[last % STAGES], (unsigned)((last / STAGES) & 1))) ok = false;
-    }
+    __syncwarp();
+    // epilogue: wait for the last MMA, then every warp reads its 32 TMEM lanes
+    bool ok = mbar_wait(&done, 0u);
     __syncthreads();
-    if (!ok) abort_flag = 1;
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!abort_flag) {
-        // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = output rows
-        const int row = m0 + warp * 32 + lane;
+    if (!ok || abort_flag) {
+        if (tid == 0) atomicExch(err, 1);
+    } else if (nk == 0) {
+        // empty K slice: its partial is zero
+        const int row = mt * BM + warp * 32 + lane;
+        float* out = Y + (size_t)blockIdx.z * (size_t)M * Ncols;
+        if (row < M)
+            for (int c = 0; c < NT; ++c) out[(size_t)row * Ncols + nt * NT + c] = 0.f;
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int row = mt * BM + warp * 32 + lane;
+        float* out = Y + (size_t)blockIdx.z * (size_t)M * Ncols;
 #pragma unroll 1
         for (int c = 0; c < NT; c += 32) {
             uint32_t r[32];
@@ -195,35 +214,35 @@ __global__ void __launch_bounds__(128, 1)
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (row < M) {
-                float4* dst = reinterpret_cast<float4*>(Y + (size_t)row * Ncols + n0 + c);
+                float4* dst = reinterpret_cast<float4*>(out + (size_t)row * Ncols + nt * NT + c);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
                                          __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
             }
         }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
 }
 
-// A'[i][k] = Re A[i][k], A'[i][n + k] = Im A[i][k]   (A complex FP32 n x n)
+// A' = [Re A | Im A] (n x 2n) written pre-tiled (128-row tiles).
 __global__ void k_embed_a(__nv_bfloat16* __restrict__ E, const float2* __restrict__ A, int n) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
-    const long long i = e / n, k = e % n;
+    const int i = (int)(e / n), k = (int)(e % n);
     const float2 v = A[e];
-    E[i * 2 * n + k] = __float2bfloat16(v.x);
-    E[i * 2 * n + n + k] = __float2bfloat16(v.y);
+    const int kt = 2 * n / BK;
+    E[tiled_off(i, k, BM, kt) / 2] = __float2bfloat16(v.x);
+    E[tiled_off(i, n + k, BM, kt) / 2] = __float2bfloat16(v.y);
 }
 
-// Bt[col][k] (K-major B' of the real embedding), col = 2j + p; zero for col >= 2N.
+// B' (K-major, pre-tiled in NT-row tiles), col = 2j + p; zero for j >= N.
 //   k <  n: p = 0 -> Re X[k][j],       p = 1 -> Im X[k][j]
 //   k >= n: p = 0 -> -Im X[k-n][j],    p = 1 -> Re X[k-n][j]
-__global__ void k_pack_bt(__nv_bfloat16* __restrict__ Bt, const float2* __restrict__ X, int n, int N, int Ncols) {
+__global__ void k_pack_bt(__nv_bfloat16* __restrict__ Bt, const float2* __restrict__ X, int n, int N, int Ncols,
+                          int NT) {
     __shared__ float2 t[32][33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;   // rows of X, rhs
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -231,24 +250,31 @@ __global__ void k_pack_bt(__nv_bfloat16* __restrict__ Bt, const float2* __restri
         t[r][threadIdx.x] = (i < n && j < N) ? X[(size_t)i * N + j] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int K = 2 * n;
+    const int kt = 2 * n / BK;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int j = j0 + r;
         const int i = i0 + threadIdx.x;
         if (i >= n || 2 * j + 1 >= Ncols) continue;
         const float2 v = (j < N) ? t[threadIdx.x][r] : make_float2(0.f, 0.f);
-        Bt[(size_t)(2 * j) * K + i] = __float2bfloat16(v.x);
-        Bt[(size_t)(2 * j) * K + n + i] = __float2bfloat16(-v.y);
-        Bt[(size_t)(2 * j + 1) * K + i] = __float2bfloat16(v.y);
-        Bt[(size_t)(2 * j + 1) * K + n + i] = __float2bfloat16(v.x);
+        Bt[tiled_off(2 * j, i, NT, kt) / 2] = __float2bfloat16(v.x);
+        Bt[tiled_off(2 * j, n + i, NT, kt) / 2] = __float2bfloat16(-v.y);
+        Bt[tiled_off(2 * j + 1, i, NT, kt) / 2] = __float2bfloat16(v.y);
+        Bt[tiled_off(2 * j + 1, n + i, NT, kt) / 2] = __float2bfloat16(v.x);
     }
 }
 
-__global__ void k_unpad_y(float2* __restrict__ Y, const float* __restrict__ Yp, int n, int N, int Ncols) {
+// Y[i][j] = sum over splits of Yp[z][i][c] (fixed order), complex output unpadded.
+__global__ void k_reduce_y(float2* __restrict__ Y, const float* __restrict__ Yp, int n, int N, int Ncols, int splits) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * N) return;
     const long long i = e / N, j = e % N;
-    Y[e] = make_float2(Yp[i * Ncols + 2 * j], Yp[i * Ncols + 2 * j + 1]);
+    float re = 0.f, im = 0.f;
+    for (int z = 0; z < splits; ++z) {
+        const float* p = Yp + (size_t)z * n * Ncols + i * Ncols + 2 * j;
+        re += p[0];
+        im += p[1];
+    }
+    Y[e] = make_float2(re, im);
 }
 
 }  // namespace tc
@@ -263,19 +289,47 @@ bool tc_coarse_supported(int n) { return n >= 128 && n % 128 == 0; }
 
 static int pick_nt(int N) { return (2 * N >= 256) ? 256 : (2 * N > 64 ? 128 : 64); }
 
+// Split-K factor: one CTA per SM (the stages fill ~192 KB of shared memory), so
+// split the K range until the tiles cover the 152 SMs once.
+static int pick_splits(int n, int Ncols, int NT) {
+    const int tiles = (Ncols / NT) * (n / tc::BM);
+    const int ktiles = 2 * n / tc::BK;
+    int S = kNumSM / (tiles > 0 ? tiles : 1);
+    if (S < 1) S = 1;
+    if (S > ktiles) S = ktiles;
+    if (S > 8) S = 8;
+    const int per = (ktiles + S - 1) / S;     // every slice non-empty
+    return (ktiles + per - 1) / per;
+}
+
 size_t coarse_inverse_bf16_scratch(int n, int N) {
     const int NT = pick_nt(N);
     const size_t ncols = (size_t)((2 * N + NT - 1) / NT) * NT;
-    return ncols * 2 * n * sizeof(__nv_bfloat16) + (size_t)n * ncols * sizeof(float) + 256;
+    const int S = pick_splits(n, (int)ncols, NT);
+    return ncols * 2 * n * sizeof(__nv_bfloat16) + (size_t)S * n * ncols * sizeof(float) + 256;
 }
 
-template <int NT>
-static void launch_tc(float* Y, const __nv_bfloat16* A, const __nv_bfloat16* Bt, int M, int K, int Ncols, int* err,
-                      cudaStream_t s) {
-    constexpr int smem = tc::STAGES * (tc::BM * tc::BK * 2 + NT * tc::BK * 2);
-    MG_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm_bf16<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 g(Ncols / NT, M / tc::BM);
-    tc::k_tc_gemm_bf16<NT><<<g, 128, smem, s>>>(Y, A, Bt, M, K, Ncols, err);
+template <int NT, int ST>
+static void launch_tc_st(float* Y, const __nv_bfloat16* A, const __nv_bfloat16* Bt, int M, int K, int Ncols,
+                         int splits, int* err, cudaStream_t s) {
+    constexpr int smem = ST * (tc::BM * tc::BK * 2 + NT * tc::BK * 2);
+    MG_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm_bf16<NT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 g(Ncols / NT, M / tc::BM, splits);
+    tc::k_tc_gemm_bf16<NT, ST><<<g, 128, smem, s>>>(Y, A, Bt, M, K, Ncols, err);
+    MG_LAUNCHED();
+}
+
+// Y (or split partials [splits][M][Ncols]) = A' B' for pre-tiled operands.
+static void launch_tc(int NT, float* Y, const __nv_bfloat16* A, const __nv_bfloat16* Bt, int M, int K, int Ncols,
+                      int splits, int* err, cudaStream_t s) {
+    if (NT == 256) launch_tc_st<256, 4>(Y, A, Bt, M, K, Ncols, splits, err, s);
+    else if (NT == 128) launch_tc_st<128, 6>(Y, A, Bt, M, K, Ncols, splits, err, s);
+    else launch_tc_st<64, 8>(Y, A, Bt, M, K, Ncols, splits, err, s);
+}
+
+static void launch_pack(__nv_bfloat16* Bt, const float2* X, int n, int N, int Ncols, int NT, cudaStream_t s) {
+    dim3 g((Ncols / 2 + 31) / 32, (n + 31) / 32);
+    tc::k_pack_bt<<<g, dim3(32, 8), 0, s>>>(Bt, X, n, N, Ncols, NT);
     MG_LAUNCHED();
 }
 
@@ -284,21 +338,15 @@ void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16*
     MG_REQUIRE(tc_coarse_supported(n), MGMLMC_EINVAL, "tensor-core coarsest solve needs n % 128 == 0");
     const int NT = pick_nt(N);
     const int Ncols = ((2 * N + NT - 1) / NT) * NT;
+    const int S = pick_splits(n, Ncols, NT);
     __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(scratch);
     float* Yp = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(scratch) + (size_t)Ncols * 2 * n * 2);
-    {
-        dim3 g((Ncols / 2 + 31) / 32, (n + 31) / 32);
-        tc::k_pack_bt<<<g, dim3(32, 8), 0, s>>>(Bt, X, n, N, Ncols);
-        MG_LAUNCHED();
-    }
-    const bool direct = (Ncols == 2 * N);
-    float* out = direct ? reinterpret_cast<float*>(Y) : Yp;
-    if (NT == 256) launch_tc<256>(out, E, Bt, n, 2 * n, Ncols, err, s);
-    else if (NT == 128) launch_tc<128>(out, E, Bt, n, 2 * n, Ncols, err, s);
-    else launch_tc<64>(out, E, Bt, n, 2 * n, Ncols, err, s);
+    launch_pack(Bt, X, n, N, Ncols, NT, s);
+    const bool direct = (Ncols == 2 * N && S == 1);
+    launch_tc(NT, direct ? reinterpret_cast<float*>(Y) : Yp, E, Bt, n, 2 * n, Ncols, S, err, s);
     if (!direct) {
         const long long tot = (long long)n * N;
-        tc::k_unpad_y<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Y, Yp, n, N, Ncols);
+        tc::k_reduce_y<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Y, Yp, n, N, Ncols, S);
         MG_LAUNCHED();
     }
 }
@@ -366,16 +414,11 @@ extern "C" int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* h, int nrhs, const floa
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         const int Ncols = 2 * nrhs;
         MG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-        {
-            dim3 g((Ncols / 2 + 31) / 32, (n + 31) / 32);
-            mg::tc::k_pack_bt<<<g, dim3(32, 8), 0, s>>>(reinterpret_cast<__nv_bfloat16*>(scratch),
-                                                       reinterpret_cast<const float2*>(x), n, nrhs, Ncols);
-            MG_LAUNCHED();
-        }
+        const int NT = (Ncols % 256 == 0) ? 256 : (Ncols % 128 == 0 ? 128 : 64);
+        mg::launch_pack(reinterpret_cast<__nv_bfloat16*>(scratch), reinterpret_cast<const float2*>(x), n, nrhs, Ncols,
+                        NT, s);
         const __nv_bfloat16* Bt = reinterpret_cast<const __nv_bfloat16*>(scratch);
-        if (Ncols % 256 == 0) mg::launch_tc<256>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
-        else if (Ncols % 128 == 0) mg::launch_tc<128>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
-        else mg::launch_tc<64>(y, L.Dinv16, Bt, n, 2 * n, Ncols, err, s);
+        mg::launch_tc(NT, y, L.Dinv16, Bt, n, 2 * n, Ncols, 1, err, s);
         int herr = 0;
         MG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
