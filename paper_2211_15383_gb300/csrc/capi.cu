@@ -347,7 +347,7 @@ int mgmlmc_get_term_deflation(mgmlmc_ctx* h, int term, int* k, double* lambda, d
     const long long n = c.lev[tl.a].n;
     if (k) *k = D.k;
     if (lambda)
-        for (int i = 0; i < D.k; ++i) lambda[i] = D.lambda[i];
+        for (int i = 0; i < D.k; ++i) lambda[i] = i < (int)D.lambda.size() ? D.lambda[i] : 0.0;
     if (L) download_block(c, L, D.Lv, n, D.k, "gd_tmp");
     if (R) download_block(c, R, D.Rv, n, D.k, "gd_tmp");
     if (tau) {
@@ -363,8 +363,9 @@ int mgmlmc_get_deflation(mgmlmc_ctx* h, double* lambda, double* sigma, double* U
     MG_REQUIRE(k > 0, MGMLMC_ESTATE, "get_deflation: no deflation computed");
     const long long n = c.lev[c.L - 1].n;
     for (int i = 0; i < k; ++i) {
-        if (lambda) lambda[i] = c.defl.lambda[i];
-        if (sigma) sigma[i] = std::fabs(c.defl.lambda[i]);
+        const double li = i < (int)c.defl.lambda.size() ? c.defl.lambda[i] : 0.0;
+        if (lambda) lambda[i] = li;
+        if (sigma) sigma[i] = std::fabs(li);
     }
     if (U) download_block(c, U, c.defl.Rv, n, k, "gd_tmp");
     if (V) download_block(c, V, c.defl.Lv, n, k, "gd_tmp");

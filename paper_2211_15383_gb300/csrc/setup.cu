@@ -237,10 +237,12 @@ static void coarsest_inverse(Ctx& c) {
     if (c.opt.mg_precision == 64) {
         if (!L.Dinv64) L.Dinv64 = c.alloc_n<double2>((size_t)n * n);
         MG_CUDA(cudaMemcpyAsync(L.Dinv64, Dd, sizeof(double2) * n * n, cudaMemcpyDeviceToDevice, c.stream));
+        ProfScope ps(c, "setup.gauss_jordan.f64", 2.0 * n * n * 16 * n, 8.0 * n * n * n);
         launch_gauss_jordan<double2>(L.Dinv64, (int)n, work, c.stream);
     } else {
         if (!L.Dinv32) L.Dinv32 = c.alloc_n<float2>((size_t)n * n);
         launch_convert<float2, double2>(L.Dinv32, Dd, n * n, c.stream);
+        ProfScope ps(c, "setup.gauss_jordan.f32", 2.0 * n * n * 8 * n, 8.0 * n * n * n);
         launch_gauss_jordan<float2>(L.Dinv32, (int)n, work, c.stream);
         if (tc_coarse_supported((int)n)) {
             if (!L.Dinv16) L.Dinv16 = c.alloc_n<__nv_bfloat16>((size_t)n * 2 * n);
@@ -267,6 +269,7 @@ static void rebuild_from(Ctx& c, int l0) {
                    "set_hierarchy: rank-deficient test vectors on an aggregate of level " + std::to_string(l + 1));
         launch_convert<float2, double2>(L.P32, L.P64, L.n * L.nvec, c.stream);
         double2* T = c.scratch<double2>("galerkin_T", galerkin_scratch_count(L.lx, L.lt, L.d, L.nvec));
+        ProfScope ps(c, "setup.galerkin", 0, 0);
         launch_galerkin(Lc.A64, L.A64, L.P64, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, T, c.stream);
         launch_convert<float2, double2>(Lc.A32, Lc.A64, (long long)Lc.nsites * 5 * Lc.d * Lc.d, c.stream);
     }
@@ -383,7 +386,10 @@ static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b)
         launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
         k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(G, b);
         small_launch_check();
-        launch_jacobi_eig(G, W, lam, b, 40, c.stream);
+        {
+            ProfScope ps(c, "setup.jacobi", 0, 0);
+            launch_jacobi_eig(G, W, lam, b, 40, c.stream);
+        }
         k_scale_cols_rsqrt<<<(b * b + 127) / 128, 128, 0, c.stream>>>(W, lam, b);
         small_launch_check();
         launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
@@ -433,7 +439,10 @@ void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool ine
         launch_gemm_hn<double2>(H, X, T, n, b, b, part, groups, c.stream);
         k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(H, b);
         small_launch_check();
-        launch_jacobi_eig(H, W, lam, b, 40, c.stream);
+        {
+            ProfScope ps(c, "setup.jacobi", 0, 0);
+            launch_jacobi_eig(H, W, lam, b, 40, c.stream);
+        }
         launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
         launch_gemm_nn<double2>(T2, T, W, (int)n, b, b, false, c.stream);
         std::swap(X, Y);
@@ -562,7 +571,10 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
         launch_gemm_hn<double2>(H, X, Y, n, nb, nb, part, groups, c.stream);
         k_hermitize<<<(nb * nb + 127) / 128, 128, 0, c.stream>>>(H, nb);
         small_launch_check();
-        launch_jacobi_eig(H, W, lam, nb, 40, c.stream, true);
+        {
+            ProfScope ps(c, "setup.jacobi", 0, 0);
+            launch_jacobi_eig(H, W, lam, nb, 40, c.stream, true);
+        }
         launch_gemm_nn<double2>(Xr, X, W, (int)n, nb, nb, false, c.stream);
         launch_gemm_nn<double2>(Yr, Y, W, (int)n, nb, nb, false, c.stream);
         k_resid_cols<<<(unsigned)((n * nb + 255) / 256), 256, 0, c.stream>>>(Y, Yr, Xr, lam, n, nb);
@@ -705,6 +717,7 @@ void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k) {
     D.tau_re = htau.x;
     D.tau_im = htau.y;
     D.inexact = true;
+    D.lambda.assign(k, 0.0);
 }
 
 }  // namespace mg
