@@ -102,6 +102,9 @@ size_t gauss_jordan_work_bytes(int n);
 // H is overwritten; W receives eigenvectors (columns), lam eigenvalues.
 void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s,
                        bool descending = false);
+// G (b x b, Hermitian positive definite) = R^H R; G is overwritten by R (upper),
+// Rinv = R^{-1}.  status[0] = 1 if G was not positive definite.
+void launch_cholesky_inv(double2* G, double2* Rinv, int b, int* status, cudaStream_t s);
 // BF16 real embedding [Re A | Im A] (n x 2n) of a complex FP32 n x n matrix for the
 // tensor-core coarsest solve.
 void launch_embed_bf16(__nv_bfloat16* E, const float2* A, int n, cudaStream_t s);

@@ -54,8 +54,58 @@ __global__ void __launch_bounds__(256) k_gemm_nn(C* __restrict__ Cm, const C* __
     }
 }
 
+// Narrow variant for few columns (the setup solves run 8 right-hand sides):
+// tile 128 x 8, thread (tx < 8 column, ty < 32 row lane) owns 4 rows.
+template <typename C>
+__global__ void __launch_bounds__(256) k_gemm_nn8(C* __restrict__ Cm, const C* __restrict__ A,
+                                                  const C* __restrict__ B, int M, int K, int Nc, bool accumulate) {
+    __shared__ C As[128][GK + 1];
+    __shared__ C Bs[GK][8];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 8 + tx;
+    const int row0 = blockIdx.y * 128, col0 = blockIdx.x * 8;
+    C acc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[r] = czero<C>();
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int e = tid; e < 128 * GK; e += 256) {
+            const int r = e / GK, k = e % GK;
+            const int gr = row0 + r, gk = k0 + k;
+            As[r][k] = (gr < M && gk < K) ? A[(long long)gr * K + gk] : czero<C>();
+        }
+        if (tid < GK * 8) {
+            const int k = tid / 8, c = tid % 8;
+            const int gk = k0 + k, gc = col0 + c;
+            Bs[k][c] = (gk < K && gc < Nc) ? B[(long long)gk * Nc + gc] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            const C bv = Bs[k][tx];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cfma(acc[r], As[ty * 4 + r][k], bv);
+        }
+        __syncthreads();
+    }
+    const int gc = col0 + tx;
+    if (gc >= Nc) return;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gr = row0 + ty * 4 + r;
+        if (gr < M) {
+            const long long idx = (long long)gr * Nc + gc;
+            Cm[idx] = accumulate ? cadd(Cm[idx], acc[r]) : acc[r];
+        }
+    }
+}
+
 template <typename C>
 void launch_gemm_nn(C* Cm, const C* A, const C* B, int M, int K, int Nc, bool accumulate, cudaStream_t s) {
+    if (Nc <= 8) {
+        dim3 g(1, (M + 127) / 128);
+        k_gemm_nn8<C><<<g, dim3(8, 32), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
+        MG_LAUNCHED();
+        return;
+    }
     dim3 g((Nc + GN - 1) / GN, (M + GM - 1) / GM);
     k_gemm_nn<C><<<g, dim3(32, 8), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
     MG_LAUNCHED();
@@ -364,6 +414,58 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double*
     }
     __syncthreads();
     for (int i = tid; i < b; i += nt) lam[i] = lcopy[i];
+}
+
+// Cholesky factor of a Hermitian positive definite b x b matrix G = R^H R (R upper,
+// right-looking outer-product form, in place in G), then Rinv = R^{-1} by
+// back-substitution, one column per thread.  One CTA; status[0] = 1 if a pivot is
+// not positive.
+__global__ void __launch_bounds__(1024) k_cholesky_inv(double2* G, double2* Rinv, int b, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < b; ++j) {
+        if (tid == 0) {
+            double d = G[j * b + j].x;
+            if (!(d > 0.0)) {
+                *status = 1;
+                d = 1e-300;
+            }
+            G[j * b + j] = make_double2(sqrt(d), 0.0);
+        }
+        __syncthreads();
+        const double inv = 1.0 / G[j * b + j].x;
+        for (int i = j + 1 + tid; i < b; i += nt) G[j * b + i] = make_double2(G[j * b + i].x * inv, G[j * b + i].y * inv);
+        __syncthreads();
+        const int m = b - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int p = j + 1 + e / m, q = j + 1 + e % m;
+            if (q < p) continue;
+            const double2 rp = G[j * b + p], rq = G[j * b + q];
+            // G[p][q] -= conj(R[j][p]) R[j][q]
+            G[p * b + q] = make_double2(G[p * b + q].x - (rp.x * rq.x + rp.y * rq.y),
+                                        G[p * b + q].y - (rp.x * rq.y - rp.y * rq.x));
+        }
+        __syncthreads();
+    }
+    // Rinv: solve R z = e_c for each column c (upper triangular back substitution)
+    for (int c = tid; c < b; c += nt) {
+        for (int i = b - 1; i >= 0; --i) {
+            double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            if (i > c) acc = make_double2(0.0, 0.0);
+            for (int k = i + 1; k <= c; ++k) {
+                const double2 r = G[i * b + k], z = Rinv[k * b + c];
+                acc.x -= r.x * z.x - r.y * z.y;
+                acc.y -= r.x * z.y + r.y * z.x;
+            }
+            const double d = G[i * b + i].x;
+            Rinv[i * b + c] = (i > c) ? make_double2(0.0, 0.0) : make_double2(acc.x / d, acc.y / d);
+        }
+    }
+}
+
+void launch_cholesky_inv(double2* G, double2* Rinv, int b, int* status, cudaStream_t s) {
+    MG_REQUIRE(b >= 1 && b <= 4096, MGMLMC_EINVAL, "cholesky: 1 <= b <= 4096");
+    k_cholesky_inv<<<1, 1024, 0, s>>>(G, Rinv, b, status);
+    MG_LAUNCHED();
 }
 
 void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s, bool descending) {

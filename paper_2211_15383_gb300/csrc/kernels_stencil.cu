@@ -225,6 +225,74 @@ __global__ void __launch_bounds__(128) k_block_stencil_d(C* __restrict__ y, cons
     }
 }
 
+// FP32 variant with two adjacent right-hand sides per thread: one 16-byte load
+// brings x for both, and every shared-memory read of the block serves two rhs.
+// Block = 128 threads = 256 rhs.  N must be even.
+template <int D, int MODE>
+__global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y, const float2* __restrict__ x,
+                                                          const float2* __restrict__ b, const float2* __restrict__ A,
+                                                          int lx, int lt, int N, double2* __restrict__ part) {
+    __shared__ float2 At[5 * D * D];
+    const int j = 2 * (blockIdx.x * 128 + threadIdx.x);
+    const int V = lx * lt;
+    float2 dyx0 = make_float2(0.f, 0.f), dyx1 = make_float2(0.f, 0.f);
+    float dyy0 = 0.f, dyy1 = 0.f;
+    for (int site = blockIdx.y; site < V; site += gridDim.y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 5 * D * D; e += 128) {
+            const int dir = e / (D * D), r = e % (D * D), c = r / D, bb = r % D;
+            At[(dir * D + bb) * D + c] = A[(long long)site * 5 * D * D + e];
+        }
+        __syncthreads();
+        if (j < N) {
+            float2 a0[D], a1[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) a0[c] = a1[c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int dir = 0; dir < 5; ++dir) {
+                const int nb = nbr_site(site, dir, lx, lt);
+                const float2* xn = x + (long long)nb * D * N + j;
+                const float2* Ad = At + dir * D * D;
+#pragma unroll 2
+                for (int bc = 0; bc < D; ++bc) {
+                    const float4 xv = *reinterpret_cast<const float4*>(xn + (long long)bc * N);
+                    const float2 x0 = make_float2(xv.x, xv.y), x1 = make_float2(xv.z, xv.w);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const float2 av = Ad[bc * D + c];
+                        cfma(a0[c], av, x0);
+                        cfma(a1[c], av, x1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const long long idx = ((long long)site * D + c) * N + j;
+                float2 o0 = a0[c], o1 = a1[c];
+                if (MODE == 1) {
+                    const float4 bv = *reinterpret_cast<const float4*>(b + idx);
+                    o0 = make_float2(bv.x - o0.x, bv.y - o0.y);
+                    o1 = make_float2(bv.z - o1.x, bv.w - o1.y);
+                }
+                *reinterpret_cast<float4*>(y + idx) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                if (MODE == 2) {
+                    const float4 xv = *reinterpret_cast<const float4*>(x + idx);
+                    cfmac(dyx0, o0, make_float2(xv.x, xv.y));
+                    cfmac(dyx1, o1, make_float2(xv.z, xv.w));
+                    dyy0 = fmaf(o0.x, o0.x, fmaf(o0.y, o0.y, dyy0));
+                    dyy1 = fmaf(o1.x, o1.x, fmaf(o1.y, o1.y, dyy1));
+                }
+            }
+        }
+    }
+    if (MODE == 2 && j < N) {
+        part[((long long)blockIdx.y * 2 + 0) * N + j] = to_d(dyx0);
+        part[((long long)blockIdx.y * 2 + 0) * N + j + 1] = to_d(dyx1);
+        part[((long long)blockIdx.y * 2 + 1) * N + j] = make_double2((double)dyy0, 0.0);
+        part[((long long)blockIdx.y * 2 + 1) * N + j + 1] = make_double2((double)dyy1, 0.0);
+    }
+}
+
 // xc[S][o] = sum_{site in S} sum_{a in spin block s(o)} conj(P[site][a][j(o)]) x[site][a]
 template <typename C>
 __global__ void k_restrict(C* __restrict__ xc, const C* __restrict__ x, const C* __restrict__ P, int lx, int lt,
@@ -432,9 +500,29 @@ static void bs_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt
     MG_LAUNCHED();
 }
 
+template <int D>
+static bool bsd_f2(float2* y, const float2* x, const float2* b, const float2* A, int lx, int lt, int N, int mode,
+                   double2* part, int groups, cudaStream_t s) {
+    if (N % 2 != 0) return false;
+    dim3 g((N / 2 + 127) / 128, groups);
+    switch (mode) {
+        case 0: k_block_stencil_f2<D, 0><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 1: k_block_stencil_f2<D, 1><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        default: k_block_stencil_f2<D, 2><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+    }
+    MG_LAUNCHED();
+    return true;
+}
+template <int D>
+static bool bsd_f2(double2*, const double2*, const double2*, const double2*, int, int, int, int, double2*, int,
+                   cudaStream_t) {
+    return false;
+}
+
 template <typename C, int D>
 static void bsd_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt, int N, int mode, double2* part,
                          int groups, cudaStream_t s) {
+    if (bsd_f2<D>(y, x, b, A, lx, lt, N, mode, part, groups, s)) return;
     dim3 g((N + 127) / 128, groups);
     switch (mode) {
         case 0: k_block_stencil_d<C, D, 0><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
@@ -444,8 +532,12 @@ static void bsd_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int l
     MG_LAUNCHED();
 }
 
+// The one-rhs-per-thread kernels need wide blocks; narrow blocks (the setup solves
+// run 8 rhs) take the generic 32-rhs-tile kernel.
+static bool use_site_kernel(int d, int N) { return (d == 8 || d == 16) && N >= 64; }
+
 int block_stencil_groups(int nsites, int d, int N) {
-    if (d == 8 || d == 16) {
+    if (use_site_kernel(d, N)) {
         const int tiles = (N + 127) / 128;
         int want = 16 * kNumSM / tiles;
         if (want < 1) want = 1;
@@ -460,8 +552,8 @@ template <typename C>
 void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N, int mode,
                           double2* part, int groups, cudaStream_t s) {
     MG_REQUIRE(d >= 2 && d <= 64, MGMLMC_EINVAL, "block stencil: 2 <= d <= 64");
-    if (d == 16) return bsd_dispatch<C, 16>(y, x, b, A, lx, lt, N, mode, part, groups, s);
-    if (d == 8) return bsd_dispatch<C, 8>(y, x, b, A, lx, lt, N, mode, part, groups, s);
+    if (use_site_kernel(d, N) && d == 16) return bsd_dispatch<C, 16>(y, x, b, A, lx, lt, N, mode, part, groups, s);
+    if (use_site_kernel(d, N) && d == 8) return bsd_dispatch<C, 8>(y, x, b, A, lx, lt, N, mode, part, groups, s);
     if (d <= 8) bs_dispatch<C, 1>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
     else if (d <= 16) bs_dispatch<C, 2>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);
     else if (d <= 32) bs_dispatch<C, 4>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);

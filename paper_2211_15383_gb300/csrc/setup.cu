@@ -224,6 +224,8 @@ static void small_launch_check() { MG_LAUNCHED(); }
 
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);   // solver.cu
 constexpr int kBootstrapRounds = 2;
+// Subspace iterations between Rayleigh-Ritz projections (and convergence checks).
+constexpr int kRayleighRitzEvery = 4;
 
 // ------------------------------------------------------------------ hierarchy
 static void coarsest_inverse(Ctx& c) {
@@ -376,13 +378,15 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
 }
 
 // ------------------------------------------------------------------ deflation
-static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
+// Loewdin orthonormalisation X <- X G^{-1/2} (G = X^H X via the Jacobi eigensolver),
+// twice: robust for nearly dependent columns, used as the fallback.
+static void orthonormalize_loewdin(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
     double2* G = c.scratch<double2>("df_G", (size_t)b * b);
     double2* W = c.scratch<double2>("df_W", (size_t)b * b);
     double* lam = c.scratch<double>("df_lamG", b);
     const int groups = gemm_hn_groups(n, b, b);
     double2* part = c.scratch<double2>("df_part", (size_t)groups * b * b);
-    for (int pass = 0; pass < 2; ++pass) {   // Loewdin orthonormalisation, twice
+    for (int pass = 0; pass < 2; ++pass) {
         launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
         k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(G, b);
         small_launch_check();
@@ -394,6 +398,35 @@ static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b)
         small_launch_check();
         launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
         std::swap(X, Y);
+    }
+}
+
+// CholQR2: X <- X R^{-1} with G = X^H X = R^H R, twice; falls back to the
+// Loewdin form if a Gram matrix is not numerically positive definite.
+static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
+    double2* G = c.scratch<double2>("df_G", (size_t)b * b);
+    double2* Ri = c.scratch<double2>("df_Ri", (size_t)b * b);
+    int* st = c.scratch<int>("df_st", 4);
+    const int groups = gemm_hn_groups(n, b, b);
+    double2* part = c.scratch<double2>("df_part", (size_t)groups * b * b);
+    double2* keep = c.scratch<double2>("df_Xkeep", (size_t)n * b);
+    MG_CUDA(cudaMemcpyAsync(keep, X, sizeof(double2) * n * b, cudaMemcpyDeviceToDevice, c.stream));
+    MG_CUDA(cudaMemsetAsync(st, 0, sizeof(int), c.stream));
+    for (int pass = 0; pass < 2; ++pass) {
+        launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
+        {
+            ProfScope ps(c, "setup.cholqr", 0, 0);
+            launch_cholesky_inv(G, Ri, b, st, c.stream);
+        }
+        launch_gemm_nn<double2>(Y, X, Ri, (int)n, b, b, false, c.stream);
+        std::swap(X, Y);
+    }
+    int hs = 0;
+    MG_CUDA(cudaMemcpyAsync(&hs, st, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (hs) {
+        MG_CUDA(cudaMemcpyAsync(X, keep, sizeof(double2) * n * b, cudaMemcpyDeviceToDevice, c.stream));
+        orthonormalize_loewdin(c, X, Y, n, b);
     }
 }
 
@@ -433,6 +466,7 @@ void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool ine
         MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "compute_deflation: coarsest solve did not converge");
         std::swap(X, Y);
         orthonormalize(c, X, Y, n, b);
+        if ((it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) continue;
         // Rayleigh-Ritz with Q = Gamma5 D
         apply_D<double2>(c, l, T, X, nullptr, b, 0, nullptr);
         launch_gamma5<double2>(T, T, L.nsites, L.d, b, c.stream);
@@ -567,6 +601,11 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
     bool conv = false;
     for (int it = 0; it < max_iters && !conv; ++it) {
         apply_J(c, a, b, X, Y, nb, eig_solve_tol);
+        if ((it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) {
+            std::swap(X, Y);               // X <- J X, orthonormalised
+            orthonormalize(c, X, Y, n, nb);
+            continue;
+        }
         // Rayleigh-Ritz on span(X): H = X^H J X, largest |lambda| first
         launch_gemm_hn<double2>(H, X, Y, n, nb, nb, part, groups, c.stream);
         k_hermitize<<<(nb * nb + 127) / 128, 128, 0, c.stream>>>(H, nb);
