@@ -55,54 +55,45 @@ __global__ void __launch_bounds__(256) k_gemm_nn(C* __restrict__ Cm, const C* __
 }
 
 // Narrow variant for few columns (the setup solves run 8 right-hand sides):
-// tile 128 x 8, thread (tx < 8 column, ty < 32 row lane) owns 4 rows.
+// tile 16 x 8 so that a 4096-row product still spreads over 256 CTAs; thread
+// (tx < 8 column, ty < 16 row) owns one output.
 template <typename C>
-__global__ void __launch_bounds__(256) k_gemm_nn8(C* __restrict__ Cm, const C* __restrict__ A,
+__global__ void __launch_bounds__(128) k_gemm_nn8(C* __restrict__ Cm, const C* __restrict__ A,
                                                   const C* __restrict__ B, int M, int K, int Nc, bool accumulate) {
-    __shared__ C As[128][GK + 1];
-    __shared__ C Bs[GK][8];
+    constexpr int ROWS = 16, KT = 64;
+    __shared__ C As[ROWS][KT + 1];
+    __shared__ C Bs[KT][8];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 8 + tx;
-    const int row0 = blockIdx.y * 128, col0 = blockIdx.x * 8;
-    C acc[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r] = czero<C>();
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int e = tid; e < 128 * GK; e += 256) {
-            const int r = e / GK, k = e % GK;
+    const int row0 = blockIdx.y * ROWS, col0 = blockIdx.x * 8;
+    C acc = czero<C>();
+    for (int k0 = 0; k0 < K; k0 += KT) {
+        for (int e = tid; e < ROWS * KT; e += 128) {
+            const int r = e / KT, k = e % KT;
             const int gr = row0 + r, gk = k0 + k;
             As[r][k] = (gr < M && gk < K) ? A[(long long)gr * K + gk] : czero<C>();
         }
-        if (tid < GK * 8) {
-            const int k = tid / 8, c = tid % 8;
+        for (int e = tid; e < KT * 8; e += 128) {
+            const int k = e / 8, c = e % 8;
             const int gk = k0 + k, gc = col0 + c;
             Bs[k][c] = (gk < K && gc < Nc) ? B[(long long)gk * Nc + gc] : czero<C>();
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < GK; ++k) {
-            const C bv = Bs[k][tx];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) cfma(acc[r], As[ty * 4 + r][k], bv);
-        }
+#pragma unroll 8
+        for (int k = 0; k < KT; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
         __syncthreads();
     }
-    const int gc = col0 + tx;
-    if (gc >= Nc) return;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int gr = row0 + ty * 4 + r;
-        if (gr < M) {
-            const long long idx = (long long)gr * Nc + gc;
-            Cm[idx] = accumulate ? cadd(Cm[idx], acc[r]) : acc[r];
-        }
+    const int gc = col0 + tx, gr = row0 + ty;
+    if (gc < Nc && gr < M) {
+        const long long idx = (long long)gr * Nc + gc;
+        Cm[idx] = accumulate ? cadd(Cm[idx], acc) : acc;
     }
 }
 
 template <typename C>
 void launch_gemm_nn(C* Cm, const C* A, const C* B, int M, int K, int Nc, bool accumulate, cudaStream_t s) {
     if (Nc <= 8) {
-        dim3 g(1, (M + 127) / 128);
-        k_gemm_nn8<C><<<g, dim3(8, 32), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
+        dim3 g(1, (M + 15) / 16);
+        k_gemm_nn8<C><<<g, dim3(8, 16), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
         MG_LAUNCHED();
         return;
     }

@@ -293,6 +293,54 @@ __global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y
     }
 }
 
+// Narrow-block variant (few rhs, as in the setup solves): thread (tx < 8 rhs,
+// ty < D output row); the blocks of the site are staged in shared memory.
+template <typename C, int D, int MODE>
+__global__ void __launch_bounds__(8 * D) k_block_stencil_narrow(C* __restrict__ y, const C* __restrict__ x,
+                                                                const C* __restrict__ b, const C* __restrict__ A,
+                                                                int lx, int lt, int N, double2* __restrict__ part) {
+    using R = re_t<C>;
+    __shared__ C As[5 * D * D];
+    __shared__ double2 red[2][D][8];
+    const int tx = threadIdx.x, c = threadIdx.y, tid = c * 8 + tx;
+    const int j = blockIdx.x * 8 + tx;
+    const int V = lx * lt;
+    C dyx = czero<C>();
+    R dyy = 0;
+    for (int site = blockIdx.y; site < V; site += gridDim.y) {
+        __syncthreads();
+        for (int e = tid; e < 5 * D * D; e += 8 * D) As[e] = A[(long long)site * 5 * D * D + e];
+        __syncthreads();
+        if (j < N) {
+            C acc = czero<C>();
+            for (int dir = 0; dir < 5; ++dir) {
+                const int nb = nbr_site(site, dir, lx, lt);
+                const C* xn = x + (long long)nb * D * N + j;
+                const C* Ar = As + (dir * D + c) * D;
+#pragma unroll
+                for (int bc = 0; bc < D; ++bc) cfma(acc, Ar[bc], xn[(long long)bc * N]);
+            }
+            const long long idx = ((long long)site * D + c) * N + j;
+            if (MODE == 1) acc = csub(b[idx], acc);
+            y[idx] = acc;
+            if (MODE == 2) {
+                cfmac(dyx, acc, x[idx]);
+                dyy = fma(acc.x, acc.x, fma(acc.y, acc.y, dyy));
+            }
+        }
+    }
+    if (MODE == 2) {
+        red[0][c][tx] = to_d(dyx);
+        red[1][c][tx] = make_double2((double)dyy, 0.0);
+        __syncthreads();
+        if (c < 2 && j < N) {
+            double2 s2 = red[c][0][tx];
+            for (int r = 1; r < D; ++r) s2 = cadd(s2, red[c][r][tx]);
+            part[((long long)blockIdx.y * 2 + c) * N + j] = s2;
+        }
+    }
+}
+
 // xc[S][o] = sum_{site in S} sum_{a in spin block s(o)} conj(P[site][a][j(o)]) x[site][a]
 template <typename C>
 __global__ void k_restrict(C* __restrict__ xc, const C* __restrict__ x, const C* __restrict__ P, int lx, int lt,
@@ -535,8 +583,10 @@ static void bsd_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int l
 // The one-rhs-per-thread kernels need wide blocks; narrow blocks (the setup solves
 // run 8 rhs) take the generic 32-rhs-tile kernel.
 static bool use_site_kernel(int d, int N) { return (d == 8 || d == 16) && N >= 64; }
+static bool use_narrow_kernel(int d, int N) { return (d == 8 || d == 16) && N <= 16; }
 
 int block_stencil_groups(int nsites, int d, int N) {
+    if (use_narrow_kernel(d, N)) return nsites;
     if (use_site_kernel(d, N)) {
         const int tiles = (N + 127) / 128;
         int want = 16 * kNumSM / tiles;
@@ -552,6 +602,20 @@ template <typename C>
 void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N, int mode,
                           double2* part, int groups, cudaStream_t s) {
     MG_REQUIRE(d >= 2 && d <= 64, MGMLMC_EINVAL, "block stencil: 2 <= d <= 64");
+    if (use_narrow_kernel(d, N)) {
+        dim3 g((N + 7) / 8, groups);
+        if (d == 16) {
+            if (mode == 0) k_block_stencil_narrow<C, 16, 0><<<g, dim3(8, 16), 0, s>>>(y, x, b, A, lx, lt, N, part);
+            else if (mode == 1) k_block_stencil_narrow<C, 16, 1><<<g, dim3(8, 16), 0, s>>>(y, x, b, A, lx, lt, N, part);
+            else k_block_stencil_narrow<C, 16, 2><<<g, dim3(8, 16), 0, s>>>(y, x, b, A, lx, lt, N, part);
+        } else {
+            if (mode == 0) k_block_stencil_narrow<C, 8, 0><<<g, dim3(8, 8), 0, s>>>(y, x, b, A, lx, lt, N, part);
+            else if (mode == 1) k_block_stencil_narrow<C, 8, 1><<<g, dim3(8, 8), 0, s>>>(y, x, b, A, lx, lt, N, part);
+            else k_block_stencil_narrow<C, 8, 2><<<g, dim3(8, 8), 0, s>>>(y, x, b, A, lx, lt, N, part);
+        }
+        MG_LAUNCHED();
+        return;
+    }
     if (use_site_kernel(d, N) && d == 16) return bsd_dispatch<C, 16>(y, x, b, A, lx, lt, N, mode, part, groups, s);
     if (use_site_kernel(d, N) && d == 8) return bsd_dispatch<C, 8>(y, x, b, A, lx, lt, N, mode, part, groups, s);
     if (d <= 8) bs_dispatch<C, 1>(y, x, b, A, lx, lt, d, N, mode, part, groups, s);

@@ -40,14 +40,19 @@ void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, doubl
     const double bytes = vec * (mode == 1 ? 3 : 2) +
                          (l == 0 ? 2.0 * L.nsites * s : 5.0 * L.nsites * L.d * L.d * s);
     const double flops = (l == 0) ? 60.0 * L.nsites * N : 40.0 * L.d * L.d * (double)L.nsites * N;
-    ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), bytes, flops);
     double2* part = nullptr;
     if (mode == 2) part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
-    if (l == 0)
-        launch_wilson<C>(y, x, b, links<C>(c), c.m0, L.lx, L.lt, N, mode, part, groups, c.stream);
-    else
-        launch_block_stencil<C>(y, x, b, blocks<C>(L), L.lx, L.lt, L.d, N, mode, part, groups, c.stream);
-    if (mode == 2) launch_finalize(dots, part, groups, 2 * N, c.stream);
+    {
+        ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), bytes, flops);
+        if (l == 0)
+            launch_wilson<C>(y, x, b, links<C>(c), c.m0, L.lx, L.lt, N, mode, part, groups, c.stream);
+        else
+            launch_block_stencil<C>(y, x, b, blocks<C>(L), L.lx, L.lt, L.d, N, mode, part, groups, c.stream);
+    }
+    if (mode == 2) {
+        ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
+        launch_finalize(dots, part, groups, 2 * N, c.stream);
+    }
 }
 
 template <typename C>

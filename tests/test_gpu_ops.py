@@ -16,6 +16,7 @@ CASES = [
     (8, 8, ((2, 2), (2, 2)), (2, 2)),
     (16, 16, ((4, 4),), (4,)),
     (12, 8, ((2, 4), (3, 1)), (2, 3)),
+    (16, 8, ((4, 4),), (8,)),            # d = 16 on the coarse level
 ]
 
 
@@ -25,7 +26,7 @@ def pkg():
 
 
 @pytest.mark.parametrize("Lx,Lt,agg,nvec", CASES)
-@pytest.mark.parametrize("nrhs", [1, 3, 37])
+@pytest.mark.parametrize("nrhs", [1, 3, 37, 70])
 def test_operators_match_oracle(pkg, Lx, Lt, agg, nvec, nrhs):
     m0 = 0.05
     theta, sv = small_problem(Lx, Lt, agg=agg, nvec=nvec)
