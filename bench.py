@@ -2,11 +2,17 @@
 """Benchmark of deflated MG-MLMC on GB300: MG-MLMC samples/s on the 128x128
 Wilson-Schwinger workload (3-level multigrid, 4x4 then 2x2 aggregates, 8 test
 vectors per spin, 64 deflated triplets of the coarsest operator, 256 Z2
-vectors per level solved as one multi-RHS block to relative residual 1e-12).
+vectors per level solved as one multi-RHS block to FP64 relative residual 1e-12).
 
 One step = one block of 256 samples on every term of the telescoping sum
 (two multigrid-preconditioned solves per difference-level sample, one solve
 plus the deflation projections for the coarsest term, FP64 sample assembly).
+The headline run solves every block in FP64 by iterative refinement around an
+FP32 multigrid cycle with a BF16 tensor-core coarsest solve; the all-FP64
+path and the plain FP64 single-rhs path are measured beside it, with the
+per-sample difference of the two batched runs on the same noise.  The line
+also carries the time to tr(D^-1) at relative error 1e-4 (the paper's
+tolerance) and the fine stencil's HBM bandwidth.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -48,18 +54,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="schwinger-128x128")
-    ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
-                    help="multigrid precision of the headline run (the outer solve is FP64 in both)")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--precision", type=int, default=32, choices=[64, 32],
+                    help="multigrid precision of the headline run: 32 = FP32 multigrid + BF16 tensor-core "
+                         "coarsest solve inside FP64 iterative refinement; 64 = all-FP64 (the outer solve, "
+                         "its residuals and every sample are FP64 in both)")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the comparison run in the other precision and the single-rhs FP64 run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--ttt-tol", type=float, default=1e-2,
+    ap.add_argument("--ttt-tol", type=float, default=1e-4,
                     help="relative error of the time-to-trace run (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--block-rhs", type=int, default=0,
                     help="override the workload's right-hand sides per block (smaller ncu captures)")
     ap.add_argument("--nvtx", action="store_true",
                     help="mark the timed regions with NVTX ranges timed_f64 / timed_mixed / timed_e2e")
+    ap.add_argument("--single-rhs-samples", type=int, default=2,
+                    help="samples per term of the plain FP64 single-rhs comparison (0 = skip)")
     return ap.parse_args()
 
 
@@ -281,7 +292,11 @@ def gpu_arm(args, rank, ws, local):
     value = samples / sec
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": sec / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == 64 else "f64 outer / f32 multigrid",
+           "dtype": "f64" if args.precision == 64 else "f64+f32+bf16",
+           "precision": ("all FP64" if args.precision == 64 else
+                         "FP64 iterative refinement (FP64 residuals, solution updates and sample sums; every "
+                         "solve to relative residual 1e-12 in FP64) around an FP32 multigrid-preconditioned "
+                         "FGMRES cycle with a BF16 tensor-core coarsest solve"),
            "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, "
                    f"counter-based Z2 noise",
            "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "m0": w.m0, "beta": w.beta,
@@ -336,38 +351,59 @@ def gpu_arm(args, rank, ws, local):
                                 "trace": [res["trace"].real, res["trace"].imag], "rel_err": res["rel_err"],
                                 "converged": bool(res["converged"]),
                                 "samples_per_term": [t["nsamples"] for t in res["terms"]]}
-    # mixed precision on the same workload, error against the FP64 run
-    if not args.no_mixed and args.precision == 64:
-        ref = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+    # the other precision on the same workload (error of the mixed run against FP64 on the
+    # same noise), then the plain FP64 single-rhs path
+    if not args.no_mixed:
+        other = 64 if args.precision == 32 else 32
+        head_samples = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
         ctx.close()
         torch.cuda.empty_cache()
-        mctx, msetup = make_ctx(pkg, w, 32)
-        got = [mctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+        octx, osetup = make_ctx(pkg, w, other)
+        oth_samples = [octx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+        mixed_s, f64_s = (head_samples, oth_samples) if args.precision == 32 else (oth_samples, head_samples)
         errs = [float(np.max(np.abs(g - r) / np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2)))))
-                for g, r in zip(got, ref)]
-        run_steps(mctx, w, nterms, 0, W, seed)
-        mctx.profile(True, reset=True)
-        msec = timed_region(torch, ws, lambda: run_steps(mctx, w, nterms, W, K, seed),
-                            "timed_mixed" if args.nvtx else None)
-        mctx.profile(False)
-        mrep = mctx.profile_report()
-        mrep.pop("__launches__", None)
-        fine = {k: v for k, v in mrep.items() if k.startswith("D1.f32")}
-        stencil = None
-        if fine:
-            v = fine["D1.f32"]
-            stencil = {"kernel": "D1.f32 (fine Wilson stencil)", "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
-                       "frac_of_measured_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                       "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
-                       "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"]}
-        out["mixed"] = {"value": samples / msec, "unit": UNIT, "ms_per_step": msec / K * 1e3,
-                        "speedup_vs_f64": (samples / msec) / value, "setup": msetup,
-                        "max_rel_sample_error_vs_f64_per_term": errs,
-                        "roofline": roofline(mrep, peaks, fp64_peak, fp32_peak),
-                        "kernel_classes": class_summary(mrep), "stencil_hbm": stencil}
-        mctx.close()
+                for g, r in zip(mixed_s, f64_s)]
+        out["max_rel_sample_error_mixed_vs_f64_per_term"] = errs
+        run_steps(octx, w, nterms, 0, W, seed)
+        octx.profile(True, reset=True)
+        otag = "timed_f64" if other == 64 else "timed_mixed"
+        osec = timed_region(torch, ws, lambda: run_steps(octx, w, nterms, W, K, seed), otag if args.nvtx else None)
+        octx.profile(False)
+        orep = octx.profile_report()
+        orep.pop("__launches__", None)
+        key = "fp64" if other == 64 else "mixed"
+        out[key] = {"value": samples / osec, "unit": UNIT, "ms_per_step": osec / K * 1e3,
+                    "headline_speedup_over_this": value / (samples / osec), "setup": osetup,
+                    "roofline": roofline(orep, peaks, fp64_peak, fp32_peak),
+                    "kernel_classes": class_summary(orep)}
+        octx.close()
+        torch.cuda.empty_cache()
+        if args.single_rhs_samples > 0:
+            # plain FP64 single-rhs GPU path: same kernels, FP64 multigrid, one rhs per solve
+            sctx = pkg.Context(mg_precision=64, max_block_rhs=1)
+            sctx.set_gauge(w.gauge())
+            sctx.set_mass(w.m0)
+            sctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
+            sctx.compute_deflation(w.k, 1e-9, 400)
+            ns = args.single_rhs_samples
+            for t in range(nterms):
+                sctx.estimate_level(t, 10 ** 6, 1, seed, samples=False)
+            ssec = timed_region(torch, ws, lambda: [sctx.estimate_level(t, 0, ns, seed, samples=False)
+                                                      for t in range(nterms)])
+            out["plain_fp64_single_rhs"] = {"value": nterms * ns * ws / ssec, "unit": UNIT,
+                                            "samples_timed": nterms * ns,
+                                            "headline_speedup_over_this": value / (nterms * ns * ws / ssec)}
+            sctx.close()
     else:
         ctx.close()
+    fine = {k: v for k, v in report.items() if k.startswith("D1.f32")}
+    if fine:
+        v = fine["D1.f32"]
+        out["stencil_hbm"] = {"kernel": "D1.f32 (fine Wilson stencil, FP32)",
+                              "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                              "frac_of_measured_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                              "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
+                              "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"]}
     return out, w
 
 

@@ -588,8 +588,9 @@ static bool use_narrow_kernel(int d, int N) { return (d == 8 || d == 16) && N <=
 int block_stencil_groups(int nsites, int d, int N) {
     if (use_narrow_kernel(d, N)) return nsites;
     if (use_site_kernel(d, N)) {
+        // about 4 resident CTAs per SM (and as many partial sums for the MR dots)
         const int tiles = (N + 127) / 128;
-        int want = 16 * kNumSM / tiles;
+        int want = 4 * kNumSM / tiles;
         if (want < 1) want = 1;
         return nsites < want ? nsites : want;
     }

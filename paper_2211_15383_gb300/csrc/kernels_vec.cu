@@ -187,8 +187,8 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
     }
 }
 
-// Partials reduction: block (32 outputs, 16 group lanes); lane ty adds groups
-// ty, ty+16, ... in order, then a fixed-order sum over the 16 lanes, so the result
+// Partials reduction: block (32 outputs, 32 group lanes); lane ty adds groups
+// ty, ty+32, ... in order, then a fixed-order sum over the 32 lanes, so the result
 // does not depend on timing (deterministic).
 template <typename T>
 __device__ __forceinline__ T zero_of();
@@ -198,21 +198,21 @@ __device__ __forceinline__ double add_of(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add_of(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_finalize(T* __restrict__ out, const T* __restrict__ part, int groups,
-                                                  int count) {
-    __shared__ T sh[16][33];
+__global__ void __launch_bounds__(1024) k_finalize(T* __restrict__ out, const T* __restrict__ part, int groups,
+                                                   int count) {
+    __shared__ T sh[32][33];
     const int j = blockIdx.x * 32 + threadIdx.x;
     T acc = zero_of<T>();
     if (j < count) {
         int g = threadIdx.y;
-#pragma unroll 4
-        for (; g < groups; g += 16) acc = add_of(acc, part[(long long)g * count + j]);
+#pragma unroll 8
+        for (; g < groups; g += 32) acc = add_of(acc, part[(long long)g * count + j]);
     }
     sh[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.y == 0 && j < count) {
         T s = sh[0][threadIdx.x];
-        for (int r = 1; r < 16; ++r) s = add_of(s, sh[r][threadIdx.x]);
+        for (int r = 1; r < 32; ++r) s = add_of(s, sh[r][threadIdx.x]);
         out[j] = s;
     }
 }
@@ -261,11 +261,11 @@ void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sig
 int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
 
 void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s) {
-    k_finalize<double2><<<(count + 31) / 32, dim3(32, 16), 0, s>>>(out, part, groups, count);
+    k_finalize<double2><<<(count + 31) / 32, dim3(32, 32), 0, s>>>(out, part, groups, count);
     MG_LAUNCHED();
 }
 void launch_finalize(double* out, const double* part, int groups, int count, cudaStream_t s) {
-    k_finalize<double><<<(count + 31) / 32, dim3(32, 16), 0, s>>>(out, part, groups, count);
+    k_finalize<double><<<(count + 31) / 32, dim3(32, 32), 0, s>>>(out, part, groups, count);
     MG_LAUNCHED();
 }
 
