@@ -20,6 +20,12 @@ struct Level {
     // Galerkin product; the fine solve uses the link-based Wilson kernel)
     double2* A64 = nullptr;
     float2* A32 = nullptr;
+    // block-Jacobi smoother (coarse levels above the coarsest): Minv[s] = A[s][0]^{-1},
+    // Ahat = block stencil of D M^{-1}
+    double2* Minv64 = nullptr;
+    float2* Minv32 = nullptr;
+    double2* Ahat64 = nullptr;
+    float2* Ahat32 = nullptr;
     // prolongation to the next level: [site][d][nvec]
     int ax = 0, at = 0, nvec = 0;
     double2* P64 = nullptr;

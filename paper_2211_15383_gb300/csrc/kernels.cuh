@@ -139,6 +139,16 @@ void launch_max_ratio(double* out, const double* resid, const double* bnorm, int
 void launch_deflation_correction(double2* s, const double2* A, const double2* B, const double* a, int k,
                                  int N, cudaStream_t s_);
 void launch_sample_stats(double* acc, const double2* samples, int N, cudaStream_t s);
+// Block-Jacobi smoother data: Minv[s] = A[s][0]^{-1} (work: nsites d^2 scratch) and the
+// block stencil Ahat of D M^{-1} (Ahat[s][dir] = A[s][dir] Minv[nbr(s,dir)]).
+void launch_block_diag_inverse(double2* Minv, double2* work, const double2* A, int nsites, int d, int* status,
+                               cudaStream_t s);
+void launch_precondition_blocks(double2* Ahat, const double2* A, const double2* Minv, int lx, int lt, int d,
+                                cudaStream_t s);
+// y[s] (+)= Minv[s] x[s] for every site (d x d complex blocks), N rhs.
+template <typename C>
+void launch_block_diag_apply(C* y, const C* x, const C* Minv, int nsites, int d, int N, bool accumulate,
+                             cudaStream_t s);
 // Dense [n][n] matrix of a 5-point block stencil (entries of coinciding neighbours add up).
 void launch_dense_from_blocks(double2* Dd, const double2* A, int lx, int lt, int d, cudaStream_t s);
 

@@ -357,3 +357,85 @@ void launch_dense_from_blocks(double2* Dd, const double2* A, int lx, int lt, int
     MG_LAUNCHED();
 }
 }  // namespace mg
+
+namespace mg {
+// Inverse of every site's self block A[s][0] (d x d complex, FP64), Gauss-Jordan
+// with partial pivoting in global memory, one thread per site.  status = 1 on a
+// zero pivot.
+__global__ void k_block_diag_inverse(double2* Minv, double2* work, const double2* A, int nsites, int d,
+                                     int* status) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsites) return;
+    double2* M = work + (long long)s * d * d;       // copy of the block, destroyed
+    double2* I = Minv + (long long)s * d * d;
+    const double2* B = A + (long long)s * 5 * d * d;  // dir 0
+    for (int e = 0; e < d * d; ++e) {
+        M[e] = B[e];
+        I[e] = make_double2((e / d) == (e % d) ? 1.0 : 0.0, 0.0);
+    }
+    for (int k = 0; k < d; ++k) {
+        int p = k;
+        double best = -1.0;
+        for (int i = k; i < d; ++i) {
+            const double m = M[i * d + k].x * M[i * d + k].x + M[i * d + k].y * M[i * d + k].y;
+            if (m > best) { best = m; p = i; }
+        }
+        if (!(best > 0.0)) { atomicExch(status, 1); return; }
+        if (p != k)
+            for (int c = 0; c < d; ++c) {
+                double2 t = M[k * d + c]; M[k * d + c] = M[p * d + c]; M[p * d + c] = t;
+                t = I[k * d + c]; I[k * d + c] = I[p * d + c]; I[p * d + c] = t;
+            }
+        const double2 pv = M[k * d + k];
+        const double den = pv.x * pv.x + pv.y * pv.y;
+        const double2 inv = make_double2(pv.x / den, -pv.y / den);
+        for (int c = 0; c < d; ++c) {
+            M[k * d + c] = cmul(M[k * d + c], inv);
+            I[k * d + c] = cmul(I[k * d + c], inv);
+        }
+        for (int i = 0; i < d; ++i) {
+            if (i == k) continue;
+            const double2 f = M[i * d + k];
+            for (int c = 0; c < d; ++c) {
+                M[i * d + c] = csub(M[i * d + c], cmul(f, M[k * d + c]));
+                I[i * d + c] = csub(I[i * d + c], cmul(f, I[k * d + c]));
+            }
+        }
+    }
+}
+
+// Ahat[s][dir] = A[s][dir] Minv[nbr(s, dir)]: the block stencil of D M^{-1}.
+__global__ void k_precondition_blocks(double2* Ahat, const double2* A, const double2* Minv, int lx, int lt, int d) {
+    const long long total = (long long)lx * lt * 5 * d * d;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int cb = (int)(e % d), c = (int)((e / d) % d), dir = (int)((e / ((long long)d * d)) % 5);
+    const int site = (int)(e / (5LL * d * d));
+    const int xx = site % lx, t = site / lx;
+    int nb;
+    switch (dir) {
+        case 1: nb = (xx + 1 == lx ? 0 : xx + 1) + lx * t; break;
+        case 2: nb = (xx == 0 ? lx - 1 : xx - 1) + lx * t; break;
+        case 3: nb = xx + lx * (t + 1 == lt ? 0 : t + 1); break;
+        case 4: nb = xx + lx * (t == 0 ? lt - 1 : t - 1); break;
+        default: nb = site;
+    }
+    const double2* Ar = A + (((long long)site * 5 + dir) * d + c) * d;
+    const double2* Mn = Minv + (long long)nb * d * d;
+    double2 acc = make_double2(0, 0);
+    for (int b = 0; b < d; ++b) cfma(acc, Ar[b], Mn[b * d + cb]);
+    Ahat[e] = acc;
+}
+
+void launch_block_diag_inverse(double2* Minv, double2* work, const double2* A, int nsites, int d, int* status,
+                               cudaStream_t s) {
+    k_block_diag_inverse<<<(nsites + 63) / 64, 64, 0, s>>>(Minv, work, A, nsites, d, status);
+    MG_LAUNCHED();
+}
+void launch_precondition_blocks(double2* Ahat, const double2* A, const double2* Minv, int lx, int lt, int d,
+                                cudaStream_t s) {
+    const long long total = (long long)lx * lt * 5 * d * d;
+    k_precondition_blocks<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ahat, A, Minv, lx, lt, d);
+    MG_LAUNCHED();
+}
+}  // namespace mg

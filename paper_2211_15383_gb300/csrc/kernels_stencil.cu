@@ -341,6 +341,41 @@ __global__ void __launch_bounds__(8 * D) k_block_stencil_narrow(C* __restrict__ 
     }
 }
 
+// y[s] (+)= Minv[s] x[s]: block = 128 rhs, one site per iteration, Minv[s] in
+// shared memory; generic d (<= 32).
+template <typename C>
+__global__ void __launch_bounds__(128) k_block_diag_apply(C* __restrict__ y, const C* __restrict__ x,
+                                                          const C* __restrict__ Minv, int nsites, int d, int N,
+                                                          bool accumulate) {
+    __shared__ C Ms[32 * 32];
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    for (int site = blockIdx.y; site < nsites; site += gridDim.y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < d * d; e += 128) Ms[e] = Minv[(long long)site * d * d + e];
+        __syncthreads();
+        if (j >= N) continue;
+        C xv[32];
+        for (int b = 0; b < d; ++b) xv[b] = x[((long long)site * d + b) * N + j];
+        for (int c = 0; c < d; ++c) {
+            C acc = accumulate ? y[((long long)site * d + c) * N + j] : czero<C>();
+            for (int b = 0; b < d; ++b) cfma(acc, Ms[c * d + b], xv[b]);
+            y[((long long)site * d + c) * N + j] = acc;
+        }
+    }
+}
+
+template <typename C>
+void launch_block_diag_apply(C* y, const C* x, const C* Minv, int nsites, int d, int N, bool accumulate,
+                             cudaStream_t s) {
+    MG_REQUIRE(d <= 32, MGMLMC_EINVAL, "block-diagonal apply: d <= 32");
+    const int tiles = (N + 127) / 128;
+    int G = 16 * kNumSM / tiles;
+    if (G > nsites) G = nsites;
+    if (G < 1) G = 1;
+    k_block_diag_apply<C><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, d, N, accumulate);
+    MG_LAUNCHED();
+}
+
 // xc[S][o] = sum_{site in S} sum_{a in spin block s(o)} conj(P[site][a][j(o)]) x[site][a]
 template <typename C>
 __global__ void k_restrict(C* __restrict__ xc, const C* __restrict__ x, const C* __restrict__ P, int lx, int lt,
@@ -588,9 +623,10 @@ static bool use_narrow_kernel(int d, int N) { return (d == 8 || d == 16) && N <=
 int block_stencil_groups(int nsites, int d, int N) {
     if (use_narrow_kernel(d, N)) return nsites;
     if (use_site_kernel(d, N)) {
-        // about 4 resident CTAs per SM (and as many partial sums for the MR dots)
+        // one site per CTA up to 16 CTAs per SM: staging and compute of different
+        // sites overlap across CTAs
         const int tiles = (N + 127) / 128;
-        int want = 4 * kNumSM / tiles;
+        int want = 16 * kNumSM / tiles;
         if (want < 1) want = 1;
         return nsites < want ? nsites : want;
     }
@@ -698,7 +734,8 @@ void launch_gamma5(C* y, const C* x, long long nsites, int d, int N, cudaStream_
                                     cudaStream_t);                                                      \
     template void launch_mr_update<C>(C*, C*, const C*, const double2*, long long, int, bool,           \
                                       cudaStream_t);                                                    \
-    template void launch_gamma5<C>(C*, const C*, long long, int, int, cudaStream_t);
+    template void launch_gamma5<C>(C*, const C*, long long, int, int, cudaStream_t);                  \
+    template void launch_block_diag_apply<C>(C*, const C*, const C*, int, int, int, bool, cudaStream_t);
 INST(double2)
 INST(float2)
 

@@ -89,6 +89,7 @@ void Ctx::free_hierarchy() {
     for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) {
         Level& L = lev[l];
         dev_free(L.A64); dev_free(L.A32); dev_free(L.P64); dev_free(L.P32); dev_free(L.tv);
+        dev_free(L.Minv64); dev_free(L.Minv32); dev_free(L.Ahat64); dev_free(L.Ahat32);
         dev_free(L.Dinv64); dev_free(L.Dinv32); dev_free(L.Dinv16);
         L = Level();
     }
@@ -257,6 +258,30 @@ static void coarsest_inverse(Ctx& c) {
     MG_REQUIRE(hs == 0, MGMLMC_EINVAL, "coarsest operator is singular (zero pivot)");
 }
 
+// Block-Jacobi smoother of coarse level l: M = block diagonal of D_l (the self
+// blocks), smoothing on the right-preconditioned operator D_l M^{-1}.
+static void block_jacobi_setup(Ctx& c, int l) {
+    Level& L = c.lev[l];
+    const size_t nb = (size_t)L.nsites * L.d * L.d;
+    if (!L.Minv64) {
+        L.Minv64 = c.alloc_n<double2>(nb);
+        L.Minv32 = c.alloc_n<float2>(nb);
+        L.Ahat64 = c.alloc_n<double2>(nb * 5);
+        L.Ahat32 = c.alloc_n<float2>(nb * 5);
+    }
+    int* status = c.scratch<int>("status_bj", 4);
+    double2* work = c.scratch<double2>("bj_work", nb);
+    MG_CUDA(cudaMemsetAsync(status, 0, sizeof(int), c.stream));
+    launch_block_diag_inverse(L.Minv64, work, L.A64, L.nsites, L.d, status, c.stream);
+    launch_precondition_blocks(L.Ahat64, L.A64, L.Minv64, L.lx, L.lt, L.d, c.stream);
+    launch_convert<float2, double2>(L.Minv32, L.Minv64, (long long)nb, c.stream);
+    launch_convert<float2, double2>(L.Ahat32, L.Ahat64, (long long)nb * 5, c.stream);
+    int hs = 0;
+    MG_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    MG_REQUIRE(hs == 0, MGMLMC_EINVAL, "set_hierarchy: singular diagonal block on level " + std::to_string(l + 1));
+}
+
 static void rebuild_from(Ctx& c, int l0) {
     int* status = c.scratch<int>("status", 4);
     for (int l = l0; l < c.L - 1; ++l) {
@@ -274,6 +299,7 @@ static void rebuild_from(Ctx& c, int l0) {
         ProfScope ps(c, "setup.galerkin", 0, 0);
         launch_galerkin(Lc.A64, L.A64, L.P64, L.lx, L.lt, L.d, L.ax, L.at, L.nvec, T, c.stream);
         launch_convert<float2, double2>(Lc.A32, Lc.A64, (long long)Lc.nsites * 5 * Lc.d * Lc.d, c.stream);
+        if (l + 1 < c.L - 1) block_jacobi_setup(c, l + 1);
     }
     coarsest_inverse(c);
 }

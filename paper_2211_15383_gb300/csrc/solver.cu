@@ -19,6 +19,12 @@ template <> const float2* links<float2>(Ctx& c) { return c.U32; }
 template <typename C> static const C* blocks(const Level& L);
 template <> const double2* blocks<double2>(const Level& L) { return L.A64; }
 template <> const float2* blocks<float2>(const Level& L) { return L.A32; }
+template <typename C> static const C* hat_blocks(const Level& L);
+template <> const double2* hat_blocks<double2>(const Level& L) { return L.Ahat64; }
+template <> const float2* hat_blocks<float2>(const Level& L) { return L.Ahat32; }
+template <typename C> static const C* minv(const Level& L);
+template <> const double2* minv<double2>(const Level& L) { return L.Minv64; }
+template <> const float2* minv<float2>(const Level& L) { return L.Minv32; }
 template <typename C> static const C* prol(const Level& L);
 template <> const double2* prol<double2>(const Level& L) { return L.P64; }
 template <> const float2* prol<float2>(const Level& L) { return L.P32; }
@@ -53,6 +59,23 @@ void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, doubl
         ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
         launch_finalize(dots, part, groups, 2 * N, c.stream);
     }
+}
+
+// y = (D_l M_l^{-1}) x with the precomputed block stencil (block-Jacobi smoother).
+template <typename C>
+static void apply_Dhat(Ctx& c, int l, C* y, const C* x, int N, double2* dots) {
+    const Level& L = c.lev[l];
+    const int groups = block_stencil_groups(L.nsites, L.d, N);
+    const double s = sizeof(C);
+    double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
+    {
+        ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
+                     (double)L.n * N * s * 2 + 5.0 * L.nsites * L.d * L.d * s,
+                     40.0 * L.d * L.d * (double)L.nsites * N);
+        launch_block_stencil<C>(y, x, nullptr, hat_blocks<C>(L), L.lx, L.lt, L.d, N, 2, part, groups, c.stream);
+    }
+    ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
+    launch_finalize(dots, part, groups, 2 * N, c.stream);
 }
 
 template <typename C>
@@ -107,6 +130,23 @@ static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero) {
     const Level& L = c.lev[l];
     C* p = c.scratch<C>(nm("mr_p", l, sizeof(C)), (size_t)L.n * N);
     double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(C)), 2 * (size_t)N);
+    if (hat_blocks<C>(L)) {
+        // block-Jacobi MR: minimal residual steps on D M^{-1} (y accumulates the
+        // preconditioned correction), then e += M^{-1} y
+        C* yh = c.scratch<C>(nm("mr_y", l, sizeof(C)), (size_t)L.n * N);
+        for (int s = 0; s < nu; ++s) {
+            apply_Dhat<C>(c, l, p, r, N, dots);
+            ProfScope ps(c, "mr" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), 5.0 * L.n * N * sizeof(C),
+                         16.0 * L.n * N);
+            launch_mr_update<C>(yh, r, p, dots, L.n, N, s == 0, c.stream);
+        }
+        if (nu > 0) {
+            ProfScope ps(c, "bjac" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
+                         3.0 * L.n * N * sizeof(C), 8.0 * L.d * (double)L.n * N);
+            launch_block_diag_apply<C>(e, yh, minv<C>(L), L.nsites, L.d, N, !e_zero, c.stream);
+        }
+        return;
+    }
     for (int s = 0; s < nu; ++s) {
         apply_D<C>(c, l, p, r, nullptr, N, 2, dots);
         ProfScope ps(c, "mr" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), 5.0 * L.n * N * sizeof(C),
