@@ -81,11 +81,13 @@ struct Profiler {
 };
 
 struct Ctx;
-// Brackets the launches issued during its lifetime with events (when enabled).
+// Brackets the launches issued during its lifetime with events (when enabled);
+// the entry joins the profiler's pending list only once both events are
+// recorded, so a synchronisation inside the scope is harmless.
 struct ProfScope {
     Ctx* c;
-    size_t idx;
     bool active;
+    Profiler::Pending p;
     ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops);
     ~ProfScope();
 };

@@ -51,11 +51,14 @@ void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign,
 // Sum of partials: out[j] = sum_g part[g][j] (count = values per group).
 void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s);
 void launch_finalize(double* out, const double* part, int groups, int count, cudaStream_t s);
+// Row-major partials (the stencils' minimal-residual dots): out[i] = sum_g part[i * groups + g].
+void launch_finalize_rows(double2* out, const double2* part, int groups, int count, cudaStream_t s);
 
 // --------------------------------------------------------------- stencils
 // Fine Wilson-Schwinger operator (2 spins, U(1) links U[site][mu]).
 //  mode 0: y = D x;  mode 1: y = b - D x;
-//  mode 2: y = D x and part[g][0][j] = <y, x>_j, part[g][1][j] = <y, y>_j (MR smoother)
+//  mode 2: y = D x and part[0][j][g] = <y, x>_j, part[1][j][g] = <y, y>_j (MR smoother;
+//          row-major in the group index g = blockIdx.y, see launch_finalize_rows)
 template <typename C>
 void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N,
                    int mode, double2* part, int groups, cudaStream_t s);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_wilson(C* __restrict__ y, const C* __re
         if (threadIdx.y < 2 && j < N) {
             double2 s = sh[threadIdx.y][0][threadIdx.x];
             for (int r = 1; r < kRowLanes; ++r) s = cadd(s, sh[threadIdx.y][r][threadIdx.x]);
-            part[((long long)blockIdx.y * 2 + threadIdx.y) * N + j] = s;
+            part[((long long)threadIdx.y * N + j) * gridDim.y + blockIdx.y] = s;
         }
     }
 }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_block_stencil(C* __restrict__ y, const 
             double2 s = sh[(threadIdx.y * kRowLanes) * (kRhsTile + 1) + threadIdx.x];
             for (int r = 1; r < kRowLanes; ++r)
                 s = cadd(s, sh[(threadIdx.y * kRowLanes + r) * (kRhsTile + 1) + threadIdx.x]);
-            part[((long long)blockIdx.y * 2 + threadIdx.y) * N + j] = s;
+            part[((long long)threadIdx.y * N + j) * gridDim.y + blockIdx.y] = s;
         }
     }
 }
@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(128) k_block_stencil_d(C* __restrict__ y, cons
     if (MODE == 2) {
         // per-rhs partials: one thread per rhs, no cross-thread reduction needed
         if (j < N) {
-            part[((long long)blockIdx.y * 2 + 0) * N + j] = to_d(dyx);
-            part[((long long)blockIdx.y * 2 + 1) * N + j] = make_double2((double)dyy, 0.0);
+            part[((long long)0 * N + j) * gridDim.y + blockIdx.y] = to_d(dyx);
+            part[((long long)1 * N + j) * gridDim.y + blockIdx.y] = make_double2((double)dyy, 0.0);
         }
     }
 }
@@ -286,10 +286,11 @@ __global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y
         }
     }
     if (MODE == 2 && j < N) {
-        part[((long long)blockIdx.y * 2 + 0) * N + j] = to_d(dyx0);
-        part[((long long)blockIdx.y * 2 + 0) * N + j + 1] = to_d(dyx1);
-        part[((long long)blockIdx.y * 2 + 1) * N + j] = make_double2((double)dyy0, 0.0);
-        part[((long long)blockIdx.y * 2 + 1) * N + j + 1] = make_double2((double)dyy1, 0.0);
+        const long long G = gridDim.y;
+        part[((long long)0 * N + j) * G + blockIdx.y] = to_d(dyx0);
+        part[((long long)0 * N + j + 1) * G + blockIdx.y] = to_d(dyx1);
+        part[((long long)1 * N + j) * G + blockIdx.y] = make_double2((double)dyy0, 0.0);
+        part[((long long)1 * N + j + 1) * G + blockIdx.y] = make_double2((double)dyy1, 0.0);
     }
 }
 
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(8 * D) k_block_stencil_narrow(C* __restrict__ 
         if (c < 2 && j < N) {
             double2 s2 = red[c][0][tx];
             for (int r = 1; r < D; ++r) s2 = cadd(s2, red[c][r][tx]);
-            part[((long long)blockIdx.y * 2 + c) * N + j] = s2;
+            part[((long long)c * N + j) * gridDim.y + blockIdx.y] = s2;
         }
     }
 }

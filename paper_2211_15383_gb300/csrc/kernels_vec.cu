@@ -260,6 +260,28 @@ void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sig
 
 int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
 
+// Row-major partials: out[i] = sum_g part[i * groups + g]; one warp per output,
+// lanes add g = lane, lane + 32, ... in order, then a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_finalize_rows(double2* __restrict__ out, const double2* __restrict__ part,
+                                                       int groups, int count) {
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= count) return;
+    const double2* row = part + (long long)i * groups;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int g = lane; g < groups; g += 32) acc = cadd(acc, row[g]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) out[i] = acc;
+}
+
+void launch_finalize_rows(double2* out, const double2* part, int groups, int count, cudaStream_t s) {
+    k_finalize_rows<<<(count + 7) / 8, 256, 0, s>>>(out, part, groups, count);
+    MG_LAUNCHED();
+}
+
 void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s) {
     k_finalize<double2><<<(count + 31) / 32, dim3(32, 32), 0, s>>>(out, part, groups, count);
     MG_LAUNCHED();

@@ -146,15 +146,15 @@ Profiler::~Profiler() {
     for (auto e : pool) cudaEventDestroy(e);
 }
 ProfScope::ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops)
-    : c(&ctx), idx(0), active(ctx.prof.on) {
+    : c(&ctx), active(ctx.prof.on) {
     if (!active) return;
-    Profiler::Pending p{key, c->prof.take(), c->prof.take(), bytes, flops};
+    p = Profiler::Pending{key, c->prof.take(), c->prof.take(), bytes, flops};
     MG_CUDA(cudaEventRecord(p.a, c->stream));
-    c->prof.pending.push_back(p);
-    idx = c->prof.pending.size() - 1;
 }
 ProfScope::~ProfScope() {
-    if (active) cudaEventRecord(c->prof.pending[idx].b, c->stream);
+    if (!active) return;
+    cudaEventRecord(p.b, c->stream);
+    c->prof.pending.push_back(p);
 }
 
 // ------------------------------------------------------------------ gauge
