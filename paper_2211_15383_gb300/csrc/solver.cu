@@ -35,8 +35,41 @@ static std::string nm(const char* base, int l, size_t sz) {
 
 static const char* prec_tag(size_t sz) { return sz == sizeof(double2) ? "f64" : "f32"; }
 
+// On the first coarse level D_2 = P_1^H D_1 P_1 (the Galerkin product); in FP64,
+// where the pipe issues 2 FMA per SM and clock, restrict(Wilson(prolong(x))) can be
+// cheaper than the 5-point stencil with dense d x d blocks.
+static bool galerkin_form_cheaper(const Ctx& c, int l) {
+    if (l != 1) return false;
+    const Level& F = c.lev[0];
+    const Level& Cl = c.lev[1];
+    const double galerkin = 16.0 * F.nvec * F.n + 60.0 * F.nsites;   // prolong + restrict + Wilson
+    const double direct = 40.0 * Cl.d * Cl.d * Cl.nsites;            // 5 blocks of d x d per site
+    return galerkin < direct;
+}
+
+template <typename C> static bool galerkin_apply(Ctx&, C*, const C*, const C*, int, int) { return false; }
+template <> bool galerkin_apply<double2>(Ctx& c, double2* y, const double2* x, const double2* b, int N, int mode) {
+    if (mode == 2 || !galerkin_form_cheaper(c, 1)) return false;
+    const Level& F = c.lev[0];
+    const Level& Cl = c.lev[1];
+    double2* t = c.scratch<double2>("gal64_t", (size_t)F.n * N);
+    double2* u = c.scratch<double2>("gal64_u", (size_t)F.n * N);
+    apply_prolong<double2>(c, 0, t, x, N, false);
+    apply_D<double2>(c, 0, u, t, nullptr, N, 0, nullptr);
+    if (mode == 0) {
+        apply_restrict<double2>(c, 0, y, u, N);
+        return true;
+    }
+    double2* v = c.scratch<double2>("gal64_v", (size_t)Cl.n * N);
+    apply_restrict<double2>(c, 0, v, u, N);
+    MG_CUDA(cudaMemcpyAsync(y, b, sizeof(double2) * Cl.n * N, cudaMemcpyDeviceToDevice, c.stream));
+    launch_axpy_rhs<double2, double2>(y, nullptr, nullptr, -1.0, v, Cl.n, N, c.stream);
+    return true;
+}
+
 template <typename C>
 void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, double2* dots) {
+    if (l == 1 && galerkin_apply<C>(c, y, x, b, N, mode)) return;
     const Level& L = c.lev[l];
     const int groups = (l == 0) ? stencil_groups(L.nsites, N) : block_stencil_groups(L.nsites, L.d, N);
     // algorithmic traffic: read x once, write y once (+ b for the residual form),
