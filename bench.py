@@ -54,10 +54,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="schwinger-128x128")
-    ap.add_argument("--precision", type=int, default=32, choices=[64, 32],
+    ap.add_argument("--precision", type=int, default=32, choices=[64, 32, 16],
                     help="multigrid precision of the headline run: 32 = FP32 multigrid + BF16 tensor-core "
-                         "coarsest solve inside FP64 iterative refinement; 64 = all-FP64 (the outer solve, "
-                         "its residuals and every sample are FP64 in both)")
+                         "coarsest solve inside FP64 iterative refinement; 16 = as 32 with the coarse "
+                         "smoother's block stencil on the tensor cores in BF16; 64 = all-FP64 (the outer "
+                         "solve, its residuals and every sample are FP64 in all three)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the comparison run in the other precision and the single-rhs FP64 run")
     ap.add_argument("--no-e2e", action="store_true")
@@ -302,7 +303,8 @@ def gpu_arm(args, rank, ws, local):
            "precision": ("all FP64" if args.precision == 64 else
                          "FP64 iterative refinement (FP64 residuals, solution updates and sample sums; every "
                          "solve to relative residual 1e-12 in FP64) around an FP32 multigrid-preconditioned "
-                         "FGMRES cycle with a BF16 tensor-core coarsest solve"),
+                         "FGMRES cycle with a BF16 tensor-core coarsest solve" +
+                         (" and BF16 tensor-core coarse smoother stencils" if args.precision == 16 else "")),
            "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, "
                    f"counter-based Z2 noise",
            "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "m0": w.m0, "beta": w.beta,
@@ -359,13 +361,13 @@ def gpu_arm(args, rank, ws, local):
     # the other precision on the same workload (error of the mixed run against FP64 on the
     # same noise), then the plain FP64 single-rhs path
     if not args.no_mixed:
-        other = 64 if args.precision == 32 else 32
+        other = 64 if args.precision != 64 else 32
         head_samples = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
         ctx.close()
         torch.cuda.empty_cache()
         octx, osetup = make_ctx(pkg, w, other)
         oth_samples = [octx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
-        mixed_s, f64_s = (head_samples, oth_samples) if args.precision == 32 else (oth_samples, head_samples)
+        mixed_s, f64_s = (head_samples, oth_samples) if args.precision != 64 else (oth_samples, head_samples)
         errs = [float(np.max(np.abs(g - r) / np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2)))))
                 for g, r in zip(mixed_s, f64_s)]
         out["max_rel_sample_error_mixed_vs_f64_per_term"] = errs

@@ -54,8 +54,10 @@ typedef void (*mgmlmc_free_fn)(void* user, void* ptr);
 typedef struct {
     int mg_precision;     /* 64: FP64 multigrid preconditioner ("plain FP64 path");
                              32: FP32 V-cycle with a BF16 tensor-core coarsest solve
-                             (mixed).  The outer FGMRES, its residuals and every sample
-                             are FP64 in both cases.                          [64]    */
+                             (mixed); 16: as 32, and the coarse-level smoother's
+                             block stencil (d = 16) on the tensor cores in BF16.
+                             The outer FGMRES, its residuals and every sample are
+                             FP64 in all cases.                                [64]    */
     double solve_tol;     /* relative residual ||b - D x|| / ||b|| of every solve;
                              Sect. 4.3 uses 1e-12.                             [1e-12] */
     int fgmres_restart;   /* Krylov basis size m of the outer FGMRES(m).       [24]    */
@@ -94,7 +96,10 @@ typedef enum {
     MGMLMC_OP_P = 2,      /* y = P_l x     (level l+1 -> l)   (l = 1..L-1)         */
     MGMLMC_OP_G5 = 3,     /* y = Gamma5^l x                                         */
     MGMLMC_OP_PREC = 4,   /* y = one multigrid cycle from level l applied to x      */
-    MGMLMC_OP_DINV_C = 5  /* y = stored inverse of the coarsest D_L applied to x    */
+    MGMLMC_OP_DINV_C = 5, /* y = stored inverse of the coarsest D_L applied to x    */
+    MGMLMC_OP_SMOOTH = 6  /* y = D_l M_l^{-1} x, M_l the block diagonal (self blocks)
+                             of D_l: the operator the coarse-level smoother iterates
+                             on (l = 2..L-1; BF16 tensor cores when mg_precision = 16) */
 } mgmlmc_opkind;
 
 /* Fill *opt with the defaults shown in brackets above. */

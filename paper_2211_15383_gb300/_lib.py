@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmgmlmc.so")
 
 MAX_LEVELS = 6
-OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C = range(6)
+OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C, OP_SMOOTH = range(7)
 
 STATUS = {0: "MGMLMC_OK", -1: "MGMLMC_EINVAL", -2: "MGMLMC_ENOMEM", -3: "MGMLMC_ENOTCONVERGED",
           -4: "MGMLMC_ETIMEOUT", -5: "MGMLMC_ECUDA", -6: "MGMLMC_ENOTIMPL", -7: "MGMLMC_ENAN",

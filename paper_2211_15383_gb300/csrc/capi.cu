@@ -36,7 +36,8 @@ using mg::Error;
 namespace {
 
 void check_options(const mgmlmc_options& o) {
-    MG_REQUIRE(o.mg_precision == 64 || o.mg_precision == 32, MGMLMC_EINVAL, "options: mg_precision must be 64 or 32");
+    MG_REQUIRE(o.mg_precision == 64 || o.mg_precision == 32 || o.mg_precision == 16, MGMLMC_EINVAL,
+               "options: mg_precision must be 64, 32 or 16");
     MG_REQUIRE(o.solve_tol > 0 && o.solve_tol < 1, MGMLMC_EINVAL, "options: 0 < solve_tol < 1");
     MG_REQUIRE(o.fgmres_restart >= 1 && o.fgmres_restart <= 63, MGMLMC_EINVAL, "options: 1 <= fgmres_restart <= 63");
     MG_REQUIRE(o.max_iters >= 1, MGMLMC_EINVAL, "options: max_iters >= 1");
@@ -523,7 +524,9 @@ int mgmlmc_apply(mgmlmc_ctx* h, int op, int level, int nrhs, const double* x, do
         else nin = c.lev[l + 1].n;
     }
     if (op == MGMLMC_OP_DINV_C) MG_REQUIRE(level == c.L, MGMLMC_EINVAL, "apply: DINV_C needs level == L");
-    MG_REQUIRE(op >= 0 && op <= 5, MGMLMC_EINVAL, "apply: unknown op");
+    if (op == MGMLMC_OP_SMOOTH)
+        MG_REQUIRE(level >= 2 && level < c.L, MGMLMC_EINVAL, "apply: SMOOTH needs 2 <= level < L");
+    MG_REQUIRE(op >= 0 && op <= 6, MGMLMC_EINVAL, "apply: unknown op");
     double2* xt = upload_block(c, x, nin, nrhs, "ap_x");
     double2* yt = c.scratch<double2>("ap_y", (size_t)nout * nrhs);
     switch (op) {
@@ -531,6 +534,17 @@ int mgmlmc_apply(mgmlmc_ctx* h, int op, int level, int nrhs, const double* x, do
         case MGMLMC_OP_PH: mg::apply_restrict<double2>(c, l, yt, xt, nrhs); break;
         case MGMLMC_OP_P: mg::apply_prolong<double2>(c, l, yt, xt, nrhs, false); break;
         case MGMLMC_OP_G5: mg::launch_gamma5<double2>(yt, xt, c.lev[l].nsites, c.lev[l].d, nrhs, c.stream); break;
+        case MGMLMC_OP_SMOOTH:
+            if (c.opt.mg_precision == 64) {
+                mg::apply_smoother_operator<double2>(c, l, yt, xt, nrhs, nullptr);
+            } else {
+                float2* x32 = c.scratch<float2>("ap_x32", (size_t)nin * nrhs);
+                float2* y32 = c.scratch<float2>("ap_y32", (size_t)nout * nrhs);
+                mg::launch_convert<float2, double2>(x32, xt, nin * nrhs, c.stream);
+                mg::apply_smoother_operator<float2>(c, l, y32, x32, nrhs, nullptr);
+                mg::launch_convert<double2, float2>(yt, y32, nout * nrhs, c.stream);
+            }
+            break;
         default:
             if (c.opt.mg_precision == 64) {
                 mg::mg_cycle<double2>(c, l, yt, xt, nrhs);
@@ -542,6 +556,7 @@ int mgmlmc_apply(mgmlmc_ctx* h, int op, int level, int nrhs, const double* x, do
                 mg::launch_convert<double2, float2>(yt, y32, nout * nrhs, c.stream);
             }
     }
+    mg::check_device_error(c);
     download_block(c, y, yt, nout, nrhs, "ap_out");
     API_END
 }

@@ -26,6 +26,8 @@ struct Level {
     float2* Minv32 = nullptr;
     double2* Ahat64 = nullptr;
     float2* Ahat32 = nullptr;
+    // mg_precision 16, d = 16: Ahat as BF16 real 32 x 32 operands of the tensor-core stencil
+    __nv_bfloat16* Ahat16 = nullptr;
     // prolongation to the next level: [site][d][nvec]
     int ax = 0, at = 0, nvec = 0;
     double2* P64 = nullptr;
@@ -144,6 +146,9 @@ template <typename C> void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, 
 template <typename C> void apply_restrict(Ctx& c, int l, C* xc, const C* x, int N);
 template <typename C> void apply_prolong(Ctx& c, int l, C* x, const C* xc, int N, bool accumulate);
 template <typename C> void mg_cycle(Ctx& c, int l, C* e, const C* r, int N);
+// y = D_l M_l^{-1} x, the operator of the block-Jacobi smoother (coarse levels
+// above the coarsest); dots (2N, may be null) receive conj(y).x and |y|^2 per rhs.
+template <typename C> void apply_smoother_operator(Ctx& c, int l, C* y, const C* x, int N, double2* dots);
 // FGMRES(m) in precision C on level l; x holds the initial guess (zero if x_zero).
 // At most max_cycles restart cycles.  Returns outer iterations; *ok = 1 if the
 // relative residual reached tol (or the cycle budget ended, for inner solves).

@@ -10,6 +10,19 @@
 
 namespace mg {
 
+// Neighbour of a coarse site in direction dir of the 5-point block stencil:
+// 0 self, 1 +x, 2 -x, 3 +t, 4 -t (periodic wrap; sites are x-fastest).
+__device__ __forceinline__ int nbr_site(int site, int dir, int lx, int lt) {
+    const int xx = site % lx, t = site / lx;
+    switch (dir) {
+        case 1: return (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+        case 2: return (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+        case 3: return xx + lx * (t + 1 == lt ? 0 : t + 1);
+        case 4: return xx + lx * (t == 0 ? lt - 1 : t - 1);
+        default: return site;
+    }
+}
+
 // ---------------------------------------------------------------- vectors
 // Z2 noise block: x[i][j] = +-1 (imag 0) for sample first+j, entry i (Sect. 1).
 template <typename C>
@@ -117,6 +130,15 @@ bool tc_coarse_supported(int n);
 void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N,
                                 void* scratch, int* err, cudaStream_t s);
 size_t coarse_inverse_bf16_scratch(int n, int N);
+// Coarse block stencil (d = 16) on the tensor cores: E holds the blocks of every
+// site and direction as BF16 real 32 x 32 operands (launch_embed_stencil_bf16);
+// y = A x (mode 0), b - A x (mode 1), A x plus per-rhs dots (mode 2, partials as
+// launch_block_stencil).  err: device flag set when a bounded wait gave up.
+bool tc_stencil_supported(int d, int N);
+void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cudaStream_t s);
+int block_stencil_tc_groups(int nsites, int N);
+void launch_block_stencil_tc(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt,
+                             int N, int mode, double2* part, int groups, int* err, cudaStream_t s);
 
 // ----------------------------------------------------------------- setup
 // Block-stencil form of the fine Wilson operator: A[site][5][2][2].

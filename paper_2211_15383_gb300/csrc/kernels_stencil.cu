@@ -87,16 +87,6 @@ __global__ void __launch_bounds__(256) k_wilson(C* __restrict__ y, const C* __re
     }
 }
 
-__device__ __forceinline__ int nbr_site(int site, int dir, int lx, int lt) {
-    const int xx = site % lx, t = site / lx;
-    switch (dir) {
-        case 1: return (xx + 1 == lx ? 0 : xx + 1) + lx * t;
-        case 2: return (xx == 0 ? lx - 1 : xx - 1) + lx * t;
-        case 3: return xx + lx * (t + 1 == lt ? 0 : t + 1);
-        case 4: return xx + lx * (t == 0 ? lt - 1 : t - 1);
-        default: return site;
-    }
-}
 
 // One block per coarse site (grid-stride): A[site] (5 d^2 complex) staged in
 // shared memory, each thread owns one rhs and RPT output rows.

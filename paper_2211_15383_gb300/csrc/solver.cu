@@ -94,21 +94,55 @@ void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, doubl
     }
 }
 
+static int* device_error_flag(Ctx& c) {
+    if (!c.dev_err) {
+        c.dev_err = c.scratch<int>("dev_err", 1);
+        MG_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
+    }
+    return c.dev_err;
+}
+
+// The block stencil of D M^{-1} runs on the tensor cores (BF16 operands, FP32
+// accumulation) when mg_precision is 16: the smoother only preconditions the
+// FP32 FGMRES, whose own matrix-vector products stay FP32.
+template <typename C> static bool tc_smoother(const Level&, int) { return false; }
+template <> bool tc_smoother<float2>(const Level& L, int N) { return L.Ahat16 && tc_stencil_supported(L.d, N); }
+template <typename C>
+static void launch_hat_tc(Ctx&, const Level&, C*, const C*, int, double2*, int) {}
+template <>
+void launch_hat_tc<float2>(Ctx& c, const Level& L, float2* y, const float2* x, int N, double2* part, int groups) {
+    launch_block_stencil_tc(y, x, nullptr, L.Ahat16, L.lx, L.lt, N, 2, part, groups, device_error_flag(c), c.stream);
+}
+
 // y = (D_l M_l^{-1}) x with the precomputed block stencil (block-Jacobi smoother).
 template <typename C>
 static void apply_Dhat(Ctx& c, int l, C* y, const C* x, int N, double2* dots) {
     const Level& L = c.lev[l];
-    const int groups = block_stencil_groups(L.nsites, L.d, N);
+    const bool tc = tc_smoother<C>(L, N);
+    const int groups = tc ? block_stencil_tc_groups(L.nsites, N) : block_stencil_groups(L.nsites, L.d, N);
     const double s = sizeof(C);
     double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
-    {
+    const double flops = 40.0 * L.d * L.d * (double)L.nsites * N;
+    if (tc) {
+        // algorithmic traffic: FP32 x and y once, the BF16 operands (4 d^2 reals per block) once
+        ProfScope ps(c, "D" + std::to_string(l + 1) + ".bf16", (double)L.n * N * s * 2 + 5.0 * L.nsites * 8.0 * L.d * L.d,
+                     flops);
+        launch_hat_tc<C>(c, L, y, x, N, part, groups);
+    } else {
         ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
-                     (double)L.n * N * s * 2 + 5.0 * L.nsites * L.d * L.d * s,
-                     40.0 * L.d * L.d * (double)L.nsites * N);
+                     (double)L.n * N * s * 2 + 5.0 * L.nsites * L.d * L.d * s, flops);
         launch_block_stencil<C>(y, x, nullptr, hat_blocks<C>(L), L.lx, L.lt, L.d, N, 2, part, groups, c.stream);
     }
     ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
     launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
+}
+
+template <typename C>
+void apply_smoother_operator(Ctx& c, int l, C* y, const C* x, int N, double2* dots) {
+    MG_REQUIRE(l >= 1 && l < c.L - 1 && hat_blocks<C>(c.lev[l]), MGMLMC_EINVAL,
+               "smoother operator: only coarse levels above the coarsest");
+    if (!dots) dots = c.scratch<double2>("smop_dots", 2 * (size_t)N);
+    apply_Dhat<C>(c, l, y, x, N, dots);
 }
 
 template <typename C>
@@ -145,11 +179,7 @@ template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int 
         // BF16 inverse on the tensor cores; algorithmic bytes: the BF16 matrix once + FP32 in/out
         ProfScope ps(c, "Dinv.bf16", (double)L.n * 2 * L.n * 2 + 2.0 * L.n * N * 8, dinv_flops(L, N));
         void* scr = c.scratch_bytes("tc_scratch", coarse_inverse_bf16_scratch((int)L.n, N));
-        if (!c.dev_err) {
-            c.dev_err = c.scratch<int>("dev_err", 1);
-            MG_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
-        }
-        launch_coarse_inverse_bf16(e, r, L.Dinv16, (int)L.n, N, scr, c.dev_err, c.stream);
+        launch_coarse_inverse_bf16(e, r, L.Dinv16, (int)L.n, N, scr, device_error_flag(c), c.stream);
         return;
     }
     ProfScope ps(c, "Dinv.f32", dinv_bytes(L, N, 8), dinv_flops(L, N));
@@ -398,6 +428,7 @@ void check_device_error(Ctx& c) {
     template void apply_restrict<C>(Ctx&, int, C*, const C*, int);                                          \
     template void apply_prolong<C>(Ctx&, int, C*, const C*, int, bool);                                     \
     template void mg_cycle<C>(Ctx&, int, C*, const C*, int);                                                \
+    template void apply_smoother_operator<C>(Ctx&, int, C*, const C*, int, double2*);                       \
     template long long fgmres<C>(Ctx&, int, const C*, C*, int, double, long long, bool, int*, int);
 INST(double2)
 INST(float2)

@@ -193,3 +193,19 @@ def test_deflated_hutchinson_on_the_fine_operator(pkg, c1):
         got, _ = ctx.estimate_level(0, 0, 48, 12)
         ref = oest.noise_samples(H, (1, None), 12, 0, 48, solvers, dref)
         assert rel_sample_error(got, ref) < TOL64
+
+
+@pytest.mark.parametrize("prec", [64, 32, 16])
+def test_three_levels_with_wide_coarse_blocks(pkg, prec):
+    # d = 16 on level 2 (8 x 8 sites) and 3 (4 x 4 sites, n = 256, tensor-core
+    # coarsest solve): mg_precision 16 runs the smoother's block stencil on the
+    # tensor cores in BF16; the FP64 outer solve keeps every sample at the bar
+    agg, nvec = ((4, 4), (2, 2)), (8, 8)
+    theta, sv = small_problem(32, 32, beta=3.0, m0=-0.05, agg=agg, nvec=nvec)
+    H = ohier.build_hierarchy(theta, -0.05, agg, nvec, sv, 2)
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, -0.05, agg, nvec, sv, 2, mg_precision=prec) as ctx:
+        for t, term in enumerate(oest.term_list(3)):
+            got, _ = ctx.estimate_level(t, 0, 40, 21)
+            ref = oest.noise_samples(H, term, 21, 0, 40, solvers)
+            assert rel_sample_error(got, ref) < TOL64, (prec, term)

@@ -129,3 +129,59 @@ def test_tensor_core_coarsest_solve(pkg, nrhs):
     # per rhs as well (no column is left unwritten or mixed up)
     err = np.linalg.norm(z - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() < 3e-2
+
+
+def _round_bf16(a):
+    """Round float32 values to BF16 (round to nearest, ties to even), as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return (u & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _round_c(z, bf16):
+    """Complex values as the GPU sees them: FP32, then (bf16) BF16 per part."""
+    z = np.asarray(z).astype(np.complex64)
+    if not bf16:
+        return z.astype(np.complex128)
+    return _round_bf16(z.real) + 1j * _round_bf16(z.imag)
+
+
+@pytest.mark.parametrize("prec", [64, 32, 16])
+@pytest.mark.parametrize("nrhs", [1, 37, 130, 300])
+def test_smoother_operator(pkg, prec, nrhs):
+    # y = D_2 M_2^{-1} x, M_2 = block diagonal (self blocks) of D_2, on a level with
+    # d = 16 (4 x 4 sites): FP64 / FP32 block stencils, and (prec 16) the tcgen05
+    # kernel with BF16 operands, whose result must equal the same products of the
+    # BF16-rounded operands up to FP32 accumulation
+    import scipy.sparse as sp
+    agg, nvec = ((4, 4), (2, 2)), (8, 8)
+    theta, sv = small_problem(16, 16, agg=agg, nvec=nvec)
+    H = ohier.build_hierarchy(theta, 0.05, agg, nvec, sv, 0)
+    D2 = H.D[1].tocsr()
+    n, d = D2.shape[0], 16
+    blocks = [np.linalg.inv(D2[s * d:(s + 1) * d, s * d:(s + 1) * d].toarray()) for s in range(n // d)]
+    Ahat = (D2 @ sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")).tocsr()
+    rng = np.random.default_rng(1000 + nrhs)
+    x = rand_complex(rng, (nrhs, n))
+    ref = (Ahat @ x.T).T
+    with make_ctx(pkg, theta, 0.05, agg, nvec, sv, 0, mg_precision=prec) as ctx:
+        y = ctx.apply(pkg.OP_SMOOTH, 2, x, n)
+        y2 = ctx.apply(pkg.OP_SMOOTH, 2, x, n)
+        with pytest.raises(pkg.MgmlmcError):
+            ctx.apply(pkg.OP_SMOOTH, 3, x[:, :64], 64)            # the coarsest level has no smoother
+    assert np.array_equal(y, y2)
+    scale = np.abs(ref).max()
+    if prec == 64:
+        assert np.abs(y - ref).max() < 1e-12 * scale
+        return
+    if prec == 32:
+        assert np.abs(y - ref).max() < 2e-5 * scale
+        return
+    # BF16 operands: the embedding (signs, layouts, neighbours) is pinned by the
+    # emulated products, the accuracy by the exact operator
+    Ab = Ahat.copy()
+    Ab.data = _round_c(Ab.data, True)
+    emu = (Ab @ _round_c(x, True).T).T
+    assert np.abs(y - emu).max() < 2e-5 * scale
+    rel = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() < 1.5e-2
