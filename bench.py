@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="schwinger-128x128")
-    ap.add_argument("--precision", type=int, default=32, choices=[64, 32, 16],
+    ap.add_argument("--precision", type=int, default=16, choices=[64, 32, 16],
                     help="multigrid precision of the headline run: 32 = FP32 multigrid + BF16 tensor-core "
                          "coarsest solve inside FP64 iterative refinement; 16 = as 32 with the coarse "
                          "smoother's block stencil on the tensor cores in BF16; 64 = all-FP64 (the outer "

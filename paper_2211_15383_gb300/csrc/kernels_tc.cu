@@ -365,22 +365,37 @@ namespace tc {
 // B(s, dir) is the real form of A(s, dir)^T:
 //     B[(c,re)][(c',re)] =  Re A[c'][c]     B[(c,im)][(c',re)] = -Im A[c'][c]
 //     B[(c,re)][(c',im)] =  Im A[c'][c]     B[(c,im)][(c',im)] =  Re A[c'][c]
-// So X needs no re-layout beyond rounding to BF16: the 128 threads of a CTA read
-// 16 rows x N rhs of the neighbour (coalesced along the rhs) and write them as
-// K-major core-matrix rows (16 B = 4 components) of a 128 x 32 BF16 tile per 128
-// rhs.  Two such stages alternate: while the tensor core multiplies one
-// direction, the threads fill the other.  B is precomputed once per level in
-// the canonical layout (2 KB per site and direction).  The accumulator of one
-// 128-rhs tile takes 32 TMEM columns; the epilogue reads it back with
-// tcgen05.ld (thread = rhs, 32 columns = 16 complex outputs) and stores rows
-// of y coalesced along the rhs.  One MMA is M = 128, N = 32, K = 16.
+// B is precomputed once per level in the canonical layout (2 KB per site and
+// direction).
+//
+// One CTA per SM (persistent), 8 warps, 256 rhs per CTA (a second grid
+// dimension covers wider blocks).  The work is a sequence of jobs (site,
+// direction), the site's own block last.  Thread 0 streams the FP32 rows of
+// each job's neighbour block (16 rows x 256 rhs, 32 KB) with 1-D bulk copies
+// into a ring of 4 staging buffers, three jobs ahead, completing on mbarriers;
+// the first job of a site also brings the site's 10 KB of B.  Every thread
+// rounds its share of the landed block to BF16 and writes it as K-major
+// core-matrix rows (16 B = 4 components of one rhs) of two 128 x 32 tiles;
+// thread 0 then issues 2 x 2 MMAs (M = 128, N = 32, K = 16) into the two TMEM
+// accumulators (32 columns each) and commits them to the barrier of that
+// operand buffer (two alternate).  After a site's last job the 8 warps read
+// the accumulators back (tcgen05.ld, thread = rhs, 32 columns = 16 complex
+// outputs), store y coalesced along the rhs and, for the dots, take x from the
+// staging buffer of the self block, still resident.
 namespace tcs {
 constexpr int D = 16;
 constexpr int KD = 2 * D;                  // reals per row of X^T (K of one direction)
 constexpr int TILE_A = 128 * KD * 2;       // 8 KB: one 128-rhs BF16 tile of X^T
 constexpr int B_DIR = KD * KD * 2;         // 2 KB: one B(s, dir)
 constexpr int B_SITE = 5 * B_DIR;          // 10 KB per site
-constexpr int kMaxTiles = 8;               // N <= 1024
+constexpr int CH = 256;                    // rhs per CTA (two 128-row tiles)
+constexpr int STG = D * CH * 8;            // 32 KB: FP32 rows of one neighbour block
+constexpr int NSTG = 4;                    // staging ring depth
+constexpr int THREADS = 256;
+constexpr int SMEM = NSTG * STG + 2 * 2 * TILE_A + 2 * B_SITE;   // 180 KB
+constexpr int TCOLS = 64;
+// direction of the o-th job of a site: the neighbours first, the self block last
+__device__ __forceinline__ int dir_of(int o) { return o == 4 ? 0 : o + 1; }
 
 // Byte offset of (row, k) in a K-major, no-swizzle tile with K = 32: 8-row groups
 // of 512 B, four 128-byte core matrices along K, rows 16 B apart.
@@ -392,11 +407,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
 }
-
-__host__ __device__ constexpr int tmem_cols(int ntile) {
-    return ntile * 32 <= 32 ? 32 : (ntile * 32 <= 64 ? 64 : (ntile * 32 <= 128 ? 128 : 256));
-}
-__host__ __device__ constexpr int smem_bytes(int ntile) { return 2 * ntile * TILE_A + B_SITE; }
 
 // B(s, dir) for every site: E[(s * 5 + dir) * 1024 + off / 2], element (n = output
 // real, k = input real) of the real form of A(s, dir)^T.
@@ -411,19 +421,25 @@ __global__ void k_embed_stencil(__nv_bfloat16* __restrict__ E, const float2* __r
     E[sd * (KD * KD) + kmaj32_off(n, k) / 2] = __float2bfloat16(v);
 }
 
-template <int NTILE, int MODE>
-__global__ void __launch_bounds__(128, 4) k_block_stencil_tc(float2* __restrict__ y, const float2* __restrict__ x,
-                                                          const float2* __restrict__ b,
-                                                          const __nv_bfloat16* __restrict__ E, int lx, int lt, int N,
-                                                          double2* __restrict__ part, int* __restrict__ err) {
-    constexpr int TCOLS = tmem_cols(NTILE);
-    constexpr int ROWS = NTILE * 128;
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_block_stencil_tc(float2* __restrict__ y, const float2* __restrict__ x, const float2* __restrict__ b,
+                       const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
+                       int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mma_done[2];
+    __shared__ __align__(8) uint64_t full[NSTG], mma_done[2];
     __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+    uint8_t* stg = smem;                          // NSTG x 32 KB FP32 staging
+    uint8_t* abuf = smem + NSTG * STG;            // 2 x 16 KB BF16 operand tiles
+    uint8_t* bbuf = abuf + 2 * 2 * TILE_A;        // 2 x 10 KB B of a site
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int V = lx * lt;
-    uint8_t* Bs = smem + 2 * NTILE * TILE_A;
+    const int G = gridDim.x;
+    const int j0 = blockIdx.y * CH;               // first rhs of this CTA
+    const int nch = min(CH, N - j0);              // its rhs count (even)
+    const int nsite = (V - (int)blockIdx.x + G - 1) / G;   // sites of this CTA
+    const int njobs = 5 * nsite;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
@@ -431,8 +447,10 @@ __global__ void __launch_bounds__(128, 4) k_block_stencil_tc(float2* __restrict_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        for (int q = 0; q < NSTG; ++q) mbar_init(&full[q], 1);
         mbar_init(&mma_done[0], 1);
         mbar_init(&mma_done[1], 1);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -441,151 +459,150 @@ __global__ void __launch_bounds__(128, 4) k_block_stencil_tc(float2* __restrict_
     const uint32_t tmem = tmem_holder;
     constexpr uint32_t IDESC = instr_desc(128, 32);
 
-    float2 dyx[NTILE];
-    float dyy[NTILE];
-#pragma unroll
-    for (int t = 0; t < NTILE; ++t) {
-        dyx[t] = make_float2(0.f, 0.f);
-        dyy[t] = 0.f;
-    }
-    // parity of the commit issued on each stage and not yet waited for (-1: none);
-    // a stage's n-th commit (0-based) completes the barrier phase of parity n & 1
-    int pend0 = -1, pend1 = -1;
-    int it = 0;
+    // job q: site blockIdx.x + (q / 5) G, direction kOrder[q % 5]; staging slot q % NSTG
+    auto issue = [&](int q) {
+        const int si = q / 5, o = q % 5;
+        const int site = blockIdx.x + si * G;
+        const int nb = nbr_site(site, dir_of(o), lx, lt);
+        uint64_t* bar = &full[q % NSTG];
+        const uint32_t row_bytes = (uint32_t)nch * 8u;
+        mbar_expect_tx(bar, 16u * row_bytes + (o == 0 ? (uint32_t)B_SITE : 0u));
+        uint8_t* dst = stg + (q % NSTG) * STG;
+        const float2* src = x + (size_t)nb * D * N + j0;
+        for (int c = 0; c < D; ++c) bulk_g2s(dst + c * (CH * 8), src + (size_t)c * N, row_bytes, bar);
+        if (o == 0) bulk_g2s(bbuf + (si & 1) * B_SITE, E + (size_t)site * (B_SITE / 2), (uint32_t)B_SITE, bar);
+    };
+    if (tid == 0)
+        for (int q = 0; q < NSTG - 1 && q < njobs; ++q) issue(q);
+
+    float2 dyx = make_float2(0.f, 0.f);
+    float dyy = 0.f;
+    int pend0 = -1, pend1 = -1;     // parity of an unwaited commit per operand buffer
     bool ok = true;
-    for (int site = blockIdx.x; site < V && ok; site += gridDim.x) {
-        for (int dir = 0; dir < 5; ++dir, ++it) {
-            const int bb = it & 1;
-            const int pend = bb ? pend1 : pend0;
-            if (pend >= 0) {
-                // the MMAs that read this stage last must be done before it is refilled
-                ok = __syncthreads_and(mbar_wait(&mma_done[bb], (unsigned)pend));
-                if (!ok) break;
-                if (bb) pend1 = -1;
-                else pend0 = -1;
+    int q = 0;
+    for (; q < njobs; ++q) {
+        const int si = q / 5, o = q % 5, slot = q % NSTG, ab = q & 1;
+        if (tid == 0 && q + NSTG - 1 < njobs) issue(q + NSTG - 1);   // its slot was drained by job q - 1
+        bool w = mbar_wait(&full[slot], (unsigned)((q / NSTG) & 1));
+        const int pend = ab ? pend1 : pend0;
+        if (w && pend >= 0) w = mbar_wait(&mma_done[ab], (unsigned)pend);
+        if (!w) atomicExch(&abort_flag, 1);
+        if (w) {
+            // FP32 staging [c][256 rhs] -> BF16 K-major tiles; unit = (component group, rhs)
+            const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);
+            uint8_t* at = abuf + ab * 2 * TILE_A;
+#pragma unroll
+            for (int k = 0; k < 4 * CH / THREADS; ++k) {
+                const int u = k * THREADS + tid;
+                const int cg = u / CH, j = u % CH;
+                float2 v[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    v[p] = (j < nch) ? sx[(4 * cg + p) * CH + j] : make_float2(0.f, 0.f);
+                uint4 wv;
+                wv.x = pack_bf16(v[0].x, v[0].y);
+                wv.y = pack_bf16(v[1].x, v[1].y);
+                wv.z = pack_bf16(v[2].x, v[2].y);
+                wv.w = pack_bf16(v[3].x, v[3].y);
+                *reinterpret_cast<uint4*>(at + (j >> 7) * TILE_A + kmaj32_off(j & 127, 8 * cg)) = wv;
             }
-            if (dir == 0) {
-                // B(s, .) of this site (all earlier MMAs have completed: see the epilogue wait)
-                const uint4* src = reinterpret_cast<const uint4*>(E + (size_t)site * (B_SITE / 2));
-                uint4* dst = reinterpret_cast<uint4*>(Bs);
-                for (int q = tid; q < B_SITE / 16; q += 128) dst[q] = src[q];
-            }
-            const float2* xn = x + (size_t)nbr_site(site, dir, lx, lt) * D * N;
-            uint8_t* abuf = smem + bb * NTILE * TILE_A;
-            // unit u = (component group cg of 4, rhs j): four 8-byte loads, one 16-byte store
-#pragma unroll
-            for (int u0 = 0; u0 < 4 * ROWS; u0 += 8 * 128) {
-                float2 v[8][4];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int u = u0 + q * 128 + tid;
-                    const int cg = u / ROWS, j = u % ROWS;
-                    const bool in = (u < 4 * ROWS) && j < N;
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        v[q][p] = in ? xn[(size_t)(4 * cg + p) * N + j] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int u = u0 + q * 128 + tid;
-                    if (u < 4 * ROWS) {
-                        const int cg = u / ROWS, j = u % ROWS;
-                        uint4 w;
-                        w.x = pack_bf16(v[q][0].x, v[q][0].y);
-                        w.y = pack_bf16(v[q][1].x, v[q][1].y);
-                        w.z = pack_bf16(v[q][2].x, v[q][2].y);
-                        w.w = pack_bf16(v[q][3].x, v[q][3].y);
-                        *reinterpret_cast<uint4*>(abuf + (j >> 7) * TILE_A + kmaj32_off(j & 127, 8 * cg)) = w;
-                    }
-                }
-            }
-            // generic-proxy shared-memory writes become visible to the tensor core
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sa = smem_u32(abuf);
-                const uint32_t sb = smem_u32(Bs + dir * B_DIR);
-#pragma unroll
-                for (int t = 0; t < NTILE; ++t) {
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ad = smem_desc(sa + t * TILE_A + ks * 256, 128, 512);
-                        const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
-                        const uint32_t acc = (dir > 0 || ks > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 32),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                    }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mma_done[bb])));
-            }
-            const int par = (it >> 1) & 1;
-            if (bb) pend1 = par;
-            else pend0 = par;
-            if (dir < 4) continue;
-            // epilogue of the site: the last commit covers every MMA issued before it
-            ok = __syncthreads_and(mbar_wait(&mma_done[bb], (unsigned)par));
-            if (!ok) break;
-            if (bb) pend1 = -1;
-            else pend0 = -1;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-            for (int t = 0; t < NTILE; ++t) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 32);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int j = t * 128 + warp * 32 + lane;
-                if (j < N) {
-#pragma unroll
-                    for (int co = 0; co < D; ++co) {
-                        const size_t idx = ((size_t)site * D + co) * N + j;
-                        float2 o = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
-                        if (MODE == 1) {
-                            const float2 bv = b[idx];
-                            o = make_float2(bv.x - o.x, bv.y - o.y);
-                        }
-                        y[idx] = o;
-                        if (MODE == 2) {
-                            const float2 xv = x[idx];
-                            // conj(y) * x, accumulated per rhs
-                            dyx[t].x = fmaf(o.x, xv.x, fmaf(o.y, xv.y, dyx[t].x));
-                            dyx[t].y = fmaf(o.x, xv.y, fmaf(-o.y, xv.x, dyx[t].y));
-                            dyy[t] = fmaf(o.x, o.x, fmaf(o.y, o.y, dyy[t]));
-                        }
-                    }
-                }
-            }
-            // TMEM reads finish before the next site's first MMA overwrites the accumulators
-            asm volatile("tcgen05.fence::before_thread_sync;");
         }
+        // generic-proxy shared-memory writes become visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (abort_flag) {
+            ok = false;
+            break;
+        }
+        const int par = (q >> 1) & 1;   // this buffer's (q / 2)-th commit
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = smem_u32(abuf + ab * 2 * TILE_A);
+            const uint32_t sb = smem_u32(bbuf + (si & 1) * B_SITE + dir_of(o) * B_DIR);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ad = smem_desc(sa + t * TILE_A + ks * 256, 128, 512);
+                    const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
+                    const uint32_t acc = (o > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 32),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mma_done[ab])));
+        }
+        if (ab) pend1 = par;
+        else pend0 = par;
+        if (o < 4) continue;
+        // epilogue of the site: the last commit covers every MMA issued before it
+        const bool we = mbar_wait(&mma_done[ab], (unsigned)par);
+        if (__syncthreads_or(!we)) {
+            ok = false;
+            break;
+        }
+        if (ab) pend1 = -1;
+        else pend0 = -1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        {
+            const int site = blockIdx.x + si * G;
+            const int t = warp >> 2;                      // tile of this warp
+            const int jl = t * 128 + (warp & 3) * 32 + lane;
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(t * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                "[%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (jl < nch) {
+                const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);   // x at this site
+                const int j = j0 + jl;
+#pragma unroll
+                for (int co = 0; co < D; ++co) {
+                    const size_t idx = ((size_t)site * D + co) * N + j;
+                    float2 ov = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
+                    if (MODE == 1) {
+                        const float2 bv = b[idx];
+                        ov = make_float2(bv.x - ov.x, bv.y - ov.y);
+                    }
+                    y[idx] = ov;
+                    if (MODE == 2) {
+                        const float2 xv = sx[co * CH + jl];
+                        // conj(y) * x, accumulated per rhs
+                        dyx.x = fmaf(ov.x, xv.x, fmaf(ov.y, xv.y, dyx.x));
+                        dyx.y = fmaf(ov.x, xv.y, fmaf(-ov.y, xv.x, dyx.y));
+                        dyy = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, dyy));
+                    }
+                }
+            }
+        }
+        // TMEM reads and staging reads finish before the next MMAs and copies
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
     }
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
-        // let MMAs still in flight finish (bounded) before the TMEM goes back
+        // let copies and MMAs still in flight finish (bounded) before the shared memory
+        // and the TMEM go back: jobs q .. q + NSTG - 1 were issued and not all waited for
+        for (int q2 = q; q2 < njobs && q2 < q + NSTG; ++q2) mbar_wait(&full[q2 % NSTG], (unsigned)((q2 / NSTG) & 1));
         if (pend0 >= 0) mbar_wait(&mma_done[0], (unsigned)pend0);
         if (pend1 >= 0) mbar_wait(&mma_done[1], (unsigned)pend1);
     } else if (MODE == 2) {
-        const long long G = gridDim.x;
-#pragma unroll
-        for (int t = 0; t < NTILE; ++t) {
-            const int j = t * 128 + warp * 32 + lane;
-            if (j < N) {
-                part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx[t].x, (double)dyx[t].y);
-                part[((long long)1 * N + j) * G + blockIdx.x] = make_double2((double)dyy[t], 0.0);
-            }
+        const int jl = (warp >> 2) * 128 + (warp & 3) * 32 + lane;
+        if (jl < nch) {
+            const int j = j0 + jl;
+            part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx.x, (double)dyx.y);
+            part[((long long)1 * N + j) * G + blockIdx.x] = make_double2((double)dyy, 0.0);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -595,7 +612,7 @@ __global__ void __launch_bounds__(128, 4) k_block_stencil_tc(float2* __restrict_
 }  // namespace tcs
 }  // namespace tc
 
-bool tc_stencil_supported(int d, int N) { return d == tc::tcs::D && N >= 1 && N <= 128 * tc::tcs::kMaxTiles; }
+bool tc_stencil_supported(int d, int N) { return d == tc::tcs::D && N >= 2 && N % 2 == 0; }
 
 void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cudaStream_t s) {
     const long long tot = (long long)nsites * 5 * tc::tcs::KD * tc::tcs::KD;
@@ -603,52 +620,33 @@ void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cu
     MG_LAUNCHED();
 }
 
-static int tc_ntile(int N) {
-    const int t = (N + 127) / 128;
-    return t <= 1 ? 1 : (t <= 2 ? 2 : (t <= 4 ? 4 : 8));
-}
-
-// Persistent CTAs: as many as fit on the SMs at once (shared memory bound), with
-// the sites spread evenly over them.
+// One persistent CTA per SM (180 KB of shared memory) per 256-rhs chunk.
 int block_stencil_tc_groups(int nsites, int N) {
-    const int per_sm_smem = 227 * 1024;
-    const int ntile = tc_ntile(N);
-    int resident = per_sm_smem / (tc::tcs::smem_bytes(ntile) + 1024);
-    if (resident > 8) resident = 8;
-    if (resident < 1) resident = 1;
-    const int slots = resident * kNumSM;
-    const int per = (nsites + slots - 1) / slots;
-    return (nsites + per - 1) / per;
+    const int chunks = (N + tc::tcs::CH - 1) / tc::tcs::CH;
+    int g = kNumSM / chunks;
+    if (g < 1) g = 1;
+    return nsites < g ? nsites : g;
 }
 
-template <int NTILE, int MODE>
+template <int MODE>
 static void bstc_launch(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt, int N,
                         double2* part, int groups, int* err, cudaStream_t s) {
-    constexpr int smem = tc::tcs::smem_bytes(NTILE);
-    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<NTILE, MODE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    tc::tcs::k_block_stencil_tc<NTILE, MODE><<<groups, 128, smem, s>>>(y, x, b, E, lx, lt, N, part, err);
+    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::tcs::SMEM));
+    dim3 g(groups, (N + tc::tcs::CH - 1) / tc::tcs::CH);
+    tc::tcs::k_block_stencil_tc<MODE><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, x, b, E, lx, lt, N, part, err);
     MG_LAUNCHED();
-}
-
-template <int NTILE>
-static void bstc_mode(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt, int N,
-                      int mode, double2* part, int groups, int* err, cudaStream_t s) {
-    if (mode == 0) bstc_launch<NTILE, 0>(y, x, b, E, lx, lt, N, part, groups, err, s);
-    else if (mode == 1) bstc_launch<NTILE, 1>(y, x, b, E, lx, lt, N, part, groups, err, s);
-    else bstc_launch<NTILE, 2>(y, x, b, E, lx, lt, N, part, groups, err, s);
 }
 
 void launch_block_stencil_tc(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt,
                              int N, int mode, double2* part, int groups, int* err, cudaStream_t s) {
-    MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16 and 1 <= N <= 1024");
+    MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16 and an even N >= 2");
     MG_REQUIRE(groups >= 1 && groups <= lx * lt, MGMLMC_EINVAL, "tensor-core stencil: bad grid");
-    switch (tc_ntile(N)) {
-        case 1: bstc_mode<1>(y, x, b, E, lx, lt, N, mode, part, groups, err, s); break;
-        case 2: bstc_mode<2>(y, x, b, E, lx, lt, N, mode, part, groups, err, s); break;
-        case 4: bstc_mode<4>(y, x, b, E, lx, lt, N, mode, part, groups, err, s); break;
-        default: bstc_mode<8>(y, x, b, E, lx, lt, N, mode, part, groups, err, s); break;
-    }
+    MG_REQUIRE(((uintptr_t)x & 15) == 0 && ((uintptr_t)E & 15) == 0, MGMLMC_EINVAL,
+               "tensor-core stencil: x and the operands must be 16-byte aligned");
+    if (mode == 0) bstc_launch<0>(y, x, b, E, lx, lt, N, part, groups, err, s);
+    else if (mode == 1) bstc_launch<1>(y, x, b, E, lx, lt, N, part, groups, err, s);
+    else bstc_launch<2>(y, x, b, E, lx, lt, N, part, groups, err, s);
 }
 
 }  // namespace mg

@@ -147,12 +147,14 @@ def _round_c(z, bf16):
 
 
 @pytest.mark.parametrize("prec", [64, 32, 16])
-@pytest.mark.parametrize("nrhs", [1, 37, 130, 300])
+@pytest.mark.parametrize("nrhs", [1, 37, 130, 300, 600])
 def test_smoother_operator(pkg, prec, nrhs):
     # y = D_2 M_2^{-1} x, M_2 = block diagonal (self blocks) of D_2, on a level with
-    # d = 16 (4 x 4 sites): FP64 / FP32 block stencils, and (prec 16) the tcgen05
-    # kernel with BF16 operands, whose result must equal the same products of the
-    # BF16-rounded operands up to FP32 accumulation
+    # d = 16 (4 x 4 sites): FP64 / FP32 block stencils, and (prec 16, even nrhs) the
+    # tcgen05 kernel with BF16 operands (256 rhs per CTA: 130 leaves a ragged tile,
+    # 300 and 600 a ragged second / third chunk), whose result must equal the same
+    # products of the BF16-rounded operands up to FP32 accumulation; odd nrhs take
+    # the FP32 stencil
     import scipy.sparse as sp
     agg, nvec = ((4, 4), (2, 2)), (8, 8)
     theta, sv = small_problem(16, 16, agg=agg, nvec=nvec)
@@ -174,7 +176,7 @@ def test_smoother_operator(pkg, prec, nrhs):
     if prec == 64:
         assert np.abs(y - ref).max() < 1e-12 * scale
         return
-    if prec == 32:
+    if prec == 32 or nrhs % 2:
         assert np.abs(y - ref).max() < 2e-5 * scale
         return
     # BF16 operands: the embedding (signs, layouts, neighbours) is pinned by the
