@@ -276,7 +276,7 @@ static void block_jacobi_setup(Ctx& c, int l) {
     launch_precondition_blocks(L.Ahat64, L.A64, L.Minv64, L.lx, L.lt, L.d, c.stream);
     launch_convert<float2, double2>(L.Minv32, L.Minv64, (long long)nb, c.stream);
     launch_convert<float2, double2>(L.Ahat32, L.Ahat64, (long long)nb * 5, c.stream);
-    if (c.opt.mg_precision == 16 && tc_stencil_supported(L.d, 1)) {
+    if (c.opt.mg_precision == 16 && tc_stencil_supported(L.d, 2)) {
         if (!L.Ahat16) L.Ahat16 = c.alloc_n<__nv_bfloat16>((size_t)L.nsites * 5 * 4 * L.d * L.d);
         launch_embed_stencil_bf16(L.Ahat16, L.Ahat32, L.nsites, c.stream);
     }

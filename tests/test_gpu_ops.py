@@ -167,8 +167,13 @@ def test_smoother_operator(pkg, prec, nrhs):
     x = rand_complex(rng, (nrhs, n))
     ref = (Ahat @ x.T).T
     with make_ctx(pkg, theta, 0.05, agg, nvec, sv, 0, mg_precision=prec) as ctx:
+        ctx.profile(True, reset=True)
         y = ctx.apply(pkg.OP_SMOOTH, 2, x, n)
         y2 = ctx.apply(pkg.OP_SMOOTH, 2, x, n)
+        classes = set(ctx.profile_report())
+        ctx.profile(False)
+        # the kernel class that ran: BF16 tensor cores exactly when prec 16 and nrhs even
+        assert ("D2.bf16" in classes) == (prec == 16 and nrhs % 2 == 0), classes
         with pytest.raises(pkg.MgmlmcError):
             ctx.apply(pkg.OP_SMOOTH, 3, x[:, :64], 64)            # the coarsest level has no smoother
     assert np.array_equal(y, y2)
