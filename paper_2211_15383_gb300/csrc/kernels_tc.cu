@@ -368,32 +368,31 @@ namespace tc {
 // B is precomputed once per level in the canonical layout (2 KB per site and
 // direction).
 //
-// One CTA per SM (persistent), 8 warps, 256 rhs per CTA (a second grid
-// dimension covers wider blocks).  The work is a sequence of jobs (site,
-// direction), the site's own block last.  Thread 0 streams the FP32 rows of
-// each job's neighbour block (16 rows x 256 rhs, 32 KB) with 1-D bulk copies
-// into a ring of 4 staging buffers, three jobs ahead, completing on mbarriers;
-// the first job of a site also brings the site's 10 KB of B.  Every thread
-// rounds its share of the landed block to BF16 and writes it as K-major
-// core-matrix rows (16 B = 4 components of one rhs) of two 128 x 32 tiles;
-// thread 0 then issues 2 x 2 MMAs (M = 128, N = 32, K = 16) into the two TMEM
-// accumulators (32 columns each) and commits them to the barrier of that
-// operand buffer (two alternate).  After a site's last job the 8 warps read
-// the accumulators back (tcgen05.ld, thread = rhs, 32 columns = 16 complex
-// outputs), store y coalesced along the rhs and, for the dots, take x from the
-// staging buffer of the self block, still resident.
+// Persistent CTAs, two per SM, each with 128 rhs (a 128 x 32 tile per job) and
+// 128 threads.  The work of a CTA is a sequence of jobs (site, direction), the
+// site's own block last.  Every thread copies its share of the FP32 rows of a
+// job's neighbour block (16 rows x 128 rhs, 16 KB) into a ring of 4 staging
+// buffers with 16-byte cp.async, three jobs ahead; the first job of a site also
+// brings the site's 10 KB of B.  When a job's copies have landed, the threads
+// round the block to BF16 and write it as K-major core-matrix rows (16 B = 4
+// components of one rhs); thread 0 then issues two MMAs (M = 128, N = 32,
+// K = 16) into the TMEM accumulator (32 columns) and commits them to the
+// barrier of that operand buffer (two alternate).  After a site's last job the
+// 4 warps read the accumulator back (tcgen05.ld, thread = rhs, 32 columns = 16
+// complex outputs), store y coalesced along the rhs and, for the dots, take x
+// from the staging buffer of the self block, still resident.
 namespace tcs {
 constexpr int D = 16;
 constexpr int KD = 2 * D;                  // reals per row of X^T (K of one direction)
 constexpr int TILE_A = 128 * KD * 2;       // 8 KB: one 128-rhs BF16 tile of X^T
 constexpr int B_DIR = KD * KD * 2;         // 2 KB: one B(s, dir)
 constexpr int B_SITE = 5 * B_DIR;          // 10 KB per site
-constexpr int CH = 256;                    // rhs per CTA (two 128-row tiles)
-constexpr int STG = D * CH * 8;            // 32 KB: FP32 rows of one neighbour block
+constexpr int CH = 128;                    // rhs per CTA (one 128-row tile)
+constexpr int STG = D * CH * 8;            // 16 KB: FP32 rows of one neighbour block
 constexpr int NSTG = 4;                    // staging ring depth
-constexpr int THREADS = 256;
-constexpr int SMEM = NSTG * STG + 2 * 2 * TILE_A + 2 * B_SITE;   // 180 KB
-constexpr int TCOLS = 64;
+constexpr int THREADS = CH;                // thread = rhs in the epilogue
+constexpr int SMEM = NSTG * STG + 2 * TILE_A + 2 * B_SITE;   // 100 KB: two CTAs per SM
+constexpr int TCOLS = 32;
 // direction of the o-th job of a site: the neighbours first, the self block last
 __device__ __forceinline__ int dir_of(int o) { return o == 4 ? 0 : o + 1; }
 
@@ -421,18 +420,25 @@ __global__ void k_embed_stencil(__nv_bfloat16* __restrict__ E, const float2* __r
     E[sd * (KD * KD) + kmaj32_off(n, k) / 2] = __float2bfloat16(v);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
+
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
     k_block_stencil_tc(float2* __restrict__ y, const float2* __restrict__ x, const float2* __restrict__ b,
                        const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[NSTG], mma_done[2];
+    __shared__ __align__(8) uint64_t mma_done[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
-    uint8_t* stg = smem;                          // NSTG x 32 KB FP32 staging
-    uint8_t* abuf = smem + NSTG * STG;            // 2 x 16 KB BF16 operand tiles
-    uint8_t* bbuf = abuf + 2 * 2 * TILE_A;        // 2 x 10 KB B of a site
+    uint8_t* stg = smem;                          // NSTG x 16 KB FP32 staging
+    uint8_t* abuf = smem + NSTG * STG;            // 2 x 8 KB BF16 operand tiles
+    uint8_t* bbuf = abuf + 2 * TILE_A;            // 2 x 10 KB B of a site
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int V = lx * lt;
     const int G = gridDim.x;
@@ -447,7 +453,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int q = 0; q < NSTG; ++q) mbar_init(&full[q], 1);
         mbar_init(&mma_done[0], 1);
         mbar_init(&mma_done[1], 1);
         abort_flag = 0;
@@ -459,38 +464,52 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = tmem_holder;
     constexpr uint32_t IDESC = instr_desc(128, 32);
 
-    // job q: site blockIdx.x + (q / 5) G, direction kOrder[q % 5]; staging slot q % NSTG
+    // job q: site blockIdx.x + (q / 5) G, direction dir_of(q % 5), staging slot q % NSTG;
+    // this thread's 16-byte pieces: rhs pairs of the 16 rows, then (first job of a
+    // site) pieces of the site's B
     auto issue = [&](int q) {
-        const int si = q / 5, o = q % 5;
-        const int site = blockIdx.x + si * G;
-        const int nb = nbr_site(site, dir_of(o), lx, lt);
-        uint64_t* bar = &full[q % NSTG];
-        const uint32_t row_bytes = (uint32_t)nch * 8u;
-        mbar_expect_tx(bar, 16u * row_bytes + (o == 0 ? (uint32_t)B_SITE : 0u));
-        uint8_t* dst = stg + (q % NSTG) * STG;
-        const float2* src = x + (size_t)nb * D * N + j0;
-        for (int c = 0; c < D; ++c) bulk_g2s(dst + c * (CH * 8), src + (size_t)c * N, row_bytes, bar);
-        if (o == 0) bulk_g2s(bbuf + (si & 1) * B_SITE, E + (size_t)site * (B_SITE / 2), (uint32_t)B_SITE, bar);
+        if (q < njobs) {
+            const int si = q / 5, o = q % 5;
+            const int site = blockIdx.x + si * G;
+            const int nb = nbr_site(site, dir_of(o), lx, lt);
+            uint8_t* dst = stg + (q % NSTG) * STG;
+            const float2* src = x + (size_t)nb * D * N + j0;
+#pragma unroll
+            for (int k = 0; k < D * CH / 2 / THREADS; ++k) {
+                const int u = k * THREADS + tid;
+                const int c = u / (CH / 2), jp = u % (CH / 2);
+                if (2 * jp < nch) cp_async16(dst + c * (CH * 8) + jp * 16, src + (size_t)c * N + 2 * jp);
+            }
+            if (o == 0) {
+                const uint8_t* bsrc = reinterpret_cast<const uint8_t*>(E + (size_t)site * (B_SITE / 2));
+                uint8_t* bdst = bbuf + (si & 1) * B_SITE;
+                for (int u = tid; u < B_SITE / 16; u += THREADS) cp_async16(bdst + u * 16, bsrc + u * 16);
+            }
+        }
+        cp_async_commit();   // one group per job slot, empty past the end
     };
-    if (tid == 0)
-        for (int q = 0; q < NSTG - 1 && q < njobs; ++q) issue(q);
+#pragma unroll
+    for (int q = 0; q < NSTG - 1; ++q) issue(q);
 
     float2 dyx = make_float2(0.f, 0.f);
     float dyy = 0.f;
     int pend0 = -1, pend1 = -1;     // parity of an unwaited commit per operand buffer
     bool ok = true;
-    int q = 0;
-    for (; q < njobs; ++q) {
+    for (int q = 0; q < njobs; ++q) {
         const int si = q / 5, o = q % 5, slot = q % NSTG, ab = q & 1;
-        if (tid == 0 && q + NSTG - 1 < njobs) issue(q + NSTG - 1);   // its slot was drained by job q - 1
-        bool w = mbar_wait(&full[slot], (unsigned)((q / NSTG) & 1));
+        issue(q + NSTG - 1);                  // into the slot that job q - 1 drained
+        cp_async_wait<NSTG - 1>();            // this thread's pieces of job q have landed
         const int pend = ab ? pend1 : pend0;
-        if (w && pend >= 0) w = mbar_wait(&mma_done[ab], (unsigned)pend);
-        if (!w) atomicExch(&abort_flag, 1);
-        if (w) {
-            // FP32 staging [c][256 rhs] -> BF16 K-major tiles; unit = (component group, rhs)
+        if (pend >= 0 && !mbar_wait(&mma_done[ab], (unsigned)pend)) atomicExch(&abort_flag, 1);
+        __syncthreads();                      // every thread's pieces of job q are visible
+        if (abort_flag) {
+            ok = false;
+            break;
+        }
+        {
+            // FP32 staging [c][128 rhs] -> BF16 K-major tile; unit = (component group, rhs)
             const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);
-            uint8_t* at = abuf + ab * 2 * TILE_A;
+            uint8_t* at = abuf + ab * TILE_A;
 #pragma unroll
             for (int k = 0; k < 4 * CH / THREADS; ++k) {
                 const int u = k * THREADS + tid;
@@ -504,33 +523,27 @@ __global__ void __launch_bounds__(THREADS, 1)
                 wv.y = pack_bf16(v[1].x, v[1].y);
                 wv.z = pack_bf16(v[2].x, v[2].y);
                 wv.w = pack_bf16(v[3].x, v[3].y);
-                *reinterpret_cast<uint4*>(at + (j >> 7) * TILE_A + kmaj32_off(j & 127, 8 * cg)) = wv;
+                *reinterpret_cast<uint4*>(at + kmaj32_off(j, 8 * cg)) = wv;
             }
         }
-        // generic-proxy shared-memory writes become visible to the tensor core
+        // generic-proxy shared-memory writes (converted tile, and B from cp.async)
+        // become visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (abort_flag) {
-            ok = false;
-            break;
-        }
         const int par = (q >> 1) & 1;   // this buffer's (q / 2)-th commit
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = smem_u32(abuf + ab * 2 * TILE_A);
+            const uint32_t sa = smem_u32(abuf + ab * TILE_A);
             const uint32_t sb = smem_u32(bbuf + (si & 1) * B_SITE + dir_of(o) * B_DIR);
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ad = smem_desc(sa + t * TILE_A + ks * 256, 128, 512);
-                    const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
-                    const uint32_t acc = (o > 0 || ks > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 32),
-                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                }
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = smem_desc(sa + ks * 256, 128, 512);
+                const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
+                const uint32_t acc = (o > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mma_done[ab])));
@@ -549,10 +562,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         {
             const int site = blockIdx.x + si * G;
-            const int t = warp >> 2;                      // tile of this warp
-            const int jl = t * 128 + (warp & 3) * 32 + lane;
+            const int jl = warp * 32 + lane;
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(t * 32);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
@@ -590,15 +602,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
+    cp_async_wait<0>();   // no copy may still target this CTA's shared memory
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
-        // let copies and MMAs still in flight finish (bounded) before the shared memory
-        // and the TMEM go back: jobs q .. q + NSTG - 1 were issued and not all waited for
-        for (int q2 = q; q2 < njobs && q2 < q + NSTG; ++q2) mbar_wait(&full[q2 % NSTG], (unsigned)((q2 / NSTG) & 1));
+        // MMAs still in flight finish (bounded) before the TMEM goes back
         if (pend0 >= 0) mbar_wait(&mma_done[0], (unsigned)pend0);
         if (pend1 >= 0) mbar_wait(&mma_done[1], (unsigned)pend1);
     } else if (MODE == 2) {
-        const int jl = (warp >> 2) * 128 + (warp & 3) * 32 + lane;
+        const int jl = warp * 32 + lane;
         if (jl < nch) {
             const int j = j0 + jl;
             part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx.x, (double)dyx.y);
@@ -620,10 +631,10 @@ void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cu
     MG_LAUNCHED();
 }
 
-// One persistent CTA per SM (180 KB of shared memory) per 256-rhs chunk.
+// Two persistent CTAs per SM (100 KB of shared memory each) over the 128-rhs chunks.
 int block_stencil_tc_groups(int nsites, int N) {
     const int chunks = (N + tc::tcs::CH - 1) / tc::tcs::CH;
-    int g = kNumSM / chunks;
+    int g = 2 * kNumSM / chunks;
     if (g < 1) g = 1;
     return nsites < g ? nsites : g;
 }
