@@ -368,19 +368,23 @@ namespace tc {
 // B is precomputed once per level in the canonical layout (2 KB per site and
 // direction).
 //
-// Persistent CTAs, two per SM, each with 128 rhs (a 128 x 32 tile per job) and
-// 128 threads.  The work of a CTA is a sequence of jobs (site, direction), the
-// site's own block last.  Every thread copies its share of the FP32 rows of a
-// job's neighbour block (16 rows x 128 rhs, 16 KB) into a ring of 4 staging
-// buffers with 16-byte cp.async, three jobs ahead; the first job of a site also
-// brings the site's 10 KB of B.  When a job's copies have landed, the threads
-// round the block to BF16 and write it as K-major core-matrix rows (16 B = 4
-// components of one rhs); thread 0 then issues two MMAs (M = 128, N = 32,
-// K = 16) into the TMEM accumulator (32 columns) and commits them to the
-// barrier of that operand buffer (two alternate).  After a site's last job the
-// 4 warps read the accumulator back (tcgen05.ld, thread = rhs, 32 columns = 16
-// complex outputs), store y coalesced along the rhs and, for the dots, take x
-// from the staging buffer of the self block, still resident.
+// Warp-specialised and persistent: two CTAs per SM, each with 128 rhs and 10
+// warps that hand work on through mbarriers.  A CTA's work is a sequence of
+// jobs (site, direction).
+//   warp 0 (one thread): streams the FP32 rows of each job's neighbour block
+//     (16 rows x 128 rhs, 16 KB) with 1-D bulk copies into a ring of 4 staging
+//     buffers (full / empty barriers);
+//   warps 2-5 (thread = rhs): round the landed block to BF16 and write it as
+//     K-major core-matrix rows (16 B = 4 components of one rhs) of a 128 x 32
+//     tile (two tiles alternate), and at a site's first job copy the site's 10 KB
+//     of B (two site slots alternate);
+//   warp 1 (one thread): issues two MMAs (M = 128, N = 32, K = 16) per job into
+//     the site's TMEM accumulator (two sets of 32 columns alternate by site) and
+//     commits them: to the tile's barrier, and after a site's last job to the
+//     accumulator's;
+//   warps 6-9 (thread = rhs): read a finished accumulator (tcgen05.ld, 32 columns
+//     = 16 complex outputs), hand it back, and store y coalesced along the rhs,
+//     with the dots against x (read from L2) for the smoother.
 namespace tcs {
 constexpr int D = 16;
 constexpr int KD = 2 * D;                  // reals per row of X^T (K of one direction)
@@ -390,9 +394,10 @@ constexpr int B_SITE = 5 * B_DIR;          // 10 KB per site
 constexpr int CH = 128;                    // rhs per CTA (one 128-row tile)
 constexpr int STG = D * CH * 8;            // 16 KB: FP32 rows of one neighbour block
 constexpr int NSTG = 4;                    // staging ring depth
-constexpr int THREADS = CH;                // thread = rhs in the epilogue
+constexpr int THREADS = 320;               // 10 warps
 constexpr int SMEM = NSTG * STG + 2 * TILE_A + 2 * B_SITE;   // 100 KB: two CTAs per SM
-constexpr int TCOLS = 32;
+constexpr int TCOLS = 64;                  // two accumulators of 32 columns
+constexpr int kMaxDevWait = 1 << 26;
 // direction of the o-th job of a site: the neighbours first, the self block last
 __device__ __forceinline__ int dir_of(int o) { return o == 4 ? 0 : o + 1; }
 
@@ -420,12 +425,25 @@ __global__ void k_embed_stencil(__nv_bfloat16* __restrict__ E, const float2* __r
     E[sd * (KD * KD) + kmaj32_off(n, k) / 2] = __float2bfloat16(v);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < kMaxDevWait; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N_>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 2)
@@ -433,12 +451,13 @@ __global__ void __launch_bounds__(THREADS, 2)
                        const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mma_done[2];
+    __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], tfull[2], tempty[2], afull[2], aempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
     uint8_t* stg = smem;                          // NSTG x 16 KB FP32 staging
     uint8_t* abuf = smem + NSTG * STG;            // 2 x 8 KB BF16 operand tiles
     uint8_t* bbuf = abuf + 2 * TILE_A;            // 2 x 10 KB B of a site
+    volatile int* abrt = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int V = lx * lt;
     const int G = gridDim.x;
@@ -453,8 +472,16 @@ __global__ void __launch_bounds__(THREADS, 2)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(&mma_done[0], 1);
-        mbar_init(&mma_done[1], 1);
+        for (int q = 0; q < NSTG; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 4);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&tfull[q], 4);
+            mbar_init(&tempty[q], 1);
+            mbar_init(&afull[q], 1);
+            mbar_init(&aempty[q], 4);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -462,109 +489,118 @@ __global__ void __launch_bounds__(THREADS, 2)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    constexpr uint32_t IDESC = instr_desc(128, 32);
 
-    // job q: site blockIdx.x + (q / 5) G, direction dir_of(q % 5), staging slot q % NSTG;
-    // this thread's 16-byte pieces: rhs pairs of the 16 rows, then (first job of a
-    // site) pieces of the site's B
-    auto issue = [&](int q) {
-        if (q < njobs) {
-            const int si = q / 5, o = q % 5;
-            const int site = blockIdx.x + si * G;
-            const int nb = nbr_site(site, dir_of(o), lx, lt);
-            uint8_t* dst = stg + (q % NSTG) * STG;
-            const float2* src = x + (size_t)nb * D * N + j0;
-#pragma unroll
-            for (int k = 0; k < D * CH / 2 / THREADS; ++k) {
-                const int u = k * THREADS + tid;
-                const int c = u / (CH / 2), jp = u % (CH / 2);
-                if (2 * jp < nch) cp_async16(dst + c * (CH * 8) + jp * 16, src + (size_t)c * N + 2 * jp);
+    if (warp == 0) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            const uint32_t row_bytes = (uint32_t)nch * 8u;
+            int q = 0;
+            for (; q < njobs; ++q) {
+                const int slot = q % NSTG;
+                if (q >= NSTG && !mbar_wait_ab(&empty[slot], (unsigned)((q / NSTG - 1) & 1), abrt)) break;
+                const int site = blockIdx.x + (q / 5) * G;
+                const int nb = nbr_site(site, dir_of(q % 5), lx, lt);
+                mbar_expect_tx(&full[slot], 16u * row_bytes);
+                uint8_t* dst = stg + slot * STG;
+                const float2* src = x + (size_t)nb * D * N + j0;
+                for (int c = 0; c < D; ++c) bulk_g2s(dst + c * (CH * 8), src + (size_t)c * N, row_bytes, &full[slot]);
             }
+            if (*abrt) {
+                // copies still in flight land before the shared memory goes back: the
+                // last job issued to each slot (earlier ones completed before reuse)
+                for (int q2 = max(0, q - NSTG); q2 < q; ++q2) mbar_wait(&full[q2 % NSTG], (unsigned)((q2 / NSTG) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = instr_desc(128, 32);
+            int last_tile = -1, last_acc = -1;
+            for (int q = 0; q < njobs; ++q) {
+                const int si = q / 5, o = q % 5, ab = q & 1, as = si & 1;
+                if (o == 0 && si >= 2 && !mbar_wait_ab(&aempty[as], (unsigned)(((si >> 1) - 1) & 1), abrt)) break;
+                if (!mbar_wait_ab(&tfull[ab], (unsigned)((q >> 1) & 1), abrt)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = smem_u32(abuf + ab * TILE_A);
+                const uint32_t sb = smem_u32(bbuf + as * B_SITE + dir_of(o) * B_DIR);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ad = smem_desc(sa + ks * 256, 128, 512);
+                    const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
+                    const uint32_t acc = (o > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + as * 32),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&tempty[ab])));
+                last_tile = q;
+                if (o == 4) {
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&afull[as])));
+                    last_acc = si;
+                }
+            }
+            if (*abrt && last_tile >= 0) {
+                // MMAs in flight complete before the TMEM goes back
+                mbar_wait(&tempty[last_tile & 1], (unsigned)((last_tile >> 1) & 1));
+            }
+            (void)last_acc;
+        }
+    } else if (warp < 6) {
+        // ---------------------------------------------------------------- converters
+        const int j = (warp - 2) * 32 + lane;     // rhs of this thread
+        for (int q = 0; q < njobs; ++q) {
+            const int si = q / 5, o = q % 5, slot = q % NSTG, ab = q & 1, as = si & 1;
+            if (!mbar_wait_ab(&full[slot], (unsigned)((q / NSTG) & 1), abrt)) break;
+            if (q >= 2 && !mbar_wait_ab(&tempty[ab], (unsigned)(((q >> 1) - 1) & 1), abrt)) break;
             if (o == 0) {
-                const uint8_t* bsrc = reinterpret_cast<const uint8_t*>(E + (size_t)site * (B_SITE / 2));
-                uint8_t* bdst = bbuf + (si & 1) * B_SITE;
-                for (int u = tid; u < B_SITE / 16; u += THREADS) cp_async16(bdst + u * 16, bsrc + u * 16);
+                // B of this site, once the MMAs of the site two back (same slot) are done
+                if (si >= 2 && !mbar_wait_ab(&afull[as], (unsigned)(((si - 2) >> 1) & 1), abrt)) break;
+                const uint4* bs = reinterpret_cast<const uint4*>(E + (size_t)(blockIdx.x + si * G) * (B_SITE / 2));
+                uint4* bd = reinterpret_cast<uint4*>(bbuf + as * B_SITE);
+                for (int u = j; u < B_SITE / 16; u += 128) bd[u] = bs[u];
             }
-        }
-        cp_async_commit();   // one group per job slot, empty past the end
-    };
-#pragma unroll
-    for (int q = 0; q < NSTG - 1; ++q) issue(q);
-
-    float2 dyx = make_float2(0.f, 0.f);
-    float dyy = 0.f;
-    int pend0 = -1, pend1 = -1;     // parity of an unwaited commit per operand buffer
-    bool ok = true;
-    for (int q = 0; q < njobs; ++q) {
-        const int si = q / 5, o = q % 5, slot = q % NSTG, ab = q & 1;
-        issue(q + NSTG - 1);                  // into the slot that job q - 1 drained
-        cp_async_wait<NSTG - 1>();            // this thread's pieces of job q have landed
-        const int pend = ab ? pend1 : pend0;
-        if (pend >= 0 && !mbar_wait(&mma_done[ab], (unsigned)pend)) atomicExch(&abort_flag, 1);
-        __syncthreads();                      // every thread's pieces of job q are visible
-        if (abort_flag) {
-            ok = false;
-            break;
-        }
-        {
-            // FP32 staging [c][128 rhs] -> BF16 K-major tile; unit = (component group, rhs)
             const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);
-            uint8_t* at = abuf + ab * TILE_A;
+            uint4 wv[4];
 #pragma unroll
-            for (int k = 0; k < 4 * CH / THREADS; ++k) {
-                const int u = k * THREADS + tid;
-                const int cg = u / CH, j = u % CH;
+            for (int cg = 0; cg < 4; ++cg) {
                 float2 v[4];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    v[p] = (j < nch) ? sx[(4 * cg + p) * CH + j] : make_float2(0.f, 0.f);
-                uint4 wv;
-                wv.x = pack_bf16(v[0].x, v[0].y);
-                wv.y = pack_bf16(v[1].x, v[1].y);
-                wv.z = pack_bf16(v[2].x, v[2].y);
-                wv.w = pack_bf16(v[3].x, v[3].y);
-                *reinterpret_cast<uint4*>(at + kmaj32_off(j, 8 * cg)) = wv;
+                for (int p = 0; p < 4; ++p) v[p] = (j < nch) ? sx[(4 * cg + p) * CH + j] : make_float2(0.f, 0.f);
+                wv[cg].x = pack_bf16(v[0].x, v[0].y);
+                wv[cg].y = pack_bf16(v[1].x, v[1].y);
+                wv[cg].z = pack_bf16(v[2].x, v[2].y);
+                wv[cg].w = pack_bf16(v[3].x, v[3].y);
             }
-        }
-        // generic-proxy shared-memory writes (converted tile, and B from cp.async)
-        // become visible to the tensor core
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        const int par = (q >> 1) & 1;   // this buffer's (q / 2)-th commit
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = smem_u32(abuf + ab * TILE_A);
-            const uint32_t sb = smem_u32(bbuf + (si & 1) * B_SITE + dir_of(o) * B_DIR);
+            // the loaded values are consumed: the staging slot may be refilled
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            uint8_t* at = abuf + ab * TILE_A;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ad = smem_desc(sa + ks * 256, 128, 512);
-                const uint64_t bd = smem_desc(sb + ks * 256, 128, 512);
-                const uint32_t acc = (o > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+            for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(at + kmaj32_off(j, 8 * cg)) = wv[cg];
+            // generic-proxy writes (tile, B) become visible to the tensor core
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfull[ab]);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int quarter = warp & 3;             // TMEM lanes this warp may read
+        const int jl = quarter * 32 + lane;
+        float2 dyx = make_float2(0.f, 0.f);
+        float dyy = 0.f;
+        bool ok = true;
+        for (int si = 0; si < nsite; ++si) {
+            const int as = si & 1;
+            if (!mbar_wait_ab(&afull[as], (unsigned)((si >> 1) & 1), abrt)) {
+                ok = false;
+                break;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mma_done[ab])));
-        }
-        if (ab) pend1 = par;
-        else pend0 = par;
-        if (o < 4) continue;
-        // epilogue of the site: the last commit covers every MMA issued before it
-        const bool we = mbar_wait(&mma_done[ab], (unsigned)par);
-        if (__syncthreads_or(!we)) {
-            ok = false;
-            break;
-        }
-        if (ab) pend1 = -1;
-        else pend0 = -1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        {
-            const int site = blockIdx.x + si * G;
-            const int jl = warp * 32 + lane;
+            asm volatile("tcgen05.fence::after_thread_sync;");
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(as * 32);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
@@ -576,8 +612,11 @@ __global__ void __launch_bounds__(THREADS, 2)
                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aempty[as]);      // accumulator may be overwritten
             if (jl < nch) {
-                const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);   // x at this site
+                const int site = blockIdx.x + si * G;
                 const int j = j0 + jl;
 #pragma unroll
                 for (int co = 0; co < D; ++co) {
@@ -589,7 +628,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                     }
                     y[idx] = ov;
                     if (MODE == 2) {
-                        const float2 xv = sx[co * CH + jl];
+                        const float2 xv = x[idx];
                         // conj(y) * x, accumulated per rhs
                         dyx.x = fmaf(ov.x, xv.x, fmaf(ov.y, xv.y, dyx.x));
                         dyx.y = fmaf(ov.x, xv.y, fmaf(-ov.y, xv.x, dyx.y));
@@ -598,19 +637,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                 }
             }
         }
-        // TMEM reads and staging reads finish before the next MMAs and copies
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-    }
-    cp_async_wait<0>();   // no copy may still target this CTA's shared memory
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // MMAs still in flight finish (bounded) before the TMEM goes back
-        if (pend0 >= 0) mbar_wait(&mma_done[0], (unsigned)pend0);
-        if (pend1 >= 0) mbar_wait(&mma_done[1], (unsigned)pend1);
-    } else if (MODE == 2) {
-        const int jl = warp * 32 + lane;
-        if (jl < nch) {
+        if (ok && MODE == 2 && jl < nch) {
             const int j = j0 + jl;
             part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx.x, (double)dyx.y);
             part[((long long)1 * N + j) * G + blockIdx.x] = make_double2((double)dyy, 0.0);
@@ -618,6 +645,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (tid == 0 && abort_flag) atomicExch(err, 1);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 }  // namespace tcs
