@@ -182,10 +182,11 @@ def ncu_traffic(kclass):
 def roofline(report, peaks, fp64_peak, fp32_peak):
     """Roofline of the kernel class with the largest device time.
 
-    The bound follows the class's precision and arithmetic intensity: BF16 classes
-    run on the tensor cores (peak: measured sustained cuBLAS BF16, the kernel runs
-    inside a long step); FP64 and FP32 classes are ALU-bound when their
-    intensity exceeds the ridge point (FMA peak / HBM bandwidth), else HBM-bound.
+    The bound follows the class's precision and arithmetic intensity: a class is
+    compute-bound when its intensity exceeds the ridge point (peak / HBM bandwidth)
+    of its unit, else HBM-bound.  BF16 classes run on the tensor cores (peak:
+    measured sustained cuBLAS BF16, the kernels run inside a long step); FP64 and
+    FP32 classes on the FMA pipes (measured FMA peaks).
     """
     cls, st = max(report.items(), key=lambda kv: kv[1]["ms"])
     per_launch_s = st["ms"] * 1e-3 / st["count"]
@@ -193,11 +194,16 @@ def roofline(report, peaks, fp64_peak, fp32_peak):
     bytes_l = st["bytes"] / st["count"]
     flops_l = st["flops"] / st["count"]
     hbm = peaks["hbm_gbs"] * 1e9
-    if prec == "bf16":
+    if prec == "bf16" and flops_l / max(bytes_l, 1.0) > (peaks.get("bf16_tflops_sustained") or
+                                                            peaks["bf16_tflops"]) * 1e12 / hbm:
         peak = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
         ach = flops_l / per_launch_s / 1e12
         out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                "peak_source": f"{peaks['source']} cuBLAS BF16 sustained"}
+    elif prec == "bf16":
+        ach = bytes_l / per_launch_s / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
     else:
         alu = fp64_peak if prec == "f64" else fp32_peak
         if flops_l / max(bytes_l, 1.0) > alu / hbm:

@@ -130,15 +130,24 @@ bool tc_coarse_supported(int n);
 void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N,
                                 void* scratch, int* err, cudaStream_t s);
 size_t coarse_inverse_bf16_scratch(int n, int N);
-// Coarse block stencil (d = 16) on the tensor cores: E holds the blocks of every
-// site and direction as BF16 real 32 x 32 operands (launch_embed_stencil_bf16);
-// y = A x (mode 0), b - A x (mode 1), A x plus per-rhs dots (mode 2, partials as
-// launch_block_stencil).  err: device flag set when a bounded wait gave up.
+// Coarse block stencil (d = 16) on the tensor cores for the block-Jacobi
+// smoother: E holds the blocks of every site and direction as BF16 real 32 x 32
+// operands (launch_embed_stencil_bf16); the input x is given as BF16 tiles
+// (per site and 128-rhs tile, 8 KB in the MMA's K-major layout, written by
+// launch_pack_tiles_bf16 or launch_mr_update_tc).  y = A x in FP32 plus per-rhs
+// dots conj(y).x, |y|^2 (partials as launch_block_stencil).  err: device flag set
+// when a bounded wait gave up.
 bool tc_stencil_supported(int d, int N);
 void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cudaStream_t s);
+size_t tc_tiles_bytes(int nsites, int N);
+void launch_pack_tiles_bf16(__nv_bfloat16* rt, const float2* x, int nsites, int N, cudaStream_t s);
+// yh (= or +=) alpha r, r -= alpha p with alpha = dots[j] / dots[N + j]; rt (may be
+// null) receives the BF16 tiles of the new r.  d = 16.
+void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* dots, int nsites, int N, bool first,
+                         __nv_bfloat16* rt, cudaStream_t s);
 int block_stencil_tc_groups(int nsites, int N);
-void launch_block_stencil_tc(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt,
-                             int N, int mode, double2* part, int groups, int* err, cudaStream_t s);
+void launch_block_stencil_tc(float2* y, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx, int lt, int N,
+                             double2* part, int groups, int* err, cudaStream_t s);
 
 // ----------------------------------------------------------------- setup
 // Block-stencil form of the fine Wilson operator: A[site][5][2][2].

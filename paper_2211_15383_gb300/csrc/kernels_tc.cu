@@ -368,23 +368,27 @@ namespace tc {
 // B is precomputed once per level in the canonical layout (2 KB per site and
 // direction).
 //
-// Warp-specialised and persistent: two CTAs per SM, each with 128 rhs and 10
-// warps that hand work on through mbarriers.  A CTA's work is a sequence of
-// jobs (site, direction).
-//   warp 0 (one thread): streams the FP32 rows of each job's neighbour block
-//     (16 rows x 128 rhs, 16 KB) with 1-D bulk copies into a ring of 4 staging
-//     buffers (full / empty barriers);
-//   warps 2-5 (thread = rhs): round the landed block to BF16 and write it as
-//     K-major core-matrix rows (16 B = 4 components of one rhs) of a 128 x 32
-//     tile (two tiles alternate), and at a site's first job copy the site's 10 KB
-//     of B (two site slots alternate);
-//   warp 1 (one thread): issues two MMAs (M = 128, N = 32, K = 16) per job into
-//     the site's TMEM accumulator (two sets of 32 columns alternate by site) and
-//     commits them: to the tile's barrier, and after a site's last job to the
-//     accumulator's;
-//   warps 6-9 (thread = rhs): read a finished accumulator (tcgen05.ld, 32 columns
-//     = 16 complex outputs), hand it back, and store y coalesced along the rhs,
-//     with the dots against x (read from L2) for the smoother.
+// The input of the stencil is not the FP32 vector itself but its BF16 copy
+// stored in the MMA's own operand layout: per site and 128-rhs tile, an 8 KB
+// K-major tile whose row j is the 16 complex components of rhs j (pad rows of a
+// partial last tile are zero).  The kernels that produce the smoother's
+// residuals write that copy as they go (k_pack_tiles for the first one,
+// k_mr_update_tc for the next ones), so the stencil moves 8 KB blocks straight
+// into shared memory and never converts.
+//
+// Warp-specialised and persistent: two CTAs per SM, each over one 128-rhs tile
+// and a strided set of sites; a CTA's work is a sequence of jobs (site,
+// direction).
+//   warp 0 (one thread): streams each job's neighbour tile (8 KB) with a 1-D
+//     bulk copy into a ring of 8 stage buffers, and with a site's first job the
+//     site's 10 KB of B (two site slots alternate);
+//   warp 1 (one thread): issues two MMAs (M = 128, N = 32, K = 16) per job
+//     straight from the stage buffer into the site's TMEM accumulator (two sets
+//     of 32 columns alternate by site) and commits them: to the stage's empty
+//     barrier, and after a site's last job to the accumulator's;
+//   warps 2-5 (thread = rhs): read a finished accumulator (tcgen05.ld, 32
+//     columns = 16 complex outputs), hand it back, store y coalesced along the
+//     rhs, and add the smoother's dots against the site's BF16 input row.
 namespace tcs {
 constexpr int D = 16;
 constexpr int KD = 2 * D;                  // reals per row of X^T (K of one direction)
@@ -392,10 +396,9 @@ constexpr int TILE_A = 128 * KD * 2;       // 8 KB: one 128-rhs BF16 tile of X^T
 constexpr int B_DIR = KD * KD * 2;         // 2 KB: one B(s, dir)
 constexpr int B_SITE = 5 * B_DIR;          // 10 KB per site
 constexpr int CH = 128;                    // rhs per CTA (one 128-row tile)
-constexpr int STG = D * CH * 8;            // 16 KB: FP32 rows of one neighbour block
-constexpr int NSTG = 4;                    // staging ring depth
-constexpr int THREADS = 320;               // 10 warps
-constexpr int SMEM = NSTG * STG + 2 * TILE_A + 2 * B_SITE;   // 100 KB: two CTAs per SM
+constexpr int NSTG = 8;                    // stage ring depth
+constexpr int THREADS = 192;               // 6 warps
+constexpr int SMEM = NSTG * TILE_A + 2 * B_SITE;   // 84 KB: two CTAs per SM
 constexpr int TCOLS = 64;                  // two accumulators of 32 columns
 constexpr int kMaxDevWait = 1 << 26;
 // direction of the o-th job of a site: the neighbours first, the self block last
@@ -425,6 +428,61 @@ __global__ void k_embed_stencil(__nv_bfloat16* __restrict__ E, const float2* __r
     E[sd * (KD * KD) + kmaj32_off(n, k) / 2] = __float2bfloat16(v);
 }
 
+// BF16 tiles of x: rt[(site * T + t) * 4096 + off / 2], zero rows for rhs >= N.
+// Thread = (site, component group of 4, rhs): four FP32 loads, one 16-byte store.
+__global__ void k_pack_tiles(__nv_bfloat16* __restrict__ rt, const float2* __restrict__ x, int nsites, int N) {
+    const int T = gridDim.x;
+    const int j = blockIdx.x * CH + threadIdx.x;
+    const int site = blockIdx.y >> 2, cg = blockIdx.y & 3;
+    float2 v[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        v[p] = (j < N) ? x[((size_t)site * D + 4 * cg + p) * N + j] : make_float2(0.f, 0.f);
+    uint4 w;
+    w.x = pack_bf16(v[0].x, v[0].y);
+    w.y = pack_bf16(v[1].x, v[1].y);
+    w.z = pack_bf16(v[2].x, v[2].y);
+    w.w = pack_bf16(v[3].x, v[3].y);
+    uint8_t* tile = reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A;
+    *reinterpret_cast<uint4*>(tile + kmaj32_off(threadIdx.x, 8 * cg)) = w;
+    (void)nsites;
+}
+
+// Minimal-residual update of the block-Jacobi smoother (alpha = dots[j] / dots[N + j]):
+// yh (=|+=) alpha r, r -= alpha p, and (rt != null) the BF16 tiles of the new r.
+__global__ void k_mr_update_tc(float2* __restrict__ yh, float2* __restrict__ r, const float2* __restrict__ p,
+                               const double2* __restrict__ dots, int N, bool first, __nv_bfloat16* __restrict__ rt) {
+    const int T = gridDim.x;
+    const int j = blockIdx.x * CH + threadIdx.x;
+    const int site = blockIdx.y >> 2, cg = blockIdx.y & 3;
+    float2 rn[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (j < N) {
+        const double2 pr = dots[j];
+        const double pp = dots[N + j].x;
+        const float ax = pp > 0.0 ? (float)(pr.x / pp) : 0.f, ay = pp > 0.0 ? (float)(pr.y / pp) : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const size_t idx = ((size_t)site * D + 4 * cg + q) * N + j;
+            const float2 rv = r[idx], pv = p[idx];
+            float2 e = first ? make_float2(0.f, 0.f) : yh[idx];
+            e.x = fmaf(ax, rv.x, fmaf(-ay, rv.y, e.x));
+            e.y = fmaf(ax, rv.y, fmaf(ay, rv.x, e.y));
+            yh[idx] = e;
+            rn[q] = make_float2(rv.x - fmaf(ax, pv.x, -ay * pv.y), rv.y - fmaf(ax, pv.y, ay * pv.x));
+            r[idx] = rn[q];
+        }
+    }
+    if (rt) {
+        uint4 w;
+        w.x = pack_bf16(rn[0].x, rn[0].y);
+        w.y = pack_bf16(rn[1].x, rn[1].y);
+        w.z = pack_bf16(rn[2].x, rn[2].y);
+        w.w = pack_bf16(rn[3].x, rn[3].y);
+        uint8_t* tile = reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A;
+        *reinterpret_cast<uint4*>(tile + kmaj32_off(threadIdx.x, 8 * cg)) = w;
+    }
+}
+
 // Bounded wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
     const uint32_t a = smem_u32(bar);
@@ -445,24 +503,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int MODE>
 __global__ void __launch_bounds__(THREADS, 2)
-    k_block_stencil_tc(float2* __restrict__ y, const float2* __restrict__ x, const float2* __restrict__ b,
+    k_block_stencil_tc(float2* __restrict__ y, const __nv_bfloat16* __restrict__ xt,
                        const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], tfull[2], tempty[2], afull[2], aempty[2];
+    __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], afull[2], aempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
-    uint8_t* stg = smem;                          // NSTG x 16 KB FP32 staging
-    uint8_t* abuf = smem + NSTG * STG;            // 2 x 8 KB BF16 operand tiles
-    uint8_t* bbuf = abuf + 2 * TILE_A;            // 2 x 10 KB B of a site
+    uint8_t* stg = smem;                          // NSTG x 8 KB BF16 operand tiles
+    uint8_t* bbuf = smem + NSTG * TILE_A;         // 2 x 10 KB B of a site
     volatile int* abrt = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int V = lx * lt;
     const int G = gridDim.x;
-    const int j0 = blockIdx.y * CH;               // first rhs of this CTA
-    const int nch = min(CH, N - j0);              // its rhs count (even)
+    const int T = gridDim.y;                      // 128-rhs tiles
+    const int t = blockIdx.y;                     // this CTA's tile
     const int nsite = (V - (int)blockIdx.x + G - 1) / G;   // sites of this CTA
     const int njobs = 5 * nsite;
 
@@ -474,11 +530,9 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (tid == 0) {
         for (int q = 0; q < NSTG; ++q) {
             mbar_init(&full[q], 1);
-            mbar_init(&empty[q], 4);
+            mbar_init(&empty[q], 1);
         }
         for (int q = 0; q < 2; ++q) {
-            mbar_init(&tfull[q], 4);
-            mbar_init(&tempty[q], 1);
             mbar_init(&afull[q], 1);
             mbar_init(&aempty[q], 4);
         }
@@ -489,21 +543,23 @@ __global__ void __launch_bounds__(THREADS, 2)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
+    const uint8_t* xtb = reinterpret_cast<const uint8_t*>(xt);
 
     if (warp == 0) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
-            const uint32_t row_bytes = (uint32_t)nch * 8u;
             int q = 0;
             for (; q < njobs; ++q) {
-                const int slot = q % NSTG;
+                const int si = q / 5, o = q % 5, slot = q % NSTG, as = si & 1;
                 if (q >= NSTG && !mbar_wait_ab(&empty[slot], (unsigned)((q / NSTG - 1) & 1), abrt)) break;
-                const int site = blockIdx.x + (q / 5) * G;
-                const int nb = nbr_site(site, dir_of(q % 5), lx, lt);
-                mbar_expect_tx(&full[slot], 16u * row_bytes);
-                uint8_t* dst = stg + slot * STG;
-                const float2* src = x + (size_t)nb * D * N + j0;
-                for (int c = 0; c < D; ++c) bulk_g2s(dst + c * (CH * 8), src + (size_t)c * N, row_bytes, &full[slot]);
+                // the B slot is free once the MMAs of the site two back are done
+                if (o == 0 && si >= 2 && !mbar_wait_ab(&afull[as], (unsigned)(((si - 2) >> 1) & 1), abrt)) break;
+                const int site = blockIdx.x + si * G;
+                const int nb = nbr_site(site, dir_of(o), lx, lt);
+                mbar_expect_tx(&full[slot], (uint32_t)TILE_A + (o == 0 ? (uint32_t)B_SITE : 0u));
+                bulk_g2s(stg + slot * TILE_A, xtb + ((size_t)nb * T + t) * TILE_A, (uint32_t)TILE_A, &full[slot]);
+                if (o == 0)
+                    bulk_g2s(bbuf + as * B_SITE, E + (size_t)site * (B_SITE / 2), (uint32_t)B_SITE, &full[slot]);
             }
             if (*abrt) {
                 // copies still in flight land before the shared memory goes back: the
@@ -515,13 +571,13 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t IDESC = instr_desc(128, 32);
-            int last_tile = -1, last_acc = -1;
+            int last = -1;
             for (int q = 0; q < njobs; ++q) {
-                const int si = q / 5, o = q % 5, ab = q & 1, as = si & 1;
+                const int si = q / 5, o = q % 5, slot = q % NSTG, as = si & 1;
                 if (o == 0 && si >= 2 && !mbar_wait_ab(&aempty[as], (unsigned)(((si >> 1) - 1) & 1), abrt)) break;
-                if (!mbar_wait_ab(&tfull[ab], (unsigned)((q >> 1) & 1), abrt)) break;
+                if (!mbar_wait_ab(&full[slot], (unsigned)((q / NSTG) & 1), abrt)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sa = smem_u32(abuf + ab * TILE_A);
+                const uint32_t sa = smem_u32(stg + slot * TILE_A);
                 const uint32_t sb = smem_u32(bbuf + as * B_SITE + dir_of(o) * B_DIR);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
@@ -534,61 +590,22 @@ __global__ void __launch_bounds__(THREADS, 2)
                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&tempty[ab])));
-                last_tile = q;
-                if (o == 4) {
+                    smem_u32(&empty[slot])));
+                if (o == 4)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&afull[as])));
-                    last_acc = si;
-                }
+                last = q;
             }
-            if (*abrt && last_tile >= 0) {
-                // MMAs in flight complete before the TMEM goes back
-                mbar_wait(&tempty[last_tile & 1], (unsigned)((last_tile >> 1) & 1));
+            if (*abrt && last >= 0) {
+                // MMAs in flight complete before the TMEM and shared memory go back
+                mbar_wait(&empty[last % NSTG], (unsigned)((last / NSTG) & 1));
             }
-            (void)last_acc;
-        }
-    } else if (warp < 6) {
-        // ---------------------------------------------------------------- converters
-        const int j = (warp - 2) * 32 + lane;     // rhs of this thread
-        for (int q = 0; q < njobs; ++q) {
-            const int si = q / 5, o = q % 5, slot = q % NSTG, ab = q & 1, as = si & 1;
-            if (!mbar_wait_ab(&full[slot], (unsigned)((q / NSTG) & 1), abrt)) break;
-            if (q >= 2 && !mbar_wait_ab(&tempty[ab], (unsigned)(((q >> 1) - 1) & 1), abrt)) break;
-            if (o == 0) {
-                // B of this site, once the MMAs of the site two back (same slot) are done
-                if (si >= 2 && !mbar_wait_ab(&afull[as], (unsigned)(((si - 2) >> 1) & 1), abrt)) break;
-                const uint4* bs = reinterpret_cast<const uint4*>(E + (size_t)(blockIdx.x + si * G) * (B_SITE / 2));
-                uint4* bd = reinterpret_cast<uint4*>(bbuf + as * B_SITE);
-                for (int u = j; u < B_SITE / 16; u += 128) bd[u] = bs[u];
-            }
-            const float2* sx = reinterpret_cast<const float2*>(stg + slot * STG);
-            uint4 wv[4];
-#pragma unroll
-            for (int cg = 0; cg < 4; ++cg) {
-                float2 v[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) v[p] = (j < nch) ? sx[(4 * cg + p) * CH + j] : make_float2(0.f, 0.f);
-                wv[cg].x = pack_bf16(v[0].x, v[0].y);
-                wv[cg].y = pack_bf16(v[1].x, v[1].y);
-                wv[cg].z = pack_bf16(v[2].x, v[2].y);
-                wv[cg].w = pack_bf16(v[3].x, v[3].y);
-            }
-            // the loaded values are consumed: the staging slot may be refilled
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            uint8_t* at = abuf + ab * TILE_A;
-#pragma unroll
-            for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(at + kmaj32_off(j, 8 * cg)) = wv[cg];
-            // generic-proxy writes (tile, B) become visible to the tensor core
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tfull[ab]);
         }
     } else {
         // ---------------------------------------------------------------- epilogue
         const int quarter = warp & 3;             // TMEM lanes this warp may read
         const int jl = quarter * 32 + lane;
+        const int j = t * CH + jl;
         float2 dyx = make_float2(0.f, 0.f);
         float dyy = 0.f;
         bool ok = true;
@@ -615,30 +632,30 @@ __global__ void __launch_bounds__(THREADS, 2)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(&aempty[as]);      // accumulator may be overwritten
-            if (jl < nch) {
+            if (j < N) {
                 const int site = blockIdx.x + si * G;
-                const int j = j0 + jl;
+                // the site's own BF16 input row (16 components of rhs j) for the dots
+                const uint8_t* own = xtb + ((size_t)site * T + t) * TILE_A;
+                uint4 xw[4];
+#pragma unroll
+                for (int cg = 0; cg < 4; ++cg) xw[cg] = *reinterpret_cast<const uint4*>(own + kmaj32_off(jl, 8 * cg));
 #pragma unroll
                 for (int co = 0; co < D; ++co) {
                     const size_t idx = ((size_t)site * D + co) * N + j;
-                    float2 ov = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
-                    if (MODE == 1) {
-                        const float2 bv = b[idx];
-                        ov = make_float2(bv.x - ov.x, bv.y - ov.y);
-                    }
+                    const float2 ov = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
                     y[idx] = ov;
-                    if (MODE == 2) {
-                        const float2 xv = x[idx];
-                        // conj(y) * x, accumulated per rhs
-                        dyx.x = fmaf(ov.x, xv.x, fmaf(ov.y, xv.y, dyx.x));
-                        dyx.y = fmaf(ov.x, xv.y, fmaf(-ov.y, xv.x, dyx.y));
-                        dyy = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, dyy));
-                    }
+                    const uint32_t wbits = (co & 3) == 0 ? xw[co >> 2].x
+                                           : (co & 3) == 1 ? xw[co >> 2].y
+                                           : (co & 3) == 2 ? xw[co >> 2].z : xw[co >> 2].w;
+                    const float2 xv = make_float2(__uint_as_float(wbits << 16), __uint_as_float(wbits & 0xFFFF0000u));
+                    // conj(y) * x, accumulated per rhs
+                    dyx.x = fmaf(ov.x, xv.x, fmaf(ov.y, xv.y, dyx.x));
+                    dyx.y = fmaf(ov.x, xv.y, fmaf(-ov.y, xv.x, dyx.y));
+                    dyy = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, dyy));
                 }
             }
         }
-        if (ok && MODE == 2 && jl < nch) {
-            const int j = j0 + jl;
+        if (ok && j < N) {
             part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx.x, (double)dyx.y);
             part[((long long)1 * N + j) * G + blockIdx.x] = make_double2((double)dyy, 0.0);
         }
@@ -651,7 +668,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 }  // namespace tcs
 }  // namespace tc
 
-bool tc_stencil_supported(int d, int N) { return d == tc::tcs::D && N >= 2 && N % 2 == 0; }
+bool tc_stencil_supported(int d, int N) { return d == tc::tcs::D && N >= 1 && N <= 65535 * tc::tcs::CH; }
 
 void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cudaStream_t s) {
     const long long tot = (long long)nsites * 5 * tc::tcs::KD * tc::tcs::KD;
@@ -659,33 +676,41 @@ void launch_embed_stencil_bf16(__nv_bfloat16* E, const float2* A, int nsites, cu
     MG_LAUNCHED();
 }
 
-// Two persistent CTAs per SM (100 KB of shared memory each) over the 128-rhs chunks.
+static int tc_tiles(int N) { return (N + tc::tcs::CH - 1) / tc::tcs::CH; }
+
+size_t tc_tiles_bytes(int nsites, int N) { return (size_t)nsites * tc_tiles(N) * tc::tcs::TILE_A; }
+
+void launch_pack_tiles_bf16(__nv_bfloat16* rt, const float2* x, int nsites, int N, cudaStream_t s) {
+    MG_REQUIRE(nsites <= 16383, MGMLMC_EINVAL, "BF16 tiles: at most 16383 sites");
+    tc::tcs::k_pack_tiles<<<dim3(tc_tiles(N), 4 * nsites), tc::tcs::CH, 0, s>>>(rt, x, nsites, N);
+    MG_LAUNCHED();
+}
+
+void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* dots, int nsites, int N, bool first,
+                         __nv_bfloat16* rt, cudaStream_t s) {
+    MG_REQUIRE(nsites <= 16383, MGMLMC_EINVAL, "BF16 tiles: at most 16383 sites");
+    tc::tcs::k_mr_update_tc<<<dim3(tc_tiles(N), 4 * nsites), tc::tcs::CH, 0, s>>>(yh, r, p, dots, N, first, rt);
+    MG_LAUNCHED();
+}
+
+// Two persistent CTAs per SM (84 KB of shared memory each) over the 128-rhs tiles.
 int block_stencil_tc_groups(int nsites, int N) {
-    const int chunks = (N + tc::tcs::CH - 1) / tc::tcs::CH;
-    int g = 2 * kNumSM / chunks;
+    int g = 2 * kNumSM / tc_tiles(N);
     if (g < 1) g = 1;
     return nsites < g ? nsites : g;
 }
 
-template <int MODE>
-static void bstc_launch(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt, int N,
-                        double2* part, int groups, int* err, cudaStream_t s) {
-    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::tcs::SMEM));
-    dim3 g(groups, (N + tc::tcs::CH - 1) / tc::tcs::CH);
-    tc::tcs::k_block_stencil_tc<MODE><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, x, b, E, lx, lt, N, part, err);
-    MG_LAUNCHED();
-}
-
-void launch_block_stencil_tc(float2* y, const float2* x, const float2* b, const __nv_bfloat16* E, int lx, int lt,
-                             int N, int mode, double2* part, int groups, int* err, cudaStream_t s) {
-    MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16 and an even N >= 2");
+void launch_block_stencil_tc(float2* y, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx, int lt, int N,
+                             double2* part, int groups, int* err, cudaStream_t s) {
+    MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16");
     MG_REQUIRE(groups >= 1 && groups <= lx * lt, MGMLMC_EINVAL, "tensor-core stencil: bad grid");
-    MG_REQUIRE(((uintptr_t)x & 15) == 0 && ((uintptr_t)E & 15) == 0, MGMLMC_EINVAL,
-               "tensor-core stencil: x and the operands must be 16-byte aligned");
-    if (mode == 0) bstc_launch<0>(y, x, b, E, lx, lt, N, part, groups, err, s);
-    else if (mode == 1) bstc_launch<1>(y, x, b, E, lx, lt, N, part, groups, err, s);
-    else bstc_launch<2>(y, x, b, E, lx, lt, N, part, groups, err, s);
+    MG_REQUIRE(((uintptr_t)xt & 15) == 0 && ((uintptr_t)E & 15) == 0, MGMLMC_EINVAL,
+               "tensor-core stencil: operands must be 16-byte aligned");
+    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::tcs::SMEM));
+    dim3 g(groups, tc_tiles(N));
+    tc::tcs::k_block_stencil_tc<<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, xt, E, lx, lt, N, part, err);
+    MG_LAUNCHED();
 }
 
 }  // namespace mg

@@ -103,38 +103,62 @@ static int* device_error_flag(Ctx& c) {
 }
 
 // The block stencil of D M^{-1} runs on the tensor cores (BF16 operands, FP32
-// accumulation) when mg_precision is 16: the smoother only preconditions the
-// FP32 FGMRES, whose own matrix-vector products stay FP32.
+// accumulation) when mg_precision is 16 and d = 16: the smoother only
+// preconditions the FP32 FGMRES, whose own matrix-vector products stay FP32.
 template <typename C> static bool tc_smoother(const Level&, int) { return false; }
 template <> bool tc_smoother<float2>(const Level& L, int N) { return L.Ahat16 && tc_stencil_supported(L.d, N); }
-template <typename C>
-static void launch_hat_tc(Ctx&, const Level&, C*, const C*, int, double2*, int) {}
-template <>
-void launch_hat_tc<float2>(Ctx& c, const Level& L, float2* y, const float2* x, int N, double2* part, int groups) {
-    launch_block_stencil_tc(y, x, nullptr, L.Ahat16, L.lx, L.lt, N, 2, part, groups, device_error_flag(c), c.stream);
+
+static __nv_bfloat16* tc_tiles(Ctx& c, int l, int N) {
+    return reinterpret_cast<__nv_bfloat16*>(c.scratch_bytes(nm("mr_rt", l, 2), tc_tiles_bytes(c.lev[l].nsites, N)));
+}
+
+// y = (D_l M_l^{-1}) x on the tensor cores, x given as its BF16 tiles xt; dots as apply_Dhat
+// (against the BF16 x).
+static void apply_Dhat_tc(Ctx& c, int l, float2* y, const __nv_bfloat16* xt, int N, double2* dots) {
+    const Level& L = c.lev[l];
+    const int groups = block_stencil_tc_groups(L.nsites, N);
+    double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
+    {
+        // algorithmic traffic: BF16 x (4 B per complex) and FP32 y once, the BF16 operands once
+        ProfScope ps(c, "D" + std::to_string(l + 1) + ".bf16",
+                     (double)L.n * N * (4 + 8) + 5.0 * L.nsites * 8.0 * L.d * L.d,
+                     40.0 * L.d * L.d * (double)L.nsites * N);
+        launch_block_stencil_tc(y, xt, L.Ahat16, L.lx, L.lt, N, part, groups, device_error_flag(c), c.stream);
+    }
+    ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
+    launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
+}
+
+static void pack_tiles(Ctx& c, int l, __nv_bfloat16* xt, const float2* x, int N) {
+    const Level& L = c.lev[l];
+    ProfScope ps(c, "pack" + std::to_string(l + 1) + ".bf16", (double)L.n * N * (8 + 4), 0.0);
+    launch_pack_tiles_bf16(xt, x, L.nsites, N, c.stream);
 }
 
 // y = (D_l M_l^{-1}) x with the precomputed block stencil (block-Jacobi smoother).
 template <typename C>
 static void apply_Dhat(Ctx& c, int l, C* y, const C* x, int N, double2* dots) {
     const Level& L = c.lev[l];
-    const bool tc = tc_smoother<C>(L, N);
-    const int groups = tc ? block_stencil_tc_groups(L.nsites, N) : block_stencil_groups(L.nsites, L.d, N);
+    const int groups = block_stencil_groups(L.nsites, L.d, N);
     const double s = sizeof(C);
     double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
-    const double flops = 40.0 * L.d * L.d * (double)L.nsites * N;
-    if (tc) {
-        // algorithmic traffic: FP32 x and y once, the BF16 operands (4 d^2 reals per block) once
-        ProfScope ps(c, "D" + std::to_string(l + 1) + ".bf16", (double)L.n * N * s * 2 + 5.0 * L.nsites * 8.0 * L.d * L.d,
-                     flops);
-        launch_hat_tc<C>(c, L, y, x, N, part, groups);
-    } else {
+    {
         ProfScope ps(c, "D" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)),
-                     (double)L.n * N * s * 2 + 5.0 * L.nsites * L.d * L.d * s, flops);
+                     (double)L.n * N * s * 2 + 5.0 * L.nsites * L.d * L.d * s,
+                     40.0 * L.d * L.d * (double)L.nsites * N);
         launch_block_stencil<C>(y, x, nullptr, hat_blocks<C>(L), L.lx, L.lt, L.d, N, 2, part, groups, c.stream);
     }
     ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
     launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
+}
+
+template <typename C> static bool apply_smoother_tc(Ctx&, int, C*, const C*, int, double2*) { return false; }
+template <> bool apply_smoother_tc<float2>(Ctx& c, int l, float2* y, const float2* x, int N, double2* dots) {
+    if (!tc_smoother<float2>(c.lev[l], N)) return false;
+    __nv_bfloat16* xt = tc_tiles(c, l, N);
+    pack_tiles(c, l, xt, x, N);
+    apply_Dhat_tc(c, l, y, xt, N, dots);
+    return true;
 }
 
 template <typename C>
@@ -142,7 +166,7 @@ void apply_smoother_operator(Ctx& c, int l, C* y, const C* x, int N, double2* do
     MG_REQUIRE(l >= 1 && l < c.L - 1 && hat_blocks<C>(c.lev[l]), MGMLMC_EINVAL,
                "smoother operator: only coarse levels above the coarsest");
     if (!dots) dots = c.scratch<double2>("smop_dots", 2 * (size_t)N);
-    apply_Dhat<C>(c, l, y, x, N, dots);
+    if (!apply_smoother_tc<C>(c, l, y, x, N, dots)) apply_Dhat<C>(c, l, y, x, N, dots);
 }
 
 template <typename C>
@@ -188,8 +212,33 @@ template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int 
 
 // nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual
 // on entry and is overwritten.
+// Block-Jacobi MR on the tensor cores: the residual's BF16 tiles are packed once,
+// then each update writes the next ones.
+template <typename C> static bool mr_smooth_tc(Ctx&, int, C*, C*, int, int, bool) { return false; }
+template <> bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bool e_zero) {
+    const Level& L = c.lev[l];
+    if (nu <= 0 || !tc_smoother<float2>(L, N)) return false;
+    float2* p = c.scratch<float2>(nm("mr_p", l, sizeof(float2)), (size_t)L.n * N);
+    float2* yh = c.scratch<float2>(nm("mr_y", l, sizeof(float2)), (size_t)L.n * N);
+    double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(float2)), 2 * (size_t)N);
+    __nv_bfloat16* rt = tc_tiles(c, l, N);
+    pack_tiles(c, l, rt, r, N);
+    for (int s = 0; s < nu; ++s) {
+        apply_Dhat_tc(c, l, p, rt, N, dots);
+        const bool more = s + 1 < nu;
+        ProfScope ps(c, "mr" + std::to_string(l + 1) + ".f32", (double)L.n * N * (5 * 8 + (more ? 4 : 0)),
+                     16.0 * L.n * N);
+        launch_mr_update_tc(yh, r, p, dots, L.nsites, N, s == 0, more ? rt : nullptr, c.stream);
+    }
+    ProfScope ps(c, "bjac" + std::to_string(l + 1) + ".f32", 3.0 * L.n * N * sizeof(float2),
+                 8.0 * L.d * (double)L.n * N);
+    launch_block_diag_apply<float2>(e, yh, L.Minv32, L.nsites, L.d, N, !e_zero, c.stream);
+    return true;
+}
+
 template <typename C>
 static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero) {
+    if (mr_smooth_tc<C>(c, l, e, r, N, nu, e_zero)) return;
     const Level& L = c.lev[l];
     C* p = c.scratch<C>(nm("mr_p", l, sizeof(C)), (size_t)L.n * N);
     double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(C)), 2 * (size_t)N);
