@@ -450,36 +450,53 @@ __global__ void k_pack_tiles(__nv_bfloat16* __restrict__ rt, const float2* __res
 
 // Minimal-residual update of the block-Jacobi smoother (alpha = dots[j] / dots[N + j]):
 // yh (=|+=) alpha r, r -= alpha p, and (rt != null) the BF16 tiles of the new r.
-__global__ void k_mr_update_tc(float2* __restrict__ yh, float2* __restrict__ r, const float2* __restrict__ p,
-                               const double2* __restrict__ dots, int N, bool first, __nv_bfloat16* __restrict__ rt) {
+// Thread = (site, rhs): the 16 rows of the site, four 16-byte tile pieces.
+__global__ void __launch_bounds__(CH) k_mr_update_tc(float2* __restrict__ yh, float2* __restrict__ r,
+                                                    const float2* __restrict__ p, const double2* __restrict__ dots,
+                                                    int N, bool first, __nv_bfloat16* __restrict__ rt) {
     const int T = gridDim.x;
     const int j = blockIdx.x * CH + threadIdx.x;
-    const int site = blockIdx.y >> 2, cg = blockIdx.y & 3;
-    float2 rn[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const int site = blockIdx.y;
+    float ax = 0.f, ay = 0.f;
     if (j < N) {
         const double2 pr = dots[j];
         const double pp = dots[N + j].x;
-        const float ax = pp > 0.0 ? (float)(pr.x / pp) : 0.f, ay = pp > 0.0 ? (float)(pr.y / pp) : 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const size_t idx = ((size_t)site * D + 4 * cg + q) * N + j;
-            const float2 rv = r[idx], pv = p[idx];
-            float2 e = first ? make_float2(0.f, 0.f) : yh[idx];
-            e.x = fmaf(ax, rv.x, fmaf(-ay, rv.y, e.x));
-            e.y = fmaf(ax, rv.y, fmaf(ay, rv.x, e.y));
-            yh[idx] = e;
-            rn[q] = make_float2(rv.x - fmaf(ax, pv.x, -ay * pv.y), rv.y - fmaf(ax, pv.y, ay * pv.x));
-            r[idx] = rn[q];
+        if (pp > 0.0) {
+            ax = (float)(pr.x / pp);
+            ay = (float)(pr.y / pp);
         }
     }
-    if (rt) {
-        uint4 w;
-        w.x = pack_bf16(rn[0].x, rn[0].y);
-        w.y = pack_bf16(rn[1].x, rn[1].y);
-        w.z = pack_bf16(rn[2].x, rn[2].y);
-        w.w = pack_bf16(rn[3].x, rn[3].y);
-        uint8_t* tile = reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A;
-        *reinterpret_cast<uint4*>(tile + kmaj32_off(threadIdx.x, 8 * cg)) = w;
+    uint8_t* tile = rt ? reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A : nullptr;
+    // all loads of the thread first (memory-level parallelism), then the arithmetic
+    float2 rv[D], pv[D], ev[D];
+    const size_t base = (size_t)site * D * N + j;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const bool in = j < N;
+        rv[c] = in ? r[base + (size_t)c * N] : make_float2(0.f, 0.f);
+        pv[c] = in ? p[base + (size_t)c * N] : make_float2(0.f, 0.f);
+        ev[c] = (in && !first) ? yh[base + (size_t)c * N] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        ev[c].x = fmaf(ax, rv[c].x, fmaf(-ay, rv[c].y, ev[c].x));
+        ev[c].y = fmaf(ax, rv[c].y, fmaf(ay, rv[c].x, ev[c].y));
+        rv[c] = make_float2(rv[c].x - fmaf(ax, pv[c].x, -ay * pv[c].y), rv[c].y - fmaf(ax, pv[c].y, ay * pv[c].x));
+        if (j < N) {
+            yh[base + (size_t)c * N] = ev[c];
+            r[base + (size_t)c * N] = rv[c];
+        }
+    }
+    if (tile) {
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+            uint4 w;
+            w.x = pack_bf16(rv[4 * cg].x, rv[4 * cg].y);
+            w.y = pack_bf16(rv[4 * cg + 1].x, rv[4 * cg + 1].y);
+            w.z = pack_bf16(rv[4 * cg + 2].x, rv[4 * cg + 2].y);
+            w.w = pack_bf16(rv[4 * cg + 3].x, rv[4 * cg + 3].y);
+            *reinterpret_cast<uint4*>(tile + kmaj32_off(threadIdx.x, 8 * cg)) = w;
+        }
     }
 }
 
@@ -688,8 +705,8 @@ void launch_pack_tiles_bf16(__nv_bfloat16* rt, const float2* x, int nsites, int 
 
 void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* dots, int nsites, int N, bool first,
                          __nv_bfloat16* rt, cudaStream_t s) {
-    MG_REQUIRE(nsites <= 16383, MGMLMC_EINVAL, "BF16 tiles: at most 16383 sites");
-    tc::tcs::k_mr_update_tc<<<dim3(tc_tiles(N), 4 * nsites), tc::tcs::CH, 0, s>>>(yh, r, p, dots, N, first, rt);
+    MG_REQUIRE(nsites <= 65535, MGMLMC_EINVAL, "BF16 tiles: at most 65535 sites");
+    tc::tcs::k_mr_update_tc<<<dim3(tc_tiles(N), nsites), tc::tcs::CH, 0, s>>>(yh, r, p, dots, N, first, rt);
     MG_LAUNCHED();
 }
 
