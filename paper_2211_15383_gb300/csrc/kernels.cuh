@@ -61,6 +61,10 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
                       cudaStream_t s);
+// As launch_multiaxpy, and norm2[j] = |w_j|^2 of the updated w (part: reduce_groups(n, N) * N scratch).
+template <typename C>
+void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
+                            double* norm2, double* part, cudaStream_t s);
 // Sum of partials: out[j] = sum_g part[g][j] (count = values per group).
 void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s);
 void launch_finalize(double* out, const double* part, int groups, int count, cudaStream_t s);

@@ -168,9 +168,10 @@ __global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, 
 
 template <typename C>
 __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef, int m, const C* __restrict__ V,
-                            double sign, long long n, int N) {
+                            double sign, long long n, int N, double* __restrict__ norm_part) {
     using R = re_t<C>;
     __shared__ C cf[64][kRhsTile];
+    __shared__ double sh[kRowLanes][kRhsTile + 1];
     const int j = blockIdx.x * kRhsTile + threadIdx.x;
     const long long stride = n * (long long)N;
     for (int k = threadIdx.y; k < m; k += kRowLanes) {
@@ -178,12 +179,24 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
         cf[k][threadIdx.x] = mk((R)(c.x * sign), (R)(c.y * sign));
     }
     __syncthreads();
-    if (j >= N) return;
-    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
-         i += (long long)gridDim.y * kRowLanes) {
-        C acc = w[i * N + j];
-        for (int k = 0; k < m; ++k) cfma(acc, cf[k][threadIdx.x], V[k * stride + i * N + j]);
-        w[i * N + j] = acc;
+    R nrm = 0;
+    if (j < N)
+        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
+             i += (long long)gridDim.y * kRowLanes) {
+            C acc = w[i * N + j];
+            for (int k = 0; k < m; ++k) cfma(acc, cf[k][threadIdx.x], V[k * stride + i * N + j]);
+            w[i * N + j] = acc;
+            nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
+        }
+    if (norm_part) {
+        // |w|^2 partials of the updated vector, as k_norm2 writes them
+        sh[threadIdx.y][threadIdx.x] = (double)nrm;
+        __syncthreads();
+        if (threadIdx.y == 0 && j < N) {
+            double t = sh[0][threadIdx.x];
+            for (int r = 1; r < kRowLanes; ++r) t += sh[r][threadIdx.x];
+            norm_part[(long long)blockIdx.y * N + j] = t;
+        }
     }
 }
 
@@ -258,7 +271,7 @@ void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sig
     MG_LAUNCHED();
 }
 
-int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
+int reduce_groups(long long n, int N) { return row_groups(n, N, 8); }
 
 // Row-major partials: out[i] = sum_g part[i * groups + g]; one warp per output,
 // lanes add g = lane, lane + 32, ... in order, then a fixed shuffle tree.
@@ -321,8 +334,17 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
-    k_multiaxpy<C><<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N);
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), reduce_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
     MG_LAUNCHED();
+}
+template <typename C>
+void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
+                            double* norm2, double* part, cudaStream_t s) {
+    MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
+    const int G = reduce_groups(n, N);
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
+    MG_LAUNCHED();
+    launch_finalize(norm2, part, G, N, s);
 }
 
 #define INST_C(C)                                                                                   \
@@ -333,7 +355,9 @@ void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign,
     template void launch_multidot<C>(double2*, const C*, int, const C*, long long, int, double2*,    \
                                      cudaStream_t);                                                  \
     template void launch_multiaxpy<C>(C*, const double2*, int, const C*, double, long long, int,     \
-                                      cudaStream_t);
+                                      cudaStream_t);                                                 \
+    template void launch_multiaxpy_norm2<C>(C*, const double2*, int, const C*, double, long long, int, \
+                                            double*, double*, cudaStream_t);
 INST_C(double2)
 INST_C(float2)
 #define INST_CC(A, B)                                                                               \

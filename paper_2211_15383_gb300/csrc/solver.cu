@@ -379,16 +379,21 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
                 const int passes = (sz == sizeof(double2)) ? 2 : 1;
                 ProfScope ps(c, "orth." + std::string(prec_tag(sz)), passes * (2 * j + 5) * (double)nN * sz,
                              passes * 2.0 * 8.0 * (j + 1) * (double)nN);
+                // the last axpy also returns |Vn|^2 (its partials), saving a pass over Vn
+                double* npart = c.scratch<double>("part_nrm", (size_t)reduce_groups(n, N) * N);
                 launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
-                launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream);
                 if (passes == 2) {
+                    launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream);
                     launch_multidot<C>(h2, V, j + 1, Vn, n, N, part, c.stream);
-                    launch_multiaxpy<C>(Vn, h2, j + 1, V, -1.0, n, N, c.stream);
+                    launch_multiaxpy_norm2<C>(Vn, h2, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
                     k_add2<<<((j + 1) * N + 127) / 128, 128, 0, c.stream>>>(h, h2, (j + 1) * N);
                     MG_LAUNCHED();
+                } else {
+                    launch_multiaxpy_norm2<C>(Vn, h, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
                 }
             }
-            norms<C>(c, hnorm, Vn, n, N);
+            k_sqrt_inplace<<<(N + 127) / 128, 128, 0, c.stream>>>(hnorm, N);
+            MG_LAUNCHED();
             launch_scale_rhs<C, C>(Vn, Vn, hnorm, true, n, N, c.stream);
             launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, m, N, c.stream);
             ++it;
