@@ -149,9 +149,13 @@ void launch_pack_tiles_bf16(__nv_bfloat16* rt, const float2* x, int nsites, int 
 // null) receives the BF16 tiles of the new r.  d = 16.
 void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* dots, int nsites, int N, bool first,
                          __nv_bfloat16* rt, cudaStream_t s);
+// yh (= or +=) alpha r, r -= alpha p with r and p as BF16 tiles (r updated in place).
+void launch_mr_update_bf16(float2* yh, __nv_bfloat16* rt, const __nv_bfloat16* pt, const double2* dots, int nsites,
+                           int N, bool first, cudaStream_t s);
 int block_stencil_tc_groups(int nsites, int N);
-void launch_block_stencil_tc(float2* y, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx, int lt, int N,
-                             double2* part, int groups, int* err, cudaStream_t s);
+// Output: y (FP32 rows) or yt (BF16 tiles), exactly one non-null.
+void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx,
+                             int lt, int N, double2* part, int groups, int* err, cudaStream_t s);
 
 // ----------------------------------------------------------------- setup
 // Block-stencil form of the fine Wilson operator: A[site][5][2][2].

@@ -500,6 +500,51 @@ __global__ void __launch_bounds__(CH) k_mr_update_tc(float2* __restrict__ yh, fl
     }
 }
 
+// Minimal-residual update with r and p held only as BF16 tiles (the smoother's
+// residual needs no more than a few digits): yh (=|+=) alpha r (FP32), r -= alpha p
+// (BF16 tiles, in place).  Thread = (site, rhs): one row of each tile.
+__global__ void __launch_bounds__(CH) k_mr_update_bf16(float2* __restrict__ yh, __nv_bfloat16* __restrict__ rt,
+                                                      const __nv_bfloat16* __restrict__ pt,
+                                                      const double2* __restrict__ dots, int N, bool first) {
+    const int T = gridDim.x;
+    const int jl = threadIdx.x, j = blockIdx.x * CH + jl;
+    const int site = blockIdx.y;
+    if (j >= N) return;                           // pad rows stay zero
+    const double2 pr = dots[j];
+    const double pp = dots[N + j].x;
+    const float ax = pp > 0.0 ? (float)(pr.x / pp) : 0.f, ay = pp > 0.0 ? (float)(pr.y / pp) : 0.f;
+    const size_t toff = ((size_t)site * T + blockIdx.x) * TILE_A;
+    uint8_t* rrow = reinterpret_cast<uint8_t*>(rt) + toff;
+    const uint8_t* prow = reinterpret_cast<const uint8_t*>(pt) + toff;
+    uint4 rw[4], pw[4];
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) {
+        rw[cg] = *reinterpret_cast<const uint4*>(rrow + kmaj32_off(jl, 8 * cg));
+        pw[cg] = *reinterpret_cast<const uint4*>(prow + kmaj32_off(jl, 8 * cg));
+    }
+    const size_t base = (size_t)site * D * N + j;
+    float2 ev[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) ev[c] = first ? make_float2(0.f, 0.f) : yh[base + (size_t)c * N];
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) {
+        uint32_t rr[4] = {rw[cg].x, rw[cg].y, rw[cg].z, rw[cg].w};
+        const uint32_t pq[4] = {pw[cg].x, pw[cg].y, pw[cg].z, pw[cg].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = 4 * cg + q;
+            const float rx = __uint_as_float(rr[q] << 16), ry = __uint_as_float(rr[q] & 0xFFFF0000u);
+            const float px = __uint_as_float(pq[q] << 16), py = __uint_as_float(pq[q] & 0xFFFF0000u);
+            ev[c].x = fmaf(ax, rx, fmaf(-ay, ry, ev[c].x));
+            ev[c].y = fmaf(ax, ry, fmaf(ay, rx, ev[c].y));
+            rr[q] = pack_bf16(rx - fmaf(ax, px, -ay * py), ry - fmaf(ax, py, ay * px));
+        }
+        *reinterpret_cast<uint4*>(rrow + kmaj32_off(jl, 8 * cg)) = make_uint4(rr[0], rr[1], rr[2], rr[3]);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) yh[base + (size_t)c * N] = ev[c];
+}
+
 // Bounded wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
     const uint32_t a = smem_u32(bar);
@@ -520,8 +565,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// TILE_OUT: y is written as BF16 tiles (yt) instead of FP32 rows (y).
+template <bool TILE_OUT>
 __global__ void __launch_bounds__(THREADS, 2)
-    k_block_stencil_tc(float2* __restrict__ y, const __nv_bfloat16* __restrict__ xt,
+    k_block_stencil_tc(float2* __restrict__ y, __nv_bfloat16* __restrict__ yt, const __nv_bfloat16* __restrict__ xt,
                        const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -649,6 +696,13 @@ __global__ void __launch_bounds__(THREADS, 2)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(&aempty[as]);      // accumulator may be overwritten
+            if (TILE_OUT && j >= N) {
+                // pad rows of a partial tile stay zero
+                uint8_t* yrow = reinterpret_cast<uint8_t*>(yt) + ((size_t)(blockIdx.x + si * G) * T + t) * TILE_A;
+#pragma unroll
+                for (int cg = 0; cg < 4; ++cg)
+                    *reinterpret_cast<uint4*>(yrow + kmaj32_off(jl, 8 * cg)) = make_uint4(0u, 0u, 0u, 0u);
+            }
             if (j < N) {
                 const int site = blockIdx.x + si * G;
                 // the site's own BF16 input row (16 components of rhs j) for the dots
@@ -656,11 +710,23 @@ __global__ void __launch_bounds__(THREADS, 2)
                 uint4 xw[4];
 #pragma unroll
                 for (int cg = 0; cg < 4; ++cg) xw[cg] = *reinterpret_cast<const uint4*>(own + kmaj32_off(jl, 8 * cg));
+                if (TILE_OUT) {
+                    uint8_t* yrow = reinterpret_cast<uint8_t*>(yt) + ((size_t)site * T + t) * TILE_A;
+#pragma unroll
+                    for (int cg = 0; cg < 4; ++cg) {
+                        uint4 w;
+                        w.x = pack_bf16(__uint_as_float(r[8 * cg + 0]), __uint_as_float(r[8 * cg + 1]));
+                        w.y = pack_bf16(__uint_as_float(r[8 * cg + 2]), __uint_as_float(r[8 * cg + 3]));
+                        w.z = pack_bf16(__uint_as_float(r[8 * cg + 4]), __uint_as_float(r[8 * cg + 5]));
+                        w.w = pack_bf16(__uint_as_float(r[8 * cg + 6]), __uint_as_float(r[8 * cg + 7]));
+                        *reinterpret_cast<uint4*>(yrow + kmaj32_off(jl, 8 * cg)) = w;
+                    }
+                }
 #pragma unroll
                 for (int co = 0; co < D; ++co) {
                     const size_t idx = ((size_t)site * D + co) * N + j;
                     const float2 ov = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
-                    y[idx] = ov;
+                    if (!TILE_OUT) y[idx] = ov;
                     const uint32_t wbits = (co & 3) == 0 ? xw[co >> 2].x
                                            : (co & 3) == 1 ? xw[co >> 2].y
                                            : (co & 3) == 2 ? xw[co >> 2].z : xw[co >> 2].w;
@@ -717,16 +783,32 @@ int block_stencil_tc_groups(int nsites, int N) {
     return nsites < g ? nsites : g;
 }
 
-void launch_block_stencil_tc(float2* y, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx, int lt, int N,
-                             double2* part, int groups, int* err, cudaStream_t s) {
+void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx,
+                             int lt, int N, double2* part, int groups, int* err, cudaStream_t s) {
     MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16");
     MG_REQUIRE(groups >= 1 && groups <= lx * lt, MGMLMC_EINVAL, "tensor-core stencil: bad grid");
-    MG_REQUIRE(((uintptr_t)xt & 15) == 0 && ((uintptr_t)E & 15) == 0, MGMLMC_EINVAL,
+    MG_REQUIRE((y != nullptr) != (yt != nullptr), MGMLMC_EINVAL, "tensor-core stencil: one output form");
+    MG_REQUIRE(((uintptr_t)xt & 15) == 0 && ((uintptr_t)E & 15) == 0 && ((uintptr_t)yt & 15) == 0, MGMLMC_EINVAL,
                "tensor-core stencil: operands must be 16-byte aligned");
-    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::tcs::SMEM));
     dim3 g(groups, tc_tiles(N));
-    tc::tcs::k_block_stencil_tc<<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, xt, E, lx, lt, N, part, err);
+    if (yt) {
+        MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::tcs::SMEM));
+        tc::tcs::k_block_stencil_tc<true><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, yt, xt, E, lx, lt, N, part,
+                                                                                    err);
+    } else {
+        MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::tcs::SMEM));
+        tc::tcs::k_block_stencil_tc<false><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, yt, xt, E, lx, lt, N, part,
+                                                                                     err);
+    }
+    MG_LAUNCHED();
+}
+
+void launch_mr_update_bf16(float2* yh, __nv_bfloat16* rt, const __nv_bfloat16* pt, const double2* dots, int nsites,
+                           int N, bool first, cudaStream_t s) {
+    MG_REQUIRE(nsites <= 65535, MGMLMC_EINVAL, "BF16 tiles: at most 65535 sites");
+    tc::tcs::k_mr_update_bf16<<<dim3(tc_tiles(N), nsites), tc::tcs::CH, 0, s>>>(yh, rt, pt, dots, N, first);
     MG_LAUNCHED();
 }
 

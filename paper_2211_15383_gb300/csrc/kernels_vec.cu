@@ -271,7 +271,7 @@ void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sig
     MG_LAUNCHED();
 }
 
-int reduce_groups(long long n, int N) { return row_groups(n, N, 8); }
+int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
 
 // Row-major partials: out[i] = sum_g part[i * groups + g]; one warp per output,
 // lanes add g = lane, lane + 32, ... in order, then a fixed shuffle tree.

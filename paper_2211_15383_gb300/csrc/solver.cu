@@ -112,18 +112,20 @@ static __nv_bfloat16* tc_tiles(Ctx& c, int l, int N) {
     return reinterpret_cast<__nv_bfloat16*>(c.scratch_bytes(nm("mr_rt", l, 2), tc_tiles_bytes(c.lev[l].nsites, N)));
 }
 
-// y = (D_l M_l^{-1}) x on the tensor cores, x given as its BF16 tiles xt; dots as apply_Dhat
-// (against the BF16 x).
-static void apply_Dhat_tc(Ctx& c, int l, float2* y, const __nv_bfloat16* xt, int N, double2* dots) {
+// y = (D_l M_l^{-1}) x on the tensor cores, x given as its BF16 tiles xt, y as FP32 rows
+// (y) or BF16 tiles (yt); dots as apply_Dhat (against the BF16 x).
+static void apply_Dhat_tc(Ctx& c, int l, float2* y, __nv_bfloat16* yt, const __nv_bfloat16* xt, int N,
+                          double2* dots) {
     const Level& L = c.lev[l];
     const int groups = block_stencil_tc_groups(L.nsites, N);
     double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
     {
-        // algorithmic traffic: BF16 x (4 B per complex) and FP32 y once, the BF16 operands once
+        // algorithmic traffic: BF16 x (4 B per complex) and y (FP32 8 B or BF16 4 B) once,
+        // the BF16 operands once
         ProfScope ps(c, "D" + std::to_string(l + 1) + ".bf16",
-                     (double)L.n * N * (4 + 8) + 5.0 * L.nsites * 8.0 * L.d * L.d,
+                     (double)L.n * N * (4 + (yt ? 4 : 8)) + 5.0 * L.nsites * 8.0 * L.d * L.d,
                      40.0 * L.d * L.d * (double)L.nsites * N);
-        launch_block_stencil_tc(y, xt, L.Ahat16, L.lx, L.lt, N, part, groups, device_error_flag(c), c.stream);
+        launch_block_stencil_tc(y, yt, xt, L.Ahat16, L.lx, L.lt, N, part, groups, device_error_flag(c), c.stream);
     }
     ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
     launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
@@ -157,7 +159,7 @@ template <> bool apply_smoother_tc<float2>(Ctx& c, int l, float2* y, const float
     if (!tc_smoother<float2>(c.lev[l], N)) return false;
     __nv_bfloat16* xt = tc_tiles(c, l, N);
     pack_tiles(c, l, xt, x, N);
-    apply_Dhat_tc(c, l, y, xt, N, dots);
+    apply_Dhat_tc(c, l, y, nullptr, xt, N, dots);
     return true;
 }
 
@@ -210,25 +212,38 @@ template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int 
     launch_gemm_nn<float2>(e, L.Dinv32, r, (int)L.n, (int)L.n, N, false, c.stream);
 }
 
-// nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual
-// on entry and is overwritten.
-// Block-Jacobi MR on the tensor cores: the residual's BF16 tiles are packed once,
-// then each update writes the next ones.
-template <typename C> static bool mr_smooth_tc(Ctx&, int, C*, C*, int, int, bool) { return false; }
-template <> bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bool e_zero) {
+// Block-Jacobi MR on the tensor cores.  The residual's BF16 tiles are packed once;
+// when the caller does not need the final residual (post-smoothing), r and p live
+// only as BF16 tiles from there on (the smoother needs a few digits, and FGMRES
+// is flexible), else r stays FP32 and each update writes the next tiles.
+template <typename C> static bool mr_smooth_tc(Ctx&, int, C*, C*, int, int, bool, bool) { return false; }
+template <>
+bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bool e_zero, bool need_r) {
     const Level& L = c.lev[l];
     if (nu <= 0 || !tc_smoother<float2>(L, N)) return false;
-    float2* p = c.scratch<float2>(nm("mr_p", l, sizeof(float2)), (size_t)L.n * N);
     float2* yh = c.scratch<float2>(nm("mr_y", l, sizeof(float2)), (size_t)L.n * N);
     double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(float2)), 2 * (size_t)N);
     __nv_bfloat16* rt = tc_tiles(c, l, N);
     pack_tiles(c, l, rt, r, N);
-    for (int s = 0; s < nu; ++s) {
-        apply_Dhat_tc(c, l, p, rt, N, dots);
-        const bool more = s + 1 < nu;
-        ProfScope ps(c, "mr" + std::to_string(l + 1) + ".f32", (double)L.n * N * (5 * 8 + (more ? 4 : 0)),
-                     16.0 * L.n * N);
-        launch_mr_update_tc(yh, r, p, dots, L.nsites, N, s == 0, more ? rt : nullptr, c.stream);
+    if (need_r) {
+        float2* p = c.scratch<float2>(nm("mr_p", l, sizeof(float2)), (size_t)L.n * N);
+        for (int s = 0; s < nu; ++s) {
+            apply_Dhat_tc(c, l, p, nullptr, rt, N, dots);
+            const bool more = s + 1 < nu;
+            ProfScope ps(c, "mr" + std::to_string(l + 1) + ".f32", (double)L.n * N * (5 * 8 + (more ? 4 : 0)),
+                         16.0 * L.n * N);
+            launch_mr_update_tc(yh, r, p, dots, L.nsites, N, s == 0, more ? rt : nullptr, c.stream);
+        }
+    } else {
+        __nv_bfloat16* pt = reinterpret_cast<__nv_bfloat16*>(
+            c.scratch_bytes(nm("mr_pt", l, 2), tc_tiles_bytes(L.nsites, N)));
+        for (int s = 0; s < nu; ++s) {
+            apply_Dhat_tc(c, l, nullptr, pt, rt, N, dots);
+            // traffic: r and p tiles read, r tiles written (4 B per complex), yh read and written
+            ProfScope ps(c, "mr" + std::to_string(l + 1) + ".bf16", (double)L.n * N * (3 * 4 + (s ? 16 : 8)),
+                         16.0 * L.n * N);
+            launch_mr_update_bf16(yh, rt, pt, dots, L.nsites, N, s == 0, c.stream);
+        }
     }
     ProfScope ps(c, "bjac" + std::to_string(l + 1) + ".f32", 3.0 * L.n * N * sizeof(float2),
                  8.0 * L.d * (double)L.n * N);
@@ -236,9 +251,11 @@ template <> bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N
     return true;
 }
 
+// nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual on
+// entry and is overwritten (with the final residual when need_r).
 template <typename C>
-static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero) {
-    if (mr_smooth_tc<C>(c, l, e, r, N, nu, e_zero)) return;
+static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero, bool need_r) {
+    if (mr_smooth_tc<C>(c, l, e, r, N, nu, e_zero, need_r)) return;
     const Level& L = c.lev[l];
     C* p = c.scratch<C>(nm("mr_p", l, sizeof(C)), (size_t)L.n * N);
     double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(C)), 2 * (size_t)N);
@@ -281,7 +298,7 @@ void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
     bool e_zero = true;
     if (c.opt.nu_pre > 0) {
         MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C) * L.n * N, cudaMemcpyDeviceToDevice, c.stream));
-        mr_smooth<C>(c, l, e, res, N, c.opt.nu_pre, true);   // leaves res = r - D e
+        mr_smooth<C>(c, l, e, res, N, c.opt.nu_pre, true, true);   // leaves res = r - D e
         e_zero = false;
         apply_restrict<C>(c, l, rc, res, N);
     } else {
@@ -291,7 +308,7 @@ void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
     apply_prolong<C>(c, l, e, ec, N, !e_zero);
     if (c.opt.nu_post > 0) {
         apply_D<C>(c, l, res, e, r, N, 1, nullptr);
-        mr_smooth<C>(c, l, e, res, N, c.opt.nu_post, false);
+        mr_smooth<C>(c, l, e, res, N, c.opt.nu_post, false, false);
     }
 }
 
