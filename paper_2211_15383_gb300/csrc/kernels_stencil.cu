@@ -538,7 +538,131 @@ __global__ void k_gamma5(C* __restrict__ y, const C* __restrict__ x, long long r
 // --------------------------------------------------------------------- launchers
 static inline dim3 blk() { return dim3(kRhsTile, kRowLanes); }
 
-int stencil_groups(int nsites, int N) { return row_groups(nsites, N, 4); }
+int stencil_groups(int nsites, int N) { return row_groups(nsites, N, 8); }
+
+// FP32 Wilson operator with two rhs per thread: 16-byte loads and stores (a warp
+// moves 512 B per access), half the index arithmetic per rhs.  N even.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_wilson_f2(float2* __restrict__ y, const float2* __restrict__ x,
+                                                   const float2* __restrict__ b, const float2* __restrict__ U,
+                                                   float mass, int lx, int lt, int N, double2* __restrict__ part) {
+    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
+    const int V = lx * lt;
+    float2 dyx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float dyy[2] = {0.f, 0.f};
+    auto ld2 = [&](const float2* base, long long idx, float2& a, float2& c) {
+        const float4 v = *reinterpret_cast<const float4*>(base + idx);
+        a = make_float2(v.x, v.y);
+        c = make_float2(v.z, v.w);
+    };
+    if (j < N) {
+        const long long N2 = 2LL * N;
+        for (int site = blockIdx.y * kRowLanes + threadIdx.y; site < V; site += gridDim.y * kRowLanes) {
+            const int xx = site % lx, t = site / lx;
+            const int sxp = (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+            const int sxm = (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+            const int stp = xx + lx * (t + 1 == lt ? 0 : t + 1);
+            const int stm = xx + lx * (t == 0 ? lt - 1 : t - 1);
+            const float sgp = (t + 1 == lt) ? -0.5f : 0.5f;   // antiperiodic time boundary, times 1/2
+            const float sgm = (t == 0) ? -0.5f : 0.5f;
+            const float2 u0 = U[2 * site], u1 = U[2 * site + 1];
+            const float2 u0m = U[2 * sxm], u1m = U[2 * stm + 1];
+            float2 p0[2], p1[2], a0[2], a1[2], c0[2], c1[2], e0[2], e1[2], f0[2], f1[2];
+            ld2(x, site * N2 + j, p0[0], p0[1]);
+            ld2(x, site * N2 + N + j, p1[0], p1[1]);
+            ld2(x, sxp * N2 + j, a0[0], a0[1]);
+            ld2(x, sxp * N2 + N + j, a1[0], a1[1]);
+            ld2(x, sxm * N2 + j, c0[0], c0[1]);
+            ld2(x, sxm * N2 + N + j, c1[0], c1[1]);
+            ld2(x, stp * N2 + j, e0[0], e0[1]);
+            ld2(x, stp * N2 + N + j, e1[0], e1[1]);
+            ld2(x, stm * N2 + j, f0[0], f0[1]);
+            ld2(x, stm * N2 + N + j, f1[0], f1[1]);
+            float2 o0[2], o1[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                o0[r] = mk(mass * p0[r].x, mass * p0[r].y);
+                o1[r] = mk(mass * p1[r].x, mass * p1[r].y);
+                {   // +x: (1 - sigma_1) psi = (a, -a), a = psi0 - psi1
+                    const float2 u = cscale(cmul(u0, csub(a0[r], a1[r])), 0.5f);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = cadd(o1[r], u);
+                }
+                {   // -x: (1 + sigma_1) psi = (c, c), c = psi0 + psi1
+                    const float2 u = cscale(cmulc(u0m, cadd(c0[r], c1[r])), 0.5f);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = csub(o1[r], u);
+                }
+                {   // +t: (1 - sigma_2) psi = (a, -i a), a = psi0 + i psi1
+                    const float2 u = cscale(cmul(u1, cadd(e0[r], ctimesi(e1[r]))), sgp);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = cadd(o1[r], ctimesi(u));
+                }
+                {   // -t: (1 + sigma_2) psi = (c, i c), c = psi0 - i psi1
+                    const float2 u = cscale(cmulc(u1m, csub(f0[r], ctimesi(f1[r]))), sgm);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = csub(o1[r], ctimesi(u));
+                }
+            }
+            if (MODE == 1) {
+                float2 b0[2], b1[2];
+                ld2(b, site * N2 + j, b0[0], b0[1]);
+                ld2(b, site * N2 + N + j, b1[0], b1[1]);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    o0[r] = csub(b0[r], o0[r]);
+                    o1[r] = csub(b1[r], o1[r]);
+                }
+            }
+            *reinterpret_cast<float4*>(y + site * N2 + j) = make_float4(o0[0].x, o0[0].y, o0[1].x, o0[1].y);
+            *reinterpret_cast<float4*>(y + site * N2 + N + j) = make_float4(o1[0].x, o1[0].y, o1[1].x, o1[1].y);
+            if (MODE == 2) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    cfmac(dyx[r], o0[r], p0[r]);
+                    cfmac(dyx[r], o1[r], p1[r]);
+                    dyy[r] = fmaf(o0[r].x, o0[r].x, fmaf(o0[r].y, o0[r].y,
+                                  fmaf(o1[r].x, o1[r].x, fmaf(o1[r].y, o1[r].y, dyy[r]))));
+                }
+            }
+        }
+    }
+    if (MODE == 2) {
+        __shared__ double2 sh[2][kRowLanes][2 * kRhsTile + 1];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            sh[0][threadIdx.y][2 * threadIdx.x + r] = to_d(dyx[r]);
+            sh[1][threadIdx.y][2 * threadIdx.x + r] = make_double2((double)dyy[r], 0.0);
+        }
+        __syncthreads();
+        // 64 rhs x 2 quantities: threads (x, y < 4) add the 8 row lanes of one each
+        const int q = threadIdx.y >> 1, jj = 2 * threadIdx.x + (threadIdx.y & 1);
+        const int jo = 2 * blockIdx.x * kRhsTile + jj;
+        if (threadIdx.y < 4 && jo < N) {
+            double2 acc = sh[q][0][jj];
+            for (int r = 1; r < kRowLanes; ++r) acc = cadd(acc, sh[q][r][jj]);
+            part[((long long)q * N + jo) * gridDim.y + blockIdx.y] = acc;
+        }
+    }
+}
+
+template <typename C>
+static bool wilson_f2(C*, const C*, const C*, const C*, re_t<C>, int, int, int, int, double2*, int, cudaStream_t) {
+    return false;
+}
+template <>
+bool wilson_f2<float2>(float2* y, const float2* x, const float2* b, const float2* U, float mass, int lx, int lt, int N,
+                       int mode, double2* part, int groups, cudaStream_t s) {
+    if (N % 2) return false;
+    dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, groups);
+    switch (mode) {
+        case 0: k_wilson_f2<0><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+        case 1: k_wilson_f2<1><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+        default: k_wilson_f2<2><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
+    }
+    MG_LAUNCHED();
+    return true;
+}
 
 template <typename C>
 void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N, int mode,
@@ -546,6 +670,7 @@ void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, 
     using R = re_t<C>;
     dim3 g(rhs_tiles(N), groups);
     const R mass = (R)(m0 + 2.0);
+    if (wilson_f2<C>(y, x, b, U, mass, lx, lt, N, mode, part, groups, s)) return;
     switch (mode) {
         case 0: k_wilson<C, 0><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
         case 1: k_wilson<C, 1><<<g, blk(), 0, s>>>(y, x, b, U, mass, lx, lt, N, part); break;
