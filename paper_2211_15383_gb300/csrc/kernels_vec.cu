@@ -200,134 +200,6 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
     }
 }
 
-static inline dim3 blk() { return dim3(kRhsTile, kRowLanes); }
-
-// FP32 variants with two rhs per thread: 16-byte accesses (a warp moves 512 B per
-// access) and half the load instructions; N even.  Same partial layouts as above.
-// Vectors k0 .. k0 + m - 1 of the basis (m <= MAXM); partials of mtot vectors.
-template <int MAXM>
-__global__ void k_multidot_f2(double2* __restrict__ part, const float2* __restrict__ V, int m,
-                              const float2* __restrict__ w, long long n, int N, int k0, int mtot) {
-    __shared__ double2 sh[kRowLanes][2 * kRhsTile + 1];
-    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
-    const long long stride = n * (long long)N;
-    float2 acc[MAXM][2];
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) acc[k][0] = acc[k][1] = make_float2(0.f, 0.f);
-    if (j < N)
-        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
-             i += (long long)gridDim.y * kRowLanes) {
-            const float4 wv = *reinterpret_cast<const float4*>(w + i * N + j);
-            const float2 w0 = make_float2(wv.x, wv.y), w1 = make_float2(wv.z, wv.w);
-#pragma unroll
-            for (int k = 0; k < MAXM; ++k)
-                if (k < m) {
-                    const float4 v = *reinterpret_cast<const float4*>(V + k * stride + i * N + j);
-                    cfmac(acc[k][0], make_float2(v.x, v.y), w0);
-                    cfmac(acc[k][1], make_float2(v.z, v.w), w1);
-                }
-        }
-    for (int k = 0; k < m; ++k) {
-        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-#pragma unroll
-        for (int kk = 0; kk < MAXM; ++kk)
-            if (kk == k) {
-                a0 = acc[kk][0];
-                a1 = acc[kk][1];
-            }
-        sh[threadIdx.y][2 * threadIdx.x] = to_d(a0);
-        sh[threadIdx.y][2 * threadIdx.x + 1] = to_d(a1);
-        __syncthreads();
-        if (threadIdx.y < 2) {
-            const int jj = 2 * threadIdx.x + threadIdx.y;
-            const int jo = 2 * blockIdx.x * kRhsTile + jj;
-            if (jo < N) {
-                double2 t = sh[0][jj];
-                for (int r = 1; r < kRowLanes; ++r) t = cadd(t, sh[r][jj]);
-                part[((long long)blockIdx.y * mtot + k0 + k) * N + jo] = t;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void k_multiaxpy_f2(float2* __restrict__ w, const double2* __restrict__ coef, int m,
-                               const float2* __restrict__ V, double sign, long long n, int N,
-                               double* __restrict__ norm_part) {
-    __shared__ float2 cf[64][2 * kRhsTile];
-    __shared__ double sh[kRowLanes][2 * kRhsTile + 1];
-    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
-    const long long stride = n * (long long)N;
-    for (int k = threadIdx.y; k < m; k += kRowLanes)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const double2 c = (j + r < N) ? coef[(long long)k * N + j + r] : make_double2(0, 0);
-            cf[k][2 * threadIdx.x + r] = make_float2((float)(c.x * sign), (float)(c.y * sign));
-        }
-    __syncthreads();
-    float n0 = 0.f, n1 = 0.f;
-    if (j < N)
-        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
-             i += (long long)gridDim.y * kRowLanes) {
-            const float4 wv = *reinterpret_cast<const float4*>(w + i * N + j);
-            float2 a0 = make_float2(wv.x, wv.y), a1 = make_float2(wv.z, wv.w);
-            for (int k = 0; k < m; ++k) {
-                const float4 v = *reinterpret_cast<const float4*>(V + k * stride + i * N + j);
-                cfma(a0, cf[k][2 * threadIdx.x], make_float2(v.x, v.y));
-                cfma(a1, cf[k][2 * threadIdx.x + 1], make_float2(v.z, v.w));
-            }
-            *reinterpret_cast<float4*>(w + i * N + j) = make_float4(a0.x, a0.y, a1.x, a1.y);
-            n0 = fmaf(a0.x, a0.x, fmaf(a0.y, a0.y, n0));
-            n1 = fmaf(a1.x, a1.x, fmaf(a1.y, a1.y, n1));
-        }
-    if (norm_part) {
-        // |w|^2 partials of the updated vector, as k_norm2 writes them
-        sh[threadIdx.y][2 * threadIdx.x] = (double)n0;
-        sh[threadIdx.y][2 * threadIdx.x + 1] = (double)n1;
-        __syncthreads();
-        if (threadIdx.y < 2) {
-            const int jj = 2 * threadIdx.x + threadIdx.y;
-            const int jo = 2 * blockIdx.x * kRhsTile + jj;
-            if (jo < N) {
-                double t = sh[0][jj];
-                for (int r = 1; r < kRowLanes; ++r) t += sh[r][jj];
-                norm_part[(long long)blockIdx.y * N + jo] = t;
-            }
-        }
-    }
-}
-
-template <typename C>
-static bool multidot_f2(double2*, const C*, int, const C*, long long, int, int, cudaStream_t) { return false; }
-template <>
-bool multidot_f2<float2>(double2* part, const float2* V, int m, const float2* w, long long n, int N, int G,
-                         cudaStream_t s) {
-    if (N % 2) return false;
-    dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, G);
-    // at most 8 vectors per launch (16 accumulators a thread); w is re-read per chunk
-    for (int k0 = 0; k0 < m; k0 += 8) {
-        const int mc = m - k0 < 8 ? m - k0 : 8;
-        const float2* Vc = V + (size_t)k0 * n * N;
-        if (mc <= 4) k_multidot_f2<4><<<g, blk(), 0, s>>>(part, Vc, mc, w, n, N, k0, m);
-        else k_multidot_f2<8><<<g, blk(), 0, s>>>(part, Vc, mc, w, n, N, k0, m);
-        MG_LAUNCHED();
-    }
-    return true;
-}
-template <typename C>
-static bool multiaxpy_f2(C*, const double2*, int, const C*, double, long long, int, double*, int, cudaStream_t) {
-    return false;
-}
-template <>
-bool multiaxpy_f2<float2>(float2* w, const double2* coef, int m, const float2* V, double sign, long long n, int N,
-                          double* part, int G, cudaStream_t s) {
-    if (N % 2) return false;
-    dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, G);
-    k_multiaxpy_f2<<<g, blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
-    MG_LAUNCHED();
-    return true;
-}
-
 // Partials reduction: block (32 outputs, 32 group lanes); lane ty adds groups
 // ty, ty+32, ... in order, then a fixed-order sum over the 32 lanes, so the result
 // does not depend on timing (deterministic).
@@ -359,6 +231,7 @@ __global__ void __launch_bounds__(1024) k_finalize(T* __restrict__ out, const T*
 }
 
 // ------------------------------------------------------------------ launchers
+static inline dim3 blk() { return dim3(kRhsTile, kRowLanes); }
 
 template <typename C>
 void launch_noise(C* x, long long n, int N, uint64_t seed, uint64_t term, int64_t first, cudaStream_t s) {
@@ -449,10 +322,6 @@ template <typename C>
 void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, int N, double2* part, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multidot: 1 <= m <= 64");
     const int G = reduce_groups(n, N);
-    if (multidot_f2<C>(part, V, m, w, n, N, G, s)) {
-        launch_finalize(out, part, G, m * N, s);
-        return;
-    }
     dim3 g(rhs_tiles(N), G);
     if (m <= 4) k_multidot<C, 4><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
     else if (m <= 8) k_multidot<C, 8><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
@@ -465,9 +334,7 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
-    const int G = reduce_groups(n, N);
-    if (multiaxpy_f2<C>(w, coef, m, V, sign, n, N, nullptr, G, s)) return;
-    k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), reduce_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
     MG_LAUNCHED();
 }
 template <typename C>
@@ -475,10 +342,8 @@ void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double
                             double* norm2, double* part, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
     const int G = reduce_groups(n, N);
-    if (!multiaxpy_f2<C>(w, coef, m, V, sign, n, N, part, G, s)) {
-        k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
-        MG_LAUNCHED();
-    }
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
+    MG_LAUNCHED();
     launch_finalize(norm2, part, G, N, s);
 }
 
