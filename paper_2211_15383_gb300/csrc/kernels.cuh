@@ -47,6 +47,8 @@ void launch_transpose(double2* out, const double2* in, long long rows, int cols,
 // ------------------------------------------------------------- reductions
 // Number of row groups (partials) used by the reduction kernels for (n, N).
 int reduce_groups(long long n, int N);
+// Row groups of launch_multiaxpy(_norm2): size of the norm partials is axpy_groups * N.
+int axpy_groups(long long n, int N);
 // out[j] = sum_i conj(x[i][j]) * y[i][j]  (double2), via scratch part[groups][N]
 template <typename Cx_, typename Cy>
 void launch_dot(double2* out, const Cx_* x, const Cy* y, long long n, int N, double2* part, cudaStream_t s);
@@ -61,7 +63,7 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
                       cudaStream_t s);
-// As launch_multiaxpy, and norm2[j] = |w_j|^2 of the updated w (part: reduce_groups(n, N) * N scratch).
+// As launch_multiaxpy, and norm2[j] = |w_j|^2 of the updated w (part: axpy_groups(n, N) * N scratch).
 template <typename C>
 void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
                             double* norm2, double* part, cudaStream_t s);

@@ -133,23 +133,44 @@ __global__ void k_norm2(double* __restrict__ part, const C* __restrict__ x, long
     }
 }
 
+// R rows per loop trip with all their loads issued first (few vectors leave too few
+// loads in flight per row otherwise).
 template <typename C, int MAXM>
 __global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, int m, const C* __restrict__ w,
                            long long n, int N) {
+    constexpr int R = MAXM <= 4 ? 4 : (MAXM <= 8 ? 2 : 1);
     __shared__ double2 sh[kRowLanes][kRhsTile + 1];
     const int j = blockIdx.x * kRhsTile + threadIdx.x;
     const long long stride = n * (long long)N;
+    const long long S = (long long)gridDim.y * kRowLanes;
     C acc[MAXM];
 #pragma unroll
     for (int k = 0; k < MAXM; ++k) acc[k] = czero<C>();
-    if (j < N)
-        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
-             i += (long long)gridDim.y * kRowLanes) {
+    if (j < N && R == 1) {
+        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n; i += S) {
             const C wv = w[i * N + j];
 #pragma unroll
             for (int k = 0; k < MAXM; ++k)
                 if (k < m) cfmac(acc[k], V[k * stride + i * N + j], wv);
         }
+    } else if (j < N) {
+        for (long long i0 = (long long)blockIdx.y * kRowLanes + threadIdx.y; i0 < n; i0 += R * S) {
+            C wv[R], vv[R][MAXM];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const long long i = i0 + r * S;
+                const bool in = i < n;
+                wv[r] = in ? w[i * N + j] : czero<C>();
+#pragma unroll
+                for (int k = 0; k < MAXM; ++k) vv[r][k] = (in && k < m) ? V[k * stride + i * N + j] : czero<C>();
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < MAXM; ++k)
+                    if (k < m) cfmac(acc[k], vv[r][k], wv[r]);
+        }
+    }
     for (int k = 0; k < m; ++k) {
         double2 v = czero<double2>();
 #pragma unroll
@@ -272,6 +293,9 @@ void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sig
 }
 
 int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
+// The axpy of Gram-Schmidt streams m + 2 vectors with few loads per row: 16 blocks
+// per SM keep more of them in flight.
+int axpy_groups(long long n, int N) { return row_groups(n, N, 16); }
 
 // Row-major partials: out[i] = sum_g part[i * groups + g]; one warp per output,
 // lanes add g = lane, lane + 32, ... in order, then a fixed shuffle tree.
@@ -334,14 +358,14 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
-    k_multiaxpy<C><<<dim3(rhs_tiles(N), reduce_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), axpy_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
     MG_LAUNCHED();
 }
 template <typename C>
 void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
                             double* norm2, double* part, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
-    const int G = reduce_groups(n, N);
+    const int G = axpy_groups(n, N);
     k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
     MG_LAUNCHED();
     launch_finalize(norm2, part, G, N, s);

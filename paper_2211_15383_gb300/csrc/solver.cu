@@ -397,7 +397,7 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
                 ProfScope ps(c, "orth." + std::string(prec_tag(sz)), passes * (2 * j + 5) * (double)nN * sz,
                              passes * 2.0 * 8.0 * (j + 1) * (double)nN);
                 // the last axpy also returns |Vn|^2 (its partials), saving a pass over Vn
-                double* npart = c.scratch<double>("part_nrm", (size_t)reduce_groups(n, N) * N);
+                double* npart = c.scratch<double>("part_nrm_ax", (size_t)axpy_groups(n, N) * N);
                 launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
                 if (passes == 2) {
                     launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream);
@@ -452,6 +452,8 @@ long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, 
     // inner tolerance: the reduction still needed this cycle (with margin), but no
     // tighter than FP32 arithmetic can deliver
     const double inner_floor = 2e-7;
+    // below this multiple of tol the next residual may be updated with an FP32 product
+    constexpr double kRecursiveResidual = 500.0;
     norms<double2>(c, bnorm, b, n, N);
     launch_zero<double2>(x, (long long)nN, c.stream);
     MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * nN, cudaMemcpyDeviceToDevice, c.stream));
@@ -476,7 +478,16 @@ long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, 
         // ~1e-6 relative, so the FP64 residual of this loop decides on restarts
         it += fgmres<float2>(c, l, r32, e32, N, inner_tol, maxit - it, true, &iok, 1);
         launch_axpy_rhs<double2, float2>(x, nullptr, rnorm, 1.0, e32, n, N, c.stream);
-        apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
+        if (ratio <= kRecursiveResidual * tol) {
+            // The residual is already small: r -= |r| D e with an FP32 product.  Its error
+            // (below 1e-4 of |r| even where D e cancels strongly) stays under tol / 20 of
+            // |b|, so the FP64 product is not needed for the last cycle.
+            float2* de = c.scratch<float2>("ir_de32", nN);
+            apply_D<float2>(c, l, de, e32, nullptr, N, 0, nullptr);
+            launch_axpy_rhs<double2, float2>(r, nullptr, rnorm, -1.0, de, n, N, c.stream);
+        } else {
+            apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
+        }
     }
     c.last_iters = it;
     check_device_error(c);
