@@ -243,15 +243,21 @@ __global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y
                 const int nb = nbr_site(site, dir, lx, lt);
                 const float2* xn = x + (long long)nb * D * N + j;
                 const float2* Ad = At + dir * D * D;
-#pragma unroll 2
-                for (int bc = 0; bc < D; ++bc) {
-                    const float4 xv = *reinterpret_cast<const float4*>(xn + (long long)bc * N);
-                    const float2 x0 = make_float2(xv.x, xv.y), x1 = make_float2(xv.z, xv.w);
+                // the neighbour's rows in groups of 4, loads first (latency of L2 hits)
+#pragma unroll 1
+                for (int b0 = 0; b0 < D; b0 += 4) {
+                    float4 xv[4];
 #pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        const float2 av = Ad[bc * D + c];
-                        cfma(a0[c], av, x0);
-                        cfma(a1[c], av, x1);
+                    for (int q = 0; q < 4; ++q) xv[q] = *reinterpret_cast<const float4*>(xn + (long long)(b0 + q) * N);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 x0 = make_float2(xv[q].x, xv[q].y), x1 = make_float2(xv[q].z, xv[q].w);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) {
+                            const float2 av = Ad[(b0 + q) * D + c];
+                            cfma(a0[c], av, x0);
+                            cfma(a1[c], av, x1);
+                        }
                     }
                 }
             }
@@ -355,6 +361,34 @@ __global__ void __launch_bounds__(128) k_block_diag_apply(C* __restrict__ y, con
     }
 }
 
+// The same with the block size fixed at compile time: the input column stays in
+// registers (a runtime d puts it in local memory), all loads issued before the FMAs.
+template <typename C, int D>
+__global__ void __launch_bounds__(128) k_block_diag_apply_d(C* __restrict__ y, const C* __restrict__ x,
+                                                            const C* __restrict__ Minv, int nsites, int N,
+                                                            bool accumulate) {
+    __shared__ C Ms[D * D];
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    for (int site = blockIdx.y; site < nsites; site += gridDim.y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < D * D; e += 128) Ms[e] = Minv[(long long)site * D * D + e];
+        __syncthreads();
+        if (j >= N) continue;
+        C xv[D], acc[D];
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            xv[b] = x[((long long)site * D + b) * N + j];
+            acc[b] = accumulate ? y[((long long)site * D + b) * N + j] : czero<C>();
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+#pragma unroll
+            for (int b = 0; b < D; ++b) cfma(acc[c], Ms[c * D + b], xv[b]);
+            y[((long long)site * D + c) * N + j] = acc[c];
+        }
+    }
+}
+
 template <typename C>
 void launch_block_diag_apply(C* y, const C* x, const C* Minv, int nsites, int d, int N, bool accumulate,
                              cudaStream_t s) {
@@ -363,7 +397,9 @@ void launch_block_diag_apply(C* y, const C* x, const C* Minv, int nsites, int d,
     int G = 16 * kNumSM / tiles;
     if (G > nsites) G = nsites;
     if (G < 1) G = 1;
-    k_block_diag_apply<C><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, d, N, accumulate);
+    if (d == 16) k_block_diag_apply_d<C, 16><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, N, accumulate);
+    else if (d == 8) k_block_diag_apply_d<C, 8><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, N, accumulate);
+    else k_block_diag_apply<C><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, d, N, accumulate);
     MG_LAUNCHED();
 }
 
