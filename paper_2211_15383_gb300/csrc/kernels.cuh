@@ -81,6 +81,14 @@ void launch_finalize_rows(double2* out, const double2* part, int groups, int cou
 template <typename C>
 void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N,
                    int mode, double2* part, int groups, cudaStream_t s);
+// Fine-level smoother in BF16 (one bf16x2 word per complex value, [row][rhs]):
+// y = D x with per-rhs dots conj(y).x, |y|^2 (partials as launch_wilson mode 2; N even),
+// the FP32 -> BF16 conversion, and e (=|+=) alpha r, r -= alpha p (r in place).
+void launch_wilson_bf16(uint32_t* y, const uint32_t* x, const float2* U, double m0, int lx, int lt, int N,
+                        double2* part, int groups, cudaStream_t s);
+void launch_pack_bf16(uint32_t* y, const float2* x, long long count, cudaStream_t s);
+void launch_mr_update_fine_bf16(float2* e, uint32_t* r, const uint32_t* p, const double2* dots, long long n, int N,
+                                bool e_is_zero, cudaStream_t s);
 // Coarse 5-point block stencil y_s = sum_dir A[s][dir] x_nbr(s,dir), d x d complex blocks,
 // dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t (periodic; boundary signs live in the blocks).
 template <typename C>

@@ -700,6 +700,144 @@ bool wilson_f2<float2>(float2* y, const float2* x, const float2* b, const float2
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Fine-level smoother with the residual and its image held in BF16 ([row][rhs],
+// one bf16x2 per complex value): the operator y = D x with the MR dots
+// conj(y).x, |y|^2 (FP32 arithmetic, two rhs per thread, 8-byte accesses), the
+// FP32 -> BF16 packing and the MR update e (=|+=) alpha r, r -= alpha p.
+__device__ __forceinline__ float2 bf2_lo(uint32_t w) { return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u)); }
+__device__ __forceinline__ uint32_t f2_bf(float2 v) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+__global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, const uint32_t* __restrict__ x,
+                                                     const float2* __restrict__ U, float mass, int lx, int lt, int N,
+                                                     double2* __restrict__ part) {
+    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
+    const int V = lx * lt;
+    float2 dyx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float dyy[2] = {0.f, 0.f};
+    auto ld2 = [&](long long idx, float2& a, float2& c) {
+        const uint2 v = *reinterpret_cast<const uint2*>(x + idx);
+        a = bf2_lo(v.x);
+        c = bf2_lo(v.y);
+    };
+    if (j < N) {
+        const long long N2 = 2LL * N;
+        for (int site = blockIdx.y * kRowLanes + threadIdx.y; site < V; site += gridDim.y * kRowLanes) {
+            const int xx = site % lx, t = site / lx;
+            const int sxp = (xx + 1 == lx ? 0 : xx + 1) + lx * t;
+            const int sxm = (xx == 0 ? lx - 1 : xx - 1) + lx * t;
+            const int stp = xx + lx * (t + 1 == lt ? 0 : t + 1);
+            const int stm = xx + lx * (t == 0 ? lt - 1 : t - 1);
+            const float sgp = (t + 1 == lt) ? -0.5f : 0.5f;   // antiperiodic time boundary, times 1/2
+            const float sgm = (t == 0) ? -0.5f : 0.5f;
+            const float2 u0 = U[2 * site], u1 = U[2 * site + 1];
+            const float2 u0m = U[2 * sxm], u1m = U[2 * stm + 1];
+            float2 p0[2], p1[2], a0[2], a1[2], c0[2], c1[2], e0[2], e1[2], f0[2], f1[2];
+            ld2(site * N2 + j, p0[0], p0[1]);
+            ld2(site * N2 + N + j, p1[0], p1[1]);
+            ld2(sxp * N2 + j, a0[0], a0[1]);
+            ld2(sxp * N2 + N + j, a1[0], a1[1]);
+            ld2(sxm * N2 + j, c0[0], c0[1]);
+            ld2(sxm * N2 + N + j, c1[0], c1[1]);
+            ld2(stp * N2 + j, e0[0], e0[1]);
+            ld2(stp * N2 + N + j, e1[0], e1[1]);
+            ld2(stm * N2 + j, f0[0], f0[1]);
+            ld2(stm * N2 + N + j, f1[0], f1[1]);
+            float2 o0[2], o1[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                o0[r] = mk(mass * p0[r].x, mass * p0[r].y);
+                o1[r] = mk(mass * p1[r].x, mass * p1[r].y);
+                {   // +x: (1 - sigma_1) psi = (a, -a), a = psi0 - psi1
+                    const float2 u = cscale(cmul(u0, csub(a0[r], a1[r])), 0.5f);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = cadd(o1[r], u);
+                }
+                {   // -x: (1 + sigma_1) psi = (c, c), c = psi0 + psi1
+                    const float2 u = cscale(cmulc(u0m, cadd(c0[r], c1[r])), 0.5f);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = csub(o1[r], u);
+                }
+                {   // +t: (1 - sigma_2) psi = (a, -i a), a = psi0 + i psi1
+                    const float2 u = cscale(cmul(u1, cadd(e0[r], ctimesi(e1[r]))), sgp);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = cadd(o1[r], ctimesi(u));
+                }
+                {   // -t: (1 + sigma_2) psi = (c, i c), c = psi0 - i psi1
+                    const float2 u = cscale(cmulc(u1m, csub(f0[r], ctimesi(f1[r]))), sgm);
+                    o0[r] = csub(o0[r], u);
+                    o1[r] = csub(o1[r], ctimesi(u));
+                }
+                cfmac(dyx[r], o0[r], p0[r]);
+                cfmac(dyx[r], o1[r], p1[r]);
+                dyy[r] = fmaf(o0[r].x, o0[r].x, fmaf(o0[r].y, o0[r].y,
+                              fmaf(o1[r].x, o1[r].x, fmaf(o1[r].y, o1[r].y, dyy[r]))));
+            }
+            *reinterpret_cast<uint2*>(y + site * N2 + j) = make_uint2(f2_bf(o0[0]), f2_bf(o0[1]));
+            *reinterpret_cast<uint2*>(y + site * N2 + N + j) = make_uint2(f2_bf(o1[0]), f2_bf(o1[1]));
+        }
+    }
+    __shared__ double2 sh[2][kRowLanes][2 * kRhsTile + 1];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        sh[0][threadIdx.y][2 * threadIdx.x + r] = to_d(dyx[r]);
+        sh[1][threadIdx.y][2 * threadIdx.x + r] = make_double2((double)dyy[r], 0.0);
+    }
+    __syncthreads();
+    // 64 rhs x 2 quantities: threads (x, y < 4) add the 8 row lanes of one each
+    const int q = threadIdx.y >> 1, jj = 2 * threadIdx.x + (threadIdx.y & 1);
+    const int jo = 2 * blockIdx.x * kRhsTile + jj;
+    if (threadIdx.y < 4 && jo < N) {
+        double2 acc = sh[q][0][jj];
+        for (int r = 1; r < kRowLanes; ++r) acc = cadd(acc, sh[q][r][jj]);
+        part[((long long)q * N + jo) * gridDim.y + blockIdx.y] = acc;
+    }
+}
+
+__global__ void k_pack_bf16(uint32_t* __restrict__ y, const float2* __restrict__ x, long long count) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < count) y[i] = f2_bf(x[i]);
+}
+
+__global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restrict__ r, const uint32_t* __restrict__ p,
+                                      const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    const double2 pr = dots[j];
+    const double pp = dots[N + j].x;
+    const float2 a = pp > 0.0 ? make_float2((float)(pr.x / pp), (float)(pr.y / pp)) : make_float2(0.f, 0.f);
+    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n; i += (long long)gridDim.y * kRowLanes) {
+        const long long idx = i * N + j;
+        const float2 rv = bf2_lo(r[idx]), pv = bf2_lo(p[idx]);
+        float2 ev = e_is_zero ? make_float2(0.f, 0.f) : e[idx];
+        cfma(ev, a, rv);
+        e[idx] = ev;
+        r[idx] = f2_bf(csub(rv, cmul(a, pv)));
+    }
+}
+
+void launch_wilson_bf16(uint32_t* y, const uint32_t* x, const float2* U, double m0, int lx, int lt, int N,
+                        double2* part, int groups, cudaStream_t s) {
+    MG_REQUIRE(N % 2 == 0, MGMLMC_EINVAL, "BF16 Wilson operator: N even");
+    dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, groups);
+    k_wilson_bf16<<<g, blk(), 0, s>>>(y, x, U, (float)(m0 + 2.0), lx, lt, N, part);
+    MG_LAUNCHED();
+}
+
+void launch_pack_bf16(uint32_t* y, const float2* x, long long count, cudaStream_t s) {
+    k_pack_bf16<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(y, x, count);
+    MG_LAUNCHED();
+}
+
+void launch_mr_update_fine_bf16(float2* e, uint32_t* r, const uint32_t* p, const double2* dots, long long n, int N,
+                                bool e_is_zero, cudaStream_t s) {
+    k_mr_update_fine_bf16<<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, s>>>(e, r, p, dots, n, N, e_is_zero);
+    MG_LAUNCHED();
+}
+
 template <typename C>
 void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N, int mode,
                    double2* part, int groups, cudaStream_t s) {

@@ -251,6 +251,41 @@ bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bo
     return true;
 }
 
+// Plain MR on the fine level with r and p in BF16 (mg_precision 16, post-smoothing):
+// the same few digits as the coarse smoother, half the traffic of the FP32 vectors;
+// the correction e stays FP32.
+template <typename C> static bool mr_smooth_fine_bf16(Ctx&, int, C*, C*, int, int, bool, bool) { return false; }
+template <>
+bool mr_smooth_fine_bf16<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bool e_zero, bool need_r) {
+    if (l != 0 || need_r || nu <= 0 || c.opt.mg_precision != 16 || N % 2) return false;
+    const Level& L = c.lev[0];
+    const size_t nN = (size_t)L.n * N;
+    uint32_t* rb = c.scratch<uint32_t>("mrf_rb", nN);
+    uint32_t* pb = c.scratch<uint32_t>("mrf_pb", nN);
+    double2* dots = c.scratch<double2>(nm("mr_dots", 0, sizeof(float2)), 2 * (size_t)N);
+    const int groups = stencil_groups(L.nsites, N);
+    double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
+    {
+        ProfScope ps(c, "pack1.bf16", (double)nN * (8 + 4), 0.0);
+        launch_pack_bf16(rb, r, (long long)nN, c.stream);
+    }
+    for (int s = 0; s < nu; ++s) {
+        {
+            // algorithmic traffic: BF16 x read and y written once (4 B per complex), links once
+            ProfScope ps(c, "D1.bf16", (double)nN * 8 + 2.0 * L.nsites * 8, 60.0 * L.nsites * N);
+            launch_wilson_bf16(pb, rb, c.U32, c.m0, L.lx, L.lt, N, part, groups, c.stream);
+        }
+        {
+            ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
+            launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
+        }
+        // traffic: r and p read, r written (4 B each), e read (after the first step) and written
+        ProfScope ps(c, "mr1.bf16", (double)nN * (12 + (e_zero && s == 0 ? 8 : 16)), 16.0 * nN);
+        launch_mr_update_fine_bf16(e, rb, pb, dots, L.n, N, e_zero && s == 0, c.stream);
+    }
+    return true;
+}
+
 // nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual on
 // entry and is overwritten (with the final residual when need_r).
 template <typename C>
@@ -276,6 +311,7 @@ static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero, boo
         }
         return;
     }
+    if (mr_smooth_fine_bf16<C>(c, l, e, r, N, nu, e_zero, need_r)) return;
     for (int s = 0; s < nu; ++s) {
         apply_D<C>(c, l, p, r, nullptr, N, 2, dots);
         ProfScope ps(c, "mr" + std::to_string(l + 1) + "." + prec_tag(sizeof(C)), 5.0 * L.n * N * sizeof(C),

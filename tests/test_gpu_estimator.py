@@ -31,7 +31,7 @@ def c1():
     return w, theta, sv, H, defl
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 16])
 def test_c1_samples_match_oracle(pkg, c1, prec):
     w, theta, sv, H, defl = c1
     solvers = oest.DirectSolvers(H)
