@@ -323,6 +323,9 @@ def gpu_arm(args, rank, ws, local):
            "setup": setup, "clocks": clocks, "ms_per_step_profiled": sec_prof / K * 1e3,
            "roofline": roofline(report, peaks, fp64_peak, fp32_peak),
            "kernel_classes": class_summary(report),
+           # device time inside profiled classes per step, against the profiled step: the
+           # remainder is launch gaps and host round trips (convergence checks)
+           "profiled_kernel_ms_per_step": sum(v["ms"] for v in report.values()) / K,
            "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
                      "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
            "iters": {t: ctx.get_stats(t)["iters"] for t in range(nterms)}}
