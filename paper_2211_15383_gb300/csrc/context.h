@@ -28,6 +28,7 @@ struct Level {
     float2* Ahat32 = nullptr;
     // mg_precision 16, d = 16: Ahat as BF16 real 32 x 32 operands of the tensor-core stencil
     __nv_bfloat16* Ahat16 = nullptr;
+    __nv_bfloat16* A16 = nullptr;    // the same for D_l itself (the V-cycle residual)
     // prolongation to the next level: [site][d][nvec]
     int ax = 0, at = 0, nvec = 0;
     double2* P64 = nullptr;

@@ -163,9 +163,11 @@ void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* 
 void launch_mr_update_bf16(float2* yh, __nv_bfloat16* rt, const __nv_bfloat16* pt, const double2* dots, int nsites,
                            int N, bool first, cudaStream_t s);
 int block_stencil_tc_groups(int nsites, int N);
-// Output: y (FP32 rows) or yt (BF16 tiles), exactly one non-null.
-void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx,
-                             int lt, int N, double2* part, int groups, int* err, cudaStream_t s);
+// Output: y (FP32 rows) or yt (BF16 tiles), exactly one non-null; with b (FP32 rows,
+// yt only) the tiles receive the residual b - A x and no dots are formed.
+void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const float2* b, const __nv_bfloat16* xt,
+                             const __nv_bfloat16* E, int lx, int lt, int N, double2* part, int groups, int* err,
+                             cudaStream_t s);
 
 // ----------------------------------------------------------------- setup
 // Block-stencil form of the fine Wilson operator: A[site][5][2][2].

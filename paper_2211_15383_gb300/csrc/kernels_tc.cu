@@ -565,12 +565,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// TILE_OUT: y is written as BF16 tiles (yt) instead of FP32 rows (y).
-template <bool TILE_OUT>
+// FORM 0: y = A x as FP32 rows, with the dots; 1: y as BF16 tiles (yt), with the dots;
+// 2: the residual b - A x as BF16 tiles (yt), b FP32 rows, no dots.
+template <int FORM>
 __global__ void __launch_bounds__(THREADS, 2)
-    k_block_stencil_tc(float2* __restrict__ y, __nv_bfloat16* __restrict__ yt, const __nv_bfloat16* __restrict__ xt,
-                       const __nv_bfloat16* __restrict__ E, int lx, int lt, int N, double2* __restrict__ part,
-                       int* __restrict__ err) {
+    k_block_stencil_tc(float2* __restrict__ y, __nv_bfloat16* __restrict__ yt, const float2* __restrict__ b,
+                       const __nv_bfloat16* __restrict__ xt, const __nv_bfloat16* __restrict__ E, int lx, int lt, int N,
+                       double2* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[NSTG], empty[NSTG], afull[2], aempty[2];
     __shared__ uint32_t tmem_holder;
@@ -696,7 +697,7 @@ __global__ void __launch_bounds__(THREADS, 2)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(&aempty[as]);      // accumulator may be overwritten
-            if (TILE_OUT && j >= N) {
+            if (FORM != 0 && j >= N) {
                 // pad rows of a partial tile stay zero
                 uint8_t* yrow = reinterpret_cast<uint8_t*>(yt) + ((size_t)(blockIdx.x + si * G) * T + t) * TILE_A;
 #pragma unroll
@@ -705,40 +706,48 @@ __global__ void __launch_bounds__(THREADS, 2)
             }
             if (j < N) {
                 const int site = blockIdx.x + si * G;
+                float2 ov[D];
+#pragma unroll
+                for (int co = 0; co < D; ++co) {
+                    ov[co] = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
+                    if (FORM == 2) {
+                        const float2 bv = b[((size_t)site * D + co) * N + j];
+                        ov[co] = make_float2(bv.x - ov[co].x, bv.y - ov[co].y);
+                    }
+                }
+                if (FORM != 0) {
+                    uint8_t* yrow = reinterpret_cast<uint8_t*>(yt) + ((size_t)site * T + t) * TILE_A;
+#pragma unroll
+                    for (int cg = 0; cg < 4; ++cg) {
+                        uint4 w;
+                        w.x = pack_bf16(ov[4 * cg].x, ov[4 * cg].y);
+                        w.y = pack_bf16(ov[4 * cg + 1].x, ov[4 * cg + 1].y);
+                        w.z = pack_bf16(ov[4 * cg + 2].x, ov[4 * cg + 2].y);
+                        w.w = pack_bf16(ov[4 * cg + 3].x, ov[4 * cg + 3].y);
+                        *reinterpret_cast<uint4*>(yrow + kmaj32_off(jl, 8 * cg)) = w;
+                    }
+                }
+                if (FORM == 2) continue;
                 // the site's own BF16 input row (16 components of rhs j) for the dots
                 const uint8_t* own = xtb + ((size_t)site * T + t) * TILE_A;
                 uint4 xw[4];
 #pragma unroll
                 for (int cg = 0; cg < 4; ++cg) xw[cg] = *reinterpret_cast<const uint4*>(own + kmaj32_off(jl, 8 * cg));
-                if (TILE_OUT) {
-                    uint8_t* yrow = reinterpret_cast<uint8_t*>(yt) + ((size_t)site * T + t) * TILE_A;
-#pragma unroll
-                    for (int cg = 0; cg < 4; ++cg) {
-                        uint4 w;
-                        w.x = pack_bf16(__uint_as_float(r[8 * cg + 0]), __uint_as_float(r[8 * cg + 1]));
-                        w.y = pack_bf16(__uint_as_float(r[8 * cg + 2]), __uint_as_float(r[8 * cg + 3]));
-                        w.z = pack_bf16(__uint_as_float(r[8 * cg + 4]), __uint_as_float(r[8 * cg + 5]));
-                        w.w = pack_bf16(__uint_as_float(r[8 * cg + 6]), __uint_as_float(r[8 * cg + 7]));
-                        *reinterpret_cast<uint4*>(yrow + kmaj32_off(jl, 8 * cg)) = w;
-                    }
-                }
 #pragma unroll
                 for (int co = 0; co < D; ++co) {
-                    const size_t idx = ((size_t)site * D + co) * N + j;
-                    const float2 ov = make_float2(__uint_as_float(r[2 * co]), __uint_as_float(r[2 * co + 1]));
-                    if (!TILE_OUT) y[idx] = ov;
+                    if (FORM == 0) y[((size_t)site * D + co) * N + j] = ov[co];
                     const uint32_t wbits = (co & 3) == 0 ? xw[co >> 2].x
                                            : (co & 3) == 1 ? xw[co >> 2].y
                                            : (co & 3) == 2 ? xw[co >> 2].z : xw[co >> 2].w;
                     const float2 xv = make_float2(__uint_as_float(wbits << 16), __uint_as_float(wbits & 0xFFFF0000u));
                     // conj(y) * x, accumulated per rhs
-                    dyx.x = fmaf(ov.x, xv.x, fmaf(ov.y, xv.y, dyx.x));
-                    dyx.y = fmaf(ov.x, xv.y, fmaf(-ov.y, xv.x, dyx.y));
-                    dyy = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, dyy));
+                    dyx.x = fmaf(ov[co].x, xv.x, fmaf(ov[co].y, xv.y, dyx.x));
+                    dyx.y = fmaf(ov[co].x, xv.y, fmaf(-ov[co].y, xv.x, dyx.y));
+                    dyy = fmaf(ov[co].x, ov[co].x, fmaf(ov[co].y, ov[co].y, dyy));
                 }
             }
         }
-        if (ok && j < N) {
+        if (FORM != 2 && ok && j < N) {
             part[((long long)0 * N + j) * G + blockIdx.x] = make_double2((double)dyx.x, (double)dyx.y);
             part[((long long)1 * N + j) * G + blockIdx.x] = make_double2((double)dyy, 0.0);
         }
@@ -783,26 +792,28 @@ int block_stencil_tc_groups(int nsites, int N) {
     return nsites < g ? nsites : g;
 }
 
-void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const __nv_bfloat16* xt, const __nv_bfloat16* E, int lx,
-                             int lt, int N, double2* part, int groups, int* err, cudaStream_t s) {
+template <int FORM>
+static void bstc_launch(float2* y, __nv_bfloat16* yt, const float2* b, const __nv_bfloat16* xt,
+                        const __nv_bfloat16* E, int lx, int lt, int N, double2* part, int groups, int* err,
+                        cudaStream_t s) {
+    MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::tcs::SMEM));
+    dim3 g(groups, tc_tiles(N));
+    tc::tcs::k_block_stencil_tc<FORM><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, yt, b, xt, E, lx, lt, N, part, err);
+    MG_LAUNCHED();
+}
+
+void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const float2* b, const __nv_bfloat16* xt,
+                             const __nv_bfloat16* E, int lx, int lt, int N, double2* part, int groups, int* err,
+                             cudaStream_t s) {
     MG_REQUIRE(tc_stencil_supported(16, N), MGMLMC_EINVAL, "tensor-core stencil: d = 16");
     MG_REQUIRE(groups >= 1 && groups <= lx * lt, MGMLMC_EINVAL, "tensor-core stencil: bad grid");
-    MG_REQUIRE((y != nullptr) != (yt != nullptr), MGMLMC_EINVAL, "tensor-core stencil: one output form");
+    MG_REQUIRE((y != nullptr) != (yt != nullptr) && !(b && y), MGMLMC_EINVAL, "tensor-core stencil: one output form");
     MG_REQUIRE(((uintptr_t)xt & 15) == 0 && ((uintptr_t)E & 15) == 0 && ((uintptr_t)yt & 15) == 0, MGMLMC_EINVAL,
                "tensor-core stencil: operands must be 16-byte aligned");
-    dim3 g(groups, tc_tiles(N));
-    if (yt) {
-        MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tc::tcs::SMEM));
-        tc::tcs::k_block_stencil_tc<true><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, yt, xt, E, lx, lt, N, part,
-                                                                                    err);
-    } else {
-        MG_CUDA(cudaFuncSetAttribute(tc::tcs::k_block_stencil_tc<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::tcs::SMEM));
-        tc::tcs::k_block_stencil_tc<false><<<g, tc::tcs::THREADS, tc::tcs::SMEM, s>>>(y, yt, xt, E, lx, lt, N, part,
-                                                                                     err);
-    }
-    MG_LAUNCHED();
+    if (y) bstc_launch<0>(y, yt, b, xt, E, lx, lt, N, part, groups, err, s);
+    else if (!b) bstc_launch<1>(y, yt, b, xt, E, lx, lt, N, part, groups, err, s);
+    else bstc_launch<2>(y, yt, b, xt, E, lx, lt, N, part, groups, err, s);
 }
 
 void launch_mr_update_bf16(float2* yh, __nv_bfloat16* rt, const __nv_bfloat16* pt, const double2* dots, int nsites,

@@ -89,7 +89,7 @@ void Ctx::free_hierarchy() {
     for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) {
         Level& L = lev[l];
         dev_free(L.A64); dev_free(L.A32); dev_free(L.P64); dev_free(L.P32); dev_free(L.tv);
-        dev_free(L.Minv64); dev_free(L.Minv32); dev_free(L.Ahat64); dev_free(L.Ahat32); dev_free(L.Ahat16);
+        dev_free(L.Minv64); dev_free(L.Minv32); dev_free(L.Ahat64); dev_free(L.Ahat32); dev_free(L.Ahat16); dev_free(L.A16);
         dev_free(L.Dinv64); dev_free(L.Dinv32); dev_free(L.Dinv16);
         L = Level();
     }
@@ -278,7 +278,9 @@ static void block_jacobi_setup(Ctx& c, int l) {
     launch_convert<float2, double2>(L.Ahat32, L.Ahat64, (long long)nb * 5, c.stream);
     if (c.opt.mg_precision == 16 && tc_stencil_supported(L.d, 2)) {
         if (!L.Ahat16) L.Ahat16 = c.alloc_n<__nv_bfloat16>((size_t)L.nsites * 5 * 4 * L.d * L.d);
+        if (!L.A16) L.A16 = c.alloc_n<__nv_bfloat16>((size_t)L.nsites * 5 * 4 * L.d * L.d);
         launch_embed_stencil_bf16(L.Ahat16, L.Ahat32, L.nsites, c.stream);
+        launch_embed_stencil_bf16(L.A16, L.A32, L.nsites, c.stream);
     }
     int hs = 0;
     MG_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, c.stream));

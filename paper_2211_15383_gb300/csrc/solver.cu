@@ -125,7 +125,8 @@ static void apply_Dhat_tc(Ctx& c, int l, float2* y, __nv_bfloat16* yt, const __n
         ProfScope ps(c, "D" + std::to_string(l + 1) + ".bf16",
                      (double)L.n * N * (4 + (yt ? 4 : 8)) + 5.0 * L.nsites * 8.0 * L.d * L.d,
                      40.0 * L.d * L.d * (double)L.nsites * N);
-        launch_block_stencil_tc(y, yt, xt, L.Ahat16, L.lx, L.lt, N, part, groups, device_error_flag(c), c.stream);
+        launch_block_stencil_tc(y, yt, nullptr, xt, L.Ahat16, L.lx, L.lt, N, part, groups, device_error_flag(c),
+                                c.stream);
     }
     ProfScope ps(c, "reduce", (double)groups * 2 * N * 16, (double)groups * 2 * N * 2);
     launch_finalize_rows(dots, part, groups, 2 * N, c.stream);
@@ -212,6 +213,26 @@ template <> void coarsest_apply<float2>(Ctx& c, float2* e, const float2* r, int 
     launch_gemm_nn<float2>(e, L.Dinv32, r, (int)L.n, (int)L.n, N, false, c.stream);
 }
 
+// nu block-Jacobi MR steps from the residual's BF16 tiles rt (overwritten), r and p
+// only as BF16 tiles; yh receives the preconditioned correction.
+static void smooth_tc_tiles(Ctx& c, int l, float2* yh, __nv_bfloat16* rt, int N, int nu, double2* dots) {
+    const Level& L = c.lev[l];
+    __nv_bfloat16* pt =
+        reinterpret_cast<__nv_bfloat16*>(c.scratch_bytes(nm("mr_pt", l, 2), tc_tiles_bytes(L.nsites, N)));
+    for (int s = 0; s < nu; ++s) {
+        apply_Dhat_tc(c, l, nullptr, pt, rt, N, dots);
+        // traffic: r and p tiles read, r tiles written (4 B per complex), yh read and written
+        ProfScope ps(c, "mr" + std::to_string(l + 1) + ".bf16", (double)L.n * N * (3 * 4 + (s ? 16 : 8)),
+                     16.0 * L.n * N);
+        launch_mr_update_bf16(yh, rt, pt, dots, L.nsites, N, s == 0, c.stream);
+    }
+}
+
+// Post-smoothing of the V-cycle on the tensor cores: the residual r - D_l e is formed
+// from BF16 tiles of e straight into the smoother's BF16 residual tiles (it only
+// feeds the smoother, which needs a few digits), then the BF16 smoother; e += M^{-1} yh.
+template <typename C> static bool residual_smooth_tc(Ctx&, int, C*, const C*, int) { return false; }
+
 // Block-Jacobi MR on the tensor cores.  The residual's BF16 tiles are packed once;
 // when the caller does not need the final residual (post-smoothing), r and p live
 // only as BF16 tiles from there on (the smoother needs a few digits, and FGMRES
@@ -235,15 +256,7 @@ bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bo
             launch_mr_update_tc(yh, r, p, dots, L.nsites, N, s == 0, more ? rt : nullptr, c.stream);
         }
     } else {
-        __nv_bfloat16* pt = reinterpret_cast<__nv_bfloat16*>(
-            c.scratch_bytes(nm("mr_pt", l, 2), tc_tiles_bytes(L.nsites, N)));
-        for (int s = 0; s < nu; ++s) {
-            apply_Dhat_tc(c, l, nullptr, pt, rt, N, dots);
-            // traffic: r and p tiles read, r tiles written (4 B per complex), yh read and written
-            ProfScope ps(c, "mr" + std::to_string(l + 1) + ".bf16", (double)L.n * N * (3 * 4 + (s ? 16 : 8)),
-                         16.0 * L.n * N);
-            launch_mr_update_bf16(yh, rt, pt, dots, L.nsites, N, s == 0, c.stream);
-        }
+        smooth_tc_tiles(c, l, yh, rt, N, nu, dots);
     }
     ProfScope ps(c, "bjac" + std::to_string(l + 1) + ".f32", 3.0 * L.n * N * sizeof(float2),
                  8.0 * L.d * (double)L.n * N);
@@ -288,6 +301,34 @@ bool mr_smooth_fine_bf16<float2>(Ctx& c, int l, float2* e, float2* r, int N, int
 
 // nu MR steps on D_l e = r0 starting from e (or 0); r holds the current residual on
 // entry and is overwritten (with the final residual when need_r).
+template <>
+bool residual_smooth_tc<float2>(Ctx& c, int l, float2* e, const float2* r, int N) {
+    const Level& L = c.lev[l];
+    const int nu = c.opt.nu_post;
+    if (nu <= 0 || !L.A16 || !tc_smoother<float2>(L, N)) return false;
+    float2* yh = c.scratch<float2>(nm("mr_y", l, sizeof(float2)), (size_t)L.n * N);
+    double2* dots = c.scratch<double2>(nm("mr_dots", l, sizeof(float2)), 2 * (size_t)N);
+    __nv_bfloat16* et =
+        reinterpret_cast<__nv_bfloat16*>(c.scratch_bytes(nm("cyc_et", l, 2), tc_tiles_bytes(L.nsites, N)));
+    __nv_bfloat16* rt = tc_tiles(c, l, N);
+    pack_tiles(c, l, et, e, N);
+    {
+        const int groups = block_stencil_tc_groups(L.nsites, N);
+        double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
+        // algorithmic traffic: e tiles (4 B per complex) and r (8 B) read, residual tiles written (4 B)
+        ProfScope ps(c, "D" + std::to_string(l + 1) + "res.bf16",
+                     (double)L.n * N * (4 + 8 + 4) + 5.0 * L.nsites * 8.0 * L.d * L.d,
+                     40.0 * L.d * L.d * (double)L.nsites * N);
+        launch_block_stencil_tc(nullptr, rt, r, et, L.A16, L.lx, L.lt, N, part, groups, device_error_flag(c),
+                                c.stream);
+    }
+    smooth_tc_tiles(c, l, yh, rt, N, nu, dots);
+    ProfScope ps(c, "bjac" + std::to_string(l + 1) + ".f32", 3.0 * L.n * N * sizeof(float2),
+                 8.0 * L.d * (double)L.n * N);
+    launch_block_diag_apply<float2>(e, yh, L.Minv32, L.nsites, L.d, N, true, c.stream);
+    return true;
+}
+
 template <typename C>
 static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero, bool need_r) {
     if (mr_smooth_tc<C>(c, l, e, r, N, nu, e_zero, need_r)) return;
@@ -342,7 +383,7 @@ void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
     }
     mg_cycle<C>(c, l + 1, ec, rc, N);
     apply_prolong<C>(c, l, e, ec, N, !e_zero);
-    if (c.opt.nu_post > 0) {
+    if (c.opt.nu_post > 0 && !residual_smooth_tc<C>(c, l, e, r, N)) {
         apply_D<C>(c, l, res, e, r, N, 1, nullptr);
         mr_smooth<C>(c, l, e, res, N, c.opt.nu_post, false, false);
     }
