@@ -49,15 +49,13 @@ void launch_transpose(double2* out, const double2* in, long long rows, int cols,
 int reduce_groups(long long n, int N);
 // Row groups of launch_multiaxpy(_norm2): size of the norm partials is axpy_groups * N.
 int axpy_groups(long long n, int N);
-// Row groups of launch_multidot: its partials hold dot_groups * m * N values.
-int dot_groups(long long n, int N);
 // out[j] = sum_i conj(x[i][j]) * y[i][j]  (double2), via scratch part[groups][N]
 template <typename Cx_, typename Cy>
 void launch_dot(double2* out, const Cx_* x, const Cy* y, long long n, int N, double2* part, cudaStream_t s);
 // out[j] = sum_i |x[i][j]|^2
 template <typename C>
 void launch_norm2(double* out, const C* x, long long n, int N, double* part, cudaStream_t s);
-// out[k][j] = <V_k, w>_j for k < m; V_k = V + k * n * N.  part: [dot_groups(n, N)][m][N].
+// out[k][j] = <V_k, w>_j for k < m; V_k = V + k * n * N.  part: [groups][m][N].
 template <typename C>
 void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, int N, double2* part,
                      cudaStream_t s);

@@ -133,53 +133,60 @@ __global__ void k_norm2(double* __restrict__ part, const C* __restrict__ x, long
     }
 }
 
-// Dots of MC consecutive basis vectors k0 .. k0 + MC - 1 with w (MC <= 4 fixed at compile
-// time: accumulators and loads stay in registers without predicates); R rows per loop
-// trip with all their loads issued first.  Partials of mtot vectors, laid out
-// [group][mtot][N].  Longer bases run as several launches (w is re-read once per 4
-// vectors, cheaper than the register pressure of one wide kernel).
-template <typename C, int MC, int R>
-__global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, const C* __restrict__ w, long long n,
-                           int N, int k0, int mtot) {
+// R rows per loop trip with all their loads issued first (few vectors leave too few
+// loads in flight per row otherwise).
+template <typename C, int MAXM>
+__global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, int m, const C* __restrict__ w,
+                           long long n, int N) {
+    constexpr int R = MAXM <= 4 ? 4 : (MAXM <= 8 ? 2 : 1);
     __shared__ double2 sh[kRowLanes][kRhsTile + 1];
     const int j = blockIdx.x * kRhsTile + threadIdx.x;
     const long long stride = n * (long long)N;
     const long long S = (long long)gridDim.y * kRowLanes;
-    C acc[MC];
+    C acc[MAXM];
 #pragma unroll
-    for (int k = 0; k < MC; ++k) acc[k] = czero<C>();
-    if (j < N)
+    for (int k = 0; k < MAXM; ++k) acc[k] = czero<C>();
+    if (j < N && R == 1) {
+        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n; i += S) {
+            const C wv = w[i * N + j];
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k)
+                if (k < m) cfmac(acc[k], V[k * stride + i * N + j], wv);
+        }
+    } else if (j < N) {
         for (long long i0 = (long long)blockIdx.y * kRowLanes + threadIdx.y; i0 < n; i0 += R * S) {
-            C wv[R], vv[R][MC];
+            C wv[R], vv[R][MAXM];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const long long i = i0 + r * S;
                 const bool in = i < n;
                 wv[r] = in ? w[i * N + j] : czero<C>();
 #pragma unroll
-                for (int k = 0; k < MC; ++k) vv[r][k] = in ? V[(k0 + k) * stride + i * N + j] : czero<C>();
+                for (int k = 0; k < MAXM; ++k) vv[r][k] = (in && k < m) ? V[k * stride + i * N + j] : czero<C>();
             }
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int k = 0; k < MC; ++k) cfmac(acc[k], vv[r][k], wv[r]);
+                for (int k = 0; k < MAXM; ++k)
+                    if (k < m) cfmac(acc[k], vv[r][k], wv[r]);
         }
+    }
+    for (int k = 0; k < m; ++k) {
+        double2 v = czero<double2>();
 #pragma unroll
-    for (int k = 0; k < MC; ++k) {
-        sh[threadIdx.y][threadIdx.x] = to_d(acc[k]);
+        for (int kk = 0; kk < MAXM; ++kk)
+            if (kk == k) v = to_d(acc[kk]);
+        sh[threadIdx.y][threadIdx.x] = v;
         __syncthreads();
         if (threadIdx.y == 0 && j < N) {
-            double2 t = sh[0][threadIdx.x];
-            for (int r = 1; r < kRowLanes; ++r) t = cadd(t, sh[r][threadIdx.x]);
-            part[((long long)blockIdx.y * mtot + k0 + k) * N + j] = t;
+            double2 s = sh[0][threadIdx.x];
+            for (int r = 1; r < kRowLanes; ++r) s = cadd(s, sh[r][threadIdx.x]);
+            part[((long long)blockIdx.y * m + k) * N + j] = s;
         }
         __syncthreads();
     }
 }
 
-// w += sign * sum_k coef[k] V[k]: each block owns a contiguous range of rows and walks
-// it two rows per trip (both loads of w and of every V[k] issued together), with
-// pointer increments; norm_part (may be null) receives |w|^2 partials of the result.
 template <typename C>
 __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef, int m, const C* __restrict__ V,
                             double sign, long long n, int N, double* __restrict__ norm_part) {
@@ -193,30 +200,15 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
         cf[k][threadIdx.x] = mk((R)(c.x * sign), (R)(c.y * sign));
     }
     __syncthreads();
-    const long long per = (n + gridDim.y - 1) / gridDim.y;
-    const long long r0 = (long long)blockIdx.y * per, r1 = min(n, r0 + per);
-    const long long step = (long long)kRowLanes * N;
     R nrm = 0;
-    if (j < N) {
-        C* wp = w + (r0 + threadIdx.y) * N + j;
-        const C* vp = V + (r0 + threadIdx.y) * N + j;
-        for (long long i0 = r0 + threadIdx.y; i0 < r1; i0 += 2 * kRowLanes, wp += 2 * step, vp += 2 * step) {
-            const bool in1 = i0 + kRowLanes < r1;
-            C a0 = wp[0];
-            C a1 = in1 ? wp[step] : czero<C>();
-            for (int k = 0; k < m; ++k) {
-                const C c = cf[k][threadIdx.x];
-                cfma(a0, c, vp[k * stride]);
-                if (in1) cfma(a1, c, vp[step + k * stride]);
-            }
-            wp[0] = a0;
-            nrm = fma(a0.x, a0.x, fma(a0.y, a0.y, nrm));
-            if (in1) {
-                wp[step] = a1;
-                nrm = fma(a1.x, a1.x, fma(a1.y, a1.y, nrm));
-            }
+    if (j < N)
+        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
+             i += (long long)gridDim.y * kRowLanes) {
+            C acc = w[i * N + j];
+            for (int k = 0; k < m; ++k) cfma(acc, cf[k][threadIdx.x], V[k * stride + i * N + j]);
+            w[i * N + j] = acc;
+            nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
         }
-    }
     if (norm_part) {
         // |w|^2 partials of the updated vector, as k_norm2 writes them
         sh[threadIdx.y][threadIdx.x] = (double)nrm;
@@ -304,7 +296,6 @@ int reduce_groups(long long n, int N) { return row_groups(n, N, 4); }
 // The axpy of Gram-Schmidt streams m + 2 vectors with few loads per row: 16 blocks
 // per SM keep more of them in flight.
 int axpy_groups(long long n, int N) { return row_groups(n, N, 16); }
-int dot_groups(long long n, int N) { return row_groups(n, N, 8); }
 
 // Row-major partials: out[i] = sum_g part[i * groups + g]; one warp per output,
 // lanes add g = lane, lane + 32, ... in order, then a fixed shuffle tree.
@@ -354,18 +345,14 @@ void launch_norm2(double* out, const C* x, long long n, int N, double* part, cud
 template <typename C>
 void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, int N, double2* part, cudaStream_t s) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multidot: 1 <= m <= 64");
-    const int G = dot_groups(n, N);
+    const int G = reduce_groups(n, N);
     dim3 g(rhs_tiles(N), G);
-    for (int k0 = 0; k0 < m; k0 += 4) {
-        const int mc = m - k0 < 4 ? m - k0 : 4;
-        switch (mc) {
-            case 1: k_multidot<C, 1, 4><<<g, blk(), 0, s>>>(part, V, w, n, N, k0, m); break;
-            case 2: k_multidot<C, 2, 4><<<g, blk(), 0, s>>>(part, V, w, n, N, k0, m); break;
-            case 3: k_multidot<C, 3, 4><<<g, blk(), 0, s>>>(part, V, w, n, N, k0, m); break;
-            default: k_multidot<C, 4, 4><<<g, blk(), 0, s>>>(part, V, w, n, N, k0, m); break;
-        }
-        MG_LAUNCHED();
-    }
+    if (m <= 4) k_multidot<C, 4><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
+    else if (m <= 8) k_multidot<C, 8><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
+    else if (m <= 16) k_multidot<C, 16><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
+    else if (m <= 32) k_multidot<C, 32><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
+    else k_multidot<C, 64><<<g, blk(), 0, s>>>(part, V, m, w, n, N);
+    MG_LAUNCHED();
     launch_finalize(out, part, G, m * N, s);
 }
 template <typename C>

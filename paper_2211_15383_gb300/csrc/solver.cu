@@ -434,7 +434,7 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
     double* cs = c.scratch<double>(nm("fg_cs", 0, sz), (size_t)N * m);
     double2* sn = c.scratch<double2>(nm("fg_sn", 0, sz), (size_t)N * m);
     double2* g = c.scratch<double2>(nm("fg_g", 0, sz), (size_t)N * (m + 1));
-    double2* part = c.scratch<double2>("part_md", (size_t)dot_groups(n, N) * (m + 1) * N);
+    double2* part = c.scratch<double2>("part_md", (size_t)reduce_groups(n, N) * (m + 1) * N);
 
     norms<C>(c, bnorm, b, n, N);
     if (x_zero) launch_zero<C>(x, (long long)nN, c.stream);
