@@ -191,8 +191,8 @@ def ncu_traffic(kclass):
     return e.get("dram_bytes_per_launch")
 
 
-def roofline(report, peaks, fp64_peak, fp32_peak):
-    """Roofline of the kernel class with the largest device time.
+def roofline(report, peaks, fp64_peak, fp32_peak, cls=None):
+    """Roofline of a kernel class (default: the one with the largest device time).
 
     The bound follows the class's precision and arithmetic intensity: a class is
     compute-bound when its intensity exceeds the ridge point (peak / HBM bandwidth)
@@ -200,7 +200,9 @@ def roofline(report, peaks, fp64_peak, fp32_peak):
     measured sustained cuBLAS BF16, the kernels run inside a long step); FP64 and
     FP32 classes on the FMA pipes (measured FMA peaks).
     """
-    cls, st = max(report.items(), key=lambda kv: kv[1]["ms"])
+    if cls is None:
+        cls = max(report.items(), key=lambda kv: kv[1]["ms"])[0]
+    st = report[cls]
     per_launch_s = st["ms"] * 1e-3 / st["count"]
     prec = cls.split(".")[-1]
     bytes_l = st["bytes"] / st["count"]
@@ -334,6 +336,9 @@ def gpu_arm(args, rank, ws, local):
                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
            "setup": setup, "clocks": clocks, "ms_per_step_profiled": sec_prof / K * 1e3,
            "roofline": roofline(report, peaks, fp64_peak, fp32_peak),
+           # the same for the next classes by device time (one entry per class)
+           "roofline_next": [roofline(report, peaks, fp64_peak, fp32_peak, k) for k, _ in
+                             sorted(report.items(), key=lambda kv: -kv[1]["ms"])[1:5]],
            "kernel_classes": class_summary(report),
            # device time inside profiled classes per step, against the profiled step: the
            # remainder is launch gaps and host round trips (convergence checks)

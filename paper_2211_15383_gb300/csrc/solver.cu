@@ -461,6 +461,15 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
         launch_scale_rhs<C, C>(V, V, beta, true, n, N, c.stream);
         launch_init_g(g, beta, m, N, c.stream);
         int j_end = -1;
+        // Inner cycles of the refinement loop converge in a repeatable number of steps
+        // per level and tolerance: the host reads the residual estimate (a round trip
+        // that leaves the GPU idle) only from two steps before the last such count on.
+        int* hint = nullptr;
+        if (max_cycles == 1) {
+            const int dec = std::min(15, std::max(0, (int)std::floor(-std::log10(tol))));
+            hint = &c.cycle_hint[l][dec];
+        }
+        const int check_from = hint ? std::max(1, *hint - 2) : 1;
         for (int j = 0; j < m; ++j) {
             C* Vj = V + (size_t)j * nN;
             C* Vn = V + (size_t)(j + 1) * nN;
@@ -492,11 +501,13 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
             launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, m, N, c.stream);
             ++it;
             j_end = j;
+            if (j + 1 < check_from && j + 1 < m && it < maxit) continue;
             launch_max_ratio(maxr, resid, bnorm, N, c.stream);
             const double est = read_scalar(c, maxr);
             if (est != est) throw Error(MGMLMC_ENAN, "FGMRES: NaN in Arnoldi");
             if (est <= tol || it >= maxit) break;
         }
+        if (hint) *hint = j_end + 1;
         launch_back_substitute(y, H, g, j_end, m, N, c.stream);
         launch_multiaxpy<C>(x, y, j_end + 1, Z, 1.0, n, N, c.stream);
         x_zero = false;
