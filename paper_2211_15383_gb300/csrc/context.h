@@ -122,8 +122,9 @@ struct Ctx {
     Deflation ddefl[MGMLMC_MAX_LEVELS];   // difference terms, by fine level: largest triplets of M_l (Sect. 4.2)
     TermStats stats[MGMLMC_MAX_LEVELS];
     long long last_iters = 0;        // outer iterations of the last solve
-    // iterations of the last inner FGMRES cycle, by level and decade of its tolerance
-    int cycle_hint[MGMLMC_MAX_LEVELS][16] = {};
+    // iterations of the last inner FGMRES cycle, by level, rhs count and decade of its
+    // tolerance
+    std::map<long long, int> cycle_hint;
 
     // ---- memory
     struct Buf { void* p = nullptr; size_t bytes = 0; };

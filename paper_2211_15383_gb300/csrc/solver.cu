@@ -467,7 +467,7 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
         int* hint = nullptr;
         if (max_cycles == 1) {
             const int dec = std::min(15, std::max(0, (int)std::floor(-std::log10(tol))));
-            hint = &c.cycle_hint[l][dec];
+            hint = &c.cycle_hint[((long long)l * 16 + dec) * (1LL << 32) + N];
         }
         const int check_from = hint ? std::max(1, *hint - 2) : 1;
         for (int j = 0; j < m; ++j) {
