@@ -82,7 +82,7 @@ template <typename C>
 void launch_wilson(C* y, const C* x, const C* b, const C* U, double m0, int lx, int lt, int N,
                    int mode, double2* part, int groups, cudaStream_t s);
 // Fine-level smoother in BF16 (one bf16x2 word per complex value, [row][rhs]):
-// y = D x with per-rhs dots conj(y).x, |y|^2 (partials as launch_wilson mode 2; N even),
+// y = D x with per-rhs dots conj(y).x, |y|^2 (partials as launch_wilson mode 2; N % 4 == 0),
 // the FP32 -> BF16 conversion, and e (=|+=) alpha r, r -= alpha p (r in place).
 void launch_wilson_bf16(uint32_t* y, const uint32_t* x, const float2* U, double m0, int lx, int lt, int N,
                         double2* part, int groups, cudaStream_t s);

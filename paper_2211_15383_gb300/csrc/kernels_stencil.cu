@@ -711,17 +711,27 @@ __device__ __forceinline__ uint32_t f2_bf(float2 v) {
     return *reinterpret_cast<const uint32_t*>(&b);
 }
 
+// Four rhs per thread: 16-byte accesses (four bf16x2 words), ten loads of a site in
+// flight per thread.  N % 4 == 0.
 __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, const uint32_t* __restrict__ x,
                                                      const float2* __restrict__ U, float mass, int lx, int lt, int N,
                                                      double2* __restrict__ part) {
-    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
+    constexpr int RPT = 4;
+    const int j = RPT * (blockIdx.x * kRhsTile + threadIdx.x);
     const int V = lx * lt;
-    float2 dyx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    float dyy[2] = {0.f, 0.f};
-    auto ld2 = [&](long long idx, float2& a, float2& c) {
-        const uint2 v = *reinterpret_cast<const uint2*>(x + idx);
-        a = bf2_lo(v.x);
-        c = bf2_lo(v.y);
+    float2 dyx[RPT];
+    float dyy[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        dyx[r] = make_float2(0.f, 0.f);
+        dyy[r] = 0.f;
+    }
+    auto ld4 = [&](long long idx, float2* v) {
+        const uint4 w = *reinterpret_cast<const uint4*>(x + idx);
+        v[0] = bf2_lo(w.x);
+        v[1] = bf2_lo(w.y);
+        v[2] = bf2_lo(w.z);
+        v[3] = bf2_lo(w.w);
     };
     if (j < N) {
         const long long N2 = 2LL * N;
@@ -735,62 +745,63 @@ __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, c
             const float sgm = (t == 0) ? -0.5f : 0.5f;
             const float2 u0 = U[2 * site], u1 = U[2 * site + 1];
             const float2 u0m = U[2 * sxm], u1m = U[2 * stm + 1];
-            float2 p0[2], p1[2], a0[2], a1[2], c0[2], c1[2], e0[2], e1[2], f0[2], f1[2];
-            ld2(site * N2 + j, p0[0], p0[1]);
-            ld2(site * N2 + N + j, p1[0], p1[1]);
-            ld2(sxp * N2 + j, a0[0], a0[1]);
-            ld2(sxp * N2 + N + j, a1[0], a1[1]);
-            ld2(sxm * N2 + j, c0[0], c0[1]);
-            ld2(sxm * N2 + N + j, c1[0], c1[1]);
-            ld2(stp * N2 + j, e0[0], e0[1]);
-            ld2(stp * N2 + N + j, e1[0], e1[1]);
-            ld2(stm * N2 + j, f0[0], f0[1]);
-            ld2(stm * N2 + N + j, f1[0], f1[1]);
-            float2 o0[2], o1[2];
+            float2 p0[RPT], p1[RPT], a0[RPT], a1[RPT], c0[RPT], c1[RPT], e0[RPT], e1[RPT], f0[RPT], f1[RPT];
+            ld4(site * N2 + j, p0);
+            ld4(site * N2 + N + j, p1);
+            ld4(sxp * N2 + j, a0);
+            ld4(sxp * N2 + N + j, a1);
+            ld4(sxm * N2 + j, c0);
+            ld4(sxm * N2 + N + j, c1);
+            ld4(stp * N2 + j, e0);
+            ld4(stp * N2 + N + j, e1);
+            ld4(stm * N2 + j, f0);
+            ld4(stm * N2 + N + j, f1);
+            uint32_t w0[RPT], w1[RPT];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                o0[r] = mk(mass * p0[r].x, mass * p0[r].y);
-                o1[r] = mk(mass * p1[r].x, mass * p1[r].y);
+            for (int r = 0; r < RPT; ++r) {
+                float2 o0 = mk(mass * p0[r].x, mass * p0[r].y), o1 = mk(mass * p1[r].x, mass * p1[r].y);
                 {   // +x: (1 - sigma_1) psi = (a, -a), a = psi0 - psi1
                     const float2 u = cscale(cmul(u0, csub(a0[r], a1[r])), 0.5f);
-                    o0[r] = csub(o0[r], u);
-                    o1[r] = cadd(o1[r], u);
+                    o0 = csub(o0, u);
+                    o1 = cadd(o1, u);
                 }
                 {   // -x: (1 + sigma_1) psi = (c, c), c = psi0 + psi1
                     const float2 u = cscale(cmulc(u0m, cadd(c0[r], c1[r])), 0.5f);
-                    o0[r] = csub(o0[r], u);
-                    o1[r] = csub(o1[r], u);
+                    o0 = csub(o0, u);
+                    o1 = csub(o1, u);
                 }
                 {   // +t: (1 - sigma_2) psi = (a, -i a), a = psi0 + i psi1
                     const float2 u = cscale(cmul(u1, cadd(e0[r], ctimesi(e1[r]))), sgp);
-                    o0[r] = csub(o0[r], u);
-                    o1[r] = cadd(o1[r], ctimesi(u));
+                    o0 = csub(o0, u);
+                    o1 = cadd(o1, ctimesi(u));
                 }
                 {   // -t: (1 + sigma_2) psi = (c, i c), c = psi0 - i psi1
                     const float2 u = cscale(cmulc(u1m, csub(f0[r], ctimesi(f1[r]))), sgm);
-                    o0[r] = csub(o0[r], u);
-                    o1[r] = csub(o1[r], ctimesi(u));
+                    o0 = csub(o0, u);
+                    o1 = csub(o1, ctimesi(u));
                 }
-                cfmac(dyx[r], o0[r], p0[r]);
-                cfmac(dyx[r], o1[r], p1[r]);
-                dyy[r] = fmaf(o0[r].x, o0[r].x, fmaf(o0[r].y, o0[r].y,
-                              fmaf(o1[r].x, o1[r].x, fmaf(o1[r].y, o1[r].y, dyy[r]))));
+                cfmac(dyx[r], o0, p0[r]);
+                cfmac(dyx[r], o1, p1[r]);
+                dyy[r] = fmaf(o0.x, o0.x, fmaf(o0.y, o0.y, fmaf(o1.x, o1.x, fmaf(o1.y, o1.y, dyy[r]))));
+                w0[r] = f2_bf(o0);
+                w1[r] = f2_bf(o1);
             }
-            *reinterpret_cast<uint2*>(y + site * N2 + j) = make_uint2(f2_bf(o0[0]), f2_bf(o0[1]));
-            *reinterpret_cast<uint2*>(y + site * N2 + N + j) = make_uint2(f2_bf(o1[0]), f2_bf(o1[1]));
+            *reinterpret_cast<uint4*>(y + site * N2 + j) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            *reinterpret_cast<uint4*>(y + site * N2 + N + j) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
         }
     }
-    __shared__ double2 sh[2][kRowLanes][2 * kRhsTile + 1];
+    __shared__ double2 sh[2][kRowLanes][RPT * kRhsTile + 1];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        sh[0][threadIdx.y][2 * threadIdx.x + r] = to_d(dyx[r]);
-        sh[1][threadIdx.y][2 * threadIdx.x + r] = make_double2((double)dyy[r], 0.0);
+    for (int r = 0; r < RPT; ++r) {
+        sh[0][threadIdx.y][RPT * threadIdx.x + r] = to_d(dyx[r]);
+        sh[1][threadIdx.y][RPT * threadIdx.x + r] = make_double2((double)dyy[r], 0.0);
     }
     __syncthreads();
-    // 64 rhs x 2 quantities: threads (x, y < 4) add the 8 row lanes of one each
-    const int q = threadIdx.y >> 1, jj = 2 * threadIdx.x + (threadIdx.y & 1);
-    const int jo = 2 * blockIdx.x * kRhsTile + jj;
-    if (threadIdx.y < 4 && jo < N) {
+    // 128 rhs x 2 quantities = 256 sums: thread (x, y) adds the 8 row lanes of
+    // quantity y / 4, rhs 4 x + y % 4
+    const int q = threadIdx.y >> 2, jj = RPT * threadIdx.x + (threadIdx.y & 3);
+    const int jo = RPT * blockIdx.x * kRhsTile + jj;
+    if (jo < N) {
         double2 acc = sh[q][0][jj];
         for (int r = 1; r < kRowLanes; ++r) acc = cadd(acc, sh[q][r][jj]);
         part[((long long)q * N + jo) * gridDim.y + blockIdx.y] = acc;
@@ -821,8 +832,8 @@ __global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restri
 
 void launch_wilson_bf16(uint32_t* y, const uint32_t* x, const float2* U, double m0, int lx, int lt, int N,
                         double2* part, int groups, cudaStream_t s) {
-    MG_REQUIRE(N % 2 == 0, MGMLMC_EINVAL, "BF16 Wilson operator: N even");
-    dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, groups);
+    MG_REQUIRE(N % 4 == 0, MGMLMC_EINVAL, "BF16 Wilson operator: N a multiple of 4");
+    dim3 g((N / 4 + kRhsTile - 1) / kRhsTile, groups);
     k_wilson_bf16<<<g, blk(), 0, s>>>(y, x, U, (float)(m0 + 2.0), lx, lt, N, part);
     MG_LAUNCHED();
 }

@@ -270,7 +270,7 @@ bool mr_smooth_tc<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bo
 template <typename C> static bool mr_smooth_fine_bf16(Ctx&, int, C*, C*, int, int, bool, bool) { return false; }
 template <>
 bool mr_smooth_fine_bf16<float2>(Ctx& c, int l, float2* e, float2* r, int N, int nu, bool e_zero, bool need_r) {
-    if (l != 0 || need_r || nu <= 0 || c.opt.mg_precision != 16 || N % 2) return false;
+    if (l != 0 || need_r || nu <= 0 || c.opt.mg_precision != 16 || N % 4) return false;
     const Level& L = c.lev[0];
     const size_t nN = (size_t)L.n * N;
     uint32_t* rb = c.scratch<uint32_t>("mrf_rb", nN);
