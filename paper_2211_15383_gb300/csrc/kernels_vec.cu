@@ -187,9 +187,6 @@ __global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, 
     }
 }
 
-// w += sign * sum_k coef[k] V[k]: each block owns a contiguous range of rows and walks
-// it two rows per trip (both loads of w and of every V[k] issued together), with
-// pointer increments; norm_part (may be null) receives |w|^2 partials of the result.
 template <typename C>
 __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef, int m, const C* __restrict__ V,
                             double sign, long long n, int N, double* __restrict__ norm_part) {
@@ -203,30 +200,15 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
         cf[k][threadIdx.x] = mk((R)(c.x * sign), (R)(c.y * sign));
     }
     __syncthreads();
-    const long long per = (n + gridDim.y - 1) / gridDim.y;
-    const long long r0 = (long long)blockIdx.y * per, r1 = min(n, r0 + per);
-    const long long step = (long long)kRowLanes * N;
     R nrm = 0;
-    if (j < N) {
-        C* wp = w + (r0 + threadIdx.y) * N + j;
-        const C* vp = V + (r0 + threadIdx.y) * N + j;
-        for (long long i0 = r0 + threadIdx.y; i0 < r1; i0 += 2 * kRowLanes, wp += 2 * step, vp += 2 * step) {
-            const bool in1 = i0 + kRowLanes < r1;
-            C a0 = wp[0];
-            C a1 = in1 ? wp[step] : czero<C>();
-            for (int k = 0; k < m; ++k) {
-                const C c = cf[k][threadIdx.x];
-                cfma(a0, c, vp[k * stride]);
-                if (in1) cfma(a1, c, vp[step + k * stride]);
-            }
-            wp[0] = a0;
-            nrm = fma(a0.x, a0.x, fma(a0.y, a0.y, nrm));
-            if (in1) {
-                wp[step] = a1;
-                nrm = fma(a1.x, a1.x, fma(a1.y, a1.y, nrm));
-            }
+    if (j < N)
+        for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
+             i += (long long)gridDim.y * kRowLanes) {
+            C acc = w[i * N + j];
+            for (int k = 0; k < m; ++k) cfma(acc, cf[k][threadIdx.x], V[k * stride + i * N + j]);
+            w[i * N + j] = acc;
+            nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
         }
-    }
     if (norm_part) {
         // |w|^2 partials of the updated vector, as k_norm2 writes them
         sh[threadIdx.y][threadIdx.x] = (double)nrm;
