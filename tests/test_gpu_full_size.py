@@ -1,5 +1,6 @@
 """Full-size parity on the 128x128 workload in the launch configuration the
-benchmark times (FP64, one block of 256 right-hand sides per term): the GPU's
+benchmark times (one block of 256 right-hand sides per term; every precision of the
+multigrid, 16 being the benchmark's): the GPU's
 own setup and deflation against the oracle's, and sampled per-sample values
 (the first 16 of each 256-sample block, which the oracle computes one by one
 with sparse-LU solves)."""
@@ -31,7 +32,7 @@ def c2():
     return w, theta, sv, H, defl
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 16])
 def test_full_size_sampled_parity(pkg, c2, prec):
     w, theta, sv, H, defl = c2
     solvers = oest.DirectSolvers(H)
