@@ -287,12 +287,7 @@ void launch_embed_bf16(__nv_bfloat16* E, const float2* A, int n, cudaStream_t s)
 
 bool tc_coarse_supported(int n) { return n >= 128 && n % 128 == 0; }
 
-// Output tile width: 256 columns, unless 128-column tiles alone already give about one
-// CTA per SM (then no split-K and no partial-sum pass is needed).
-static int pick_nt(int n, int N) {
-    if (2 * N >= 256 && (2 * N / 128) * (n / tc::BM) >= kNumSM * 3 / 4 && (2 * N) % 128 == 0) return 128;
-    return (2 * N >= 256) ? 256 : (2 * N > 64 ? 128 : 64);
-}
+static int pick_nt(int N) { return (2 * N >= 256) ? 256 : (2 * N > 64 ? 128 : 64); }
 
 // Split-K factor: one CTA per SM (the stages fill ~192 KB of shared memory), so
 // split the K range until the tiles cover the 152 SMs once.
@@ -308,7 +303,7 @@ static int pick_splits(int n, int Ncols, int NT) {
 }
 
 size_t coarse_inverse_bf16_scratch(int n, int N) {
-    const int NT = pick_nt(n, N);
+    const int NT = pick_nt(N);
     const size_t ncols = (size_t)((2 * N + NT - 1) / NT) * NT;
     const int S = pick_splits(n, (int)ncols, NT);
     return ncols * 2 * n * sizeof(__nv_bfloat16) + (size_t)S * n * ncols * sizeof(float) + 256;
@@ -341,7 +336,7 @@ static void launch_pack(__nv_bfloat16* Bt, const float2* X, int n, int N, int Nc
 void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N, void* scratch,
                                 int* err, cudaStream_t s) {
     MG_REQUIRE(tc_coarse_supported(n), MGMLMC_EINVAL, "tensor-core coarsest solve needs n % 128 == 0");
-    const int NT = pick_nt(n, N);
+    const int NT = pick_nt(N);
     const int Ncols = ((2 * N + NT - 1) / NT) * NT;
     const int S = pick_splits(n, Ncols, NT);
     __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(scratch);
