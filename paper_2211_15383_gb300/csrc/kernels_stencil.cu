@@ -813,20 +813,28 @@ __global__ void k_pack_bf16(uint32_t* __restrict__ y, const float2* __restrict__
     if (i < count) y[i] = f2_bf(x[i]);
 }
 
+// Two rhs per thread: 8-byte BF16 and 16-byte FP32 accesses.  N even.
 __global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restrict__ r, const uint32_t* __restrict__ p,
                                       const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
-    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
     if (j >= N) return;
-    const double2 pr = dots[j];
-    const double pp = dots[N + j].x;
-    const float2 a = pp > 0.0 ? make_float2((float)(pr.x / pp), (float)(pr.y / pp)) : make_float2(0.f, 0.f);
+    float2 a[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const double2 pr = dots[j + q];
+        const double pp = dots[N + j + q].x;
+        a[q] = pp > 0.0 ? make_float2((float)(pr.x / pp), (float)(pr.y / pp)) : make_float2(0.f, 0.f);
+    }
     for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n; i += (long long)gridDim.y * kRowLanes) {
         const long long idx = i * N + j;
-        const float2 rv = bf2_lo(r[idx]), pv = bf2_lo(p[idx]);
-        float2 ev = e_is_zero ? make_float2(0.f, 0.f) : e[idx];
-        cfma(ev, a, rv);
-        e[idx] = ev;
-        r[idx] = f2_bf(csub(rv, cmul(a, pv)));
+        const uint2 rw = *reinterpret_cast<const uint2*>(r + idx), pw = *reinterpret_cast<const uint2*>(p + idx);
+        float4 ev = e_is_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(e + idx);
+        const float2 r0 = bf2_lo(rw.x), r1 = bf2_lo(rw.y), p0 = bf2_lo(pw.x), p1 = bf2_lo(pw.y);
+        float2 e0 = make_float2(ev.x, ev.y), e1 = make_float2(ev.z, ev.w);
+        cfma(e0, a[0], r0);
+        cfma(e1, a[1], r1);
+        *reinterpret_cast<float4*>(e + idx) = make_float4(e0.x, e0.y, e1.x, e1.y);
+        *reinterpret_cast<uint2*>(r + idx) = make_uint2(f2_bf(csub(r0, cmul(a[0], p0))), f2_bf(csub(r1, cmul(a[1], p1))));
     }
 }
 
@@ -845,7 +853,9 @@ void launch_pack_bf16(uint32_t* y, const float2* x, long long count, cudaStream_
 
 void launch_mr_update_fine_bf16(float2* e, uint32_t* r, const uint32_t* p, const double2* dots, long long n, int N,
                                 bool e_is_zero, cudaStream_t s) {
-    k_mr_update_fine_bf16<<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, s>>>(e, r, p, dots, n, N, e_is_zero);
+    MG_REQUIRE(N % 2 == 0, MGMLMC_EINVAL, "BF16 MR update: N even");
+    k_mr_update_fine_bf16<<<dim3((N / 2 + kRhsTile - 1) / kRhsTile, row_groups(n, N)), blk(), 0, s>>>(e, r, p, dots,
+                                                                                                    n, N, e_is_zero);
     MG_LAUNCHED();
 }
 

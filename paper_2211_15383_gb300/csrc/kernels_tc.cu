@@ -376,11 +376,11 @@ namespace tc {
 // k_mr_update_tc for the next ones), so the stencil moves 8 KB blocks straight
 // into shared memory and never converts.
 //
-// Warp-specialised and persistent: two CTAs per SM, each over one 128-rhs tile
+// Warp-specialised and persistent: three CTAs per SM, each over one 128-rhs tile
 // and a strided set of sites; a CTA's work is a sequence of jobs (site,
 // direction).
 //   warp 0 (one thread): streams each job's neighbour tile (8 KB) with a 1-D
-//     bulk copy into a ring of 8 stage buffers, and with a site's first job the
+//     bulk copy into a ring of 6 stage buffers, and with a site's first job the
 //     site's 10 KB of B (two site slots alternate);
 //   warp 1 (one thread): issues two MMAs (M = 128, N = 32, K = 16) per job
 //     straight from the stage buffer into the site's TMEM accumulator (two sets
@@ -396,9 +396,10 @@ constexpr int TILE_A = 128 * KD * 2;       // 8 KB: one 128-rhs BF16 tile of X^T
 constexpr int B_DIR = KD * KD * 2;         // 2 KB: one B(s, dir)
 constexpr int B_SITE = 5 * B_DIR;          // 10 KB per site
 constexpr int CH = 128;                    // rhs per CTA (one 128-row tile)
-constexpr int NSTG = 8;                    // stage ring depth
+constexpr int NSTG = 6;                    // stage ring depth
 constexpr int THREADS = 192;               // 6 warps
-constexpr int SMEM = NSTG * TILE_A + 2 * B_SITE;   // 84 KB: two CTAs per SM
+constexpr int kCtasPerSm = 3;              // three pipelines per SM
+constexpr int SMEM = NSTG * TILE_A + 2 * B_SITE;   // 68 KB: three CTAs per SM
 constexpr int TCOLS = 64;                  // two accumulators of 32 columns
 constexpr int kMaxDevWait = 1 << 26;
 // direction of the o-th job of a site: the neighbours first, the self block last
@@ -568,7 +569,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // FORM 0: y = A x as FP32 rows, with the dots; 1: y as BF16 tiles (yt), with the dots;
 // 2: the residual b - A x as BF16 tiles (yt), b FP32 rows, no dots.
 template <int FORM>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, kCtasPerSm)
     k_block_stencil_tc(float2* __restrict__ y, __nv_bfloat16* __restrict__ yt, const float2* __restrict__ b,
                        const __nv_bfloat16* __restrict__ xt, const __nv_bfloat16* __restrict__ E, int lx, int lt, int N,
                        double2* __restrict__ part, int* __restrict__ err) {
@@ -785,9 +786,9 @@ void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* 
     MG_LAUNCHED();
 }
 
-// Two persistent CTAs per SM (84 KB of shared memory each) over the 128-rhs tiles.
+// Three persistent CTAs per SM (68 KB of shared memory each) over the 128-rhs tiles.
 int block_stencil_tc_groups(int nsites, int N) {
-    int g = 2 * kNumSM / tc_tiles(N);
+    int g = tc::tcs::kCtasPerSm * kNumSM / tc_tiles(N);
     if (g < 1) g = 1;
     return nsites < g ? nsites : g;
 }
