@@ -537,6 +537,106 @@ __global__ void __launch_bounds__(128) k_prolong_nv(C* __restrict__ x, const C* 
     }
 }
 
+// The same two operators with the dofs per fine site (D) fixed at compile time: the
+// loads of QB aggregate sites (QB * D values per thread) are issued together before
+// the FMAs, instead of one load per loop trip.
+template <typename C, int NV, int D, int QB>
+__global__ void __launch_bounds__(128) k_restrict_nvd(C* __restrict__ xc, const C* __restrict__ x,
+                                                      const C* __restrict__ P, int lx, int lt, int ax, int at, int N) {
+    extern __shared__ __align__(16) unsigned char smem_rp[];
+    C* Ps = reinterpret_cast<C*>(smem_rp);
+    constexpr int HD = D / 2;
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int cx = lx / ax, ct = lt / at, na = ax * at;
+    const int nP = na * D * NV;
+    for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
+        const int X = S % cx, T = S / cx;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nP; e += 128) {
+            const int q = e / (D * NV), r = e % (D * NV);
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            Ps[e] = P[(long long)site * D * NV + r];
+        }
+        __syncthreads();
+        if (j >= N) continue;
+        C acc[2 * NV];
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) acc[o] = czero<C>();
+        for (int q0 = 0; q0 < na; q0 += QB) {
+            C xv[QB][D];
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq) {
+                const int q = q0 + qq;
+                const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    xv[qq][a] = q < na ? x[((long long)site * D + a) * N + j] : czero<C>();
+            }
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq) {
+                if (q0 + qq >= na) break;
+                const C* Pq = Ps + (q0 + qq) * D * NV;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfmac(acc[(a < HD ? 0 : NV) + jv], Pq[a * NV + jv], xv[qq][a]);
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) xc[((long long)S * 2 * NV + o) * N + j] = acc[o];
+    }
+}
+
+template <typename C, int NV, int D, int QB>
+__global__ void __launch_bounds__(128) k_prolong_nvd(C* __restrict__ x, const C* __restrict__ xc,
+                                                     const C* __restrict__ P, int lx, int lt, int ax, int at, int N,
+                                                     bool accumulate) {
+    extern __shared__ __align__(16) unsigned char smem_rp[];
+    C* Ps = reinterpret_cast<C*>(smem_rp);
+    constexpr int HD = D / 2;
+    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int cx = lx / ax, ct = lt / at, na = ax * at;
+    const int nP = na * D * NV;
+    for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
+        const int X = S % cx, T = S / cx;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nP; e += 128) {
+            const int q = e / (D * NV), r = e % (D * NV);
+            const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+            Ps[e] = P[(long long)site * D * NV + r];
+        }
+        __syncthreads();
+        if (j >= N) continue;
+        C cv[2 * NV];
+#pragma unroll
+        for (int o = 0; o < 2 * NV; ++o) cv[o] = xc[((long long)S * 2 * NV + o) * N + j];
+        for (int q0 = 0; q0 < na; q0 += QB) {
+            C ov[QB][D];
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq) {
+                const int q = q0 + qq;
+                const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    ov[qq][a] = (accumulate && q < na) ? x[((long long)site * D + a) * N + j] : czero<C>();
+            }
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq) {
+                const int q = q0 + qq;
+                if (q >= na) break;
+                const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
+                const C* Pq = Ps + q * D * NV;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+#pragma unroll
+                    for (int jv = 0; jv < NV; ++jv) cfma(ov[qq][a], Pq[a * NV + jv], cv[(a < HD ? 0 : NV) + jv]);
+                    x[((long long)site * D + a) * N + j] = ov[qq][a];
+                }
+            }
+        }
+    }
+}
+
 template <typename C>
 __global__ void k_mr_update(C* __restrict__ e, C* __restrict__ r, const C* __restrict__ p,
                             const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
@@ -981,6 +1081,18 @@ static void rp_launch(bool restrict_op, C* xc_or_x, const C* in, const C* P, int
     if (G > ncs) G = ncs;
     if (G < 1) G = 1;
     const size_t sm = (size_t)ax * at * d * NV * sizeof(C);
+    if (d == 2) {
+        if (restrict_op) k_restrict_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
+        else k_prolong_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
+        MG_LAUNCHED();
+        return;
+    }
+    if (d == 16) {
+        if (restrict_op) k_restrict_nvd<C, NV, 16, 1><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
+        else k_prolong_nvd<C, NV, 16, 1><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
+        MG_LAUNCHED();
+        return;
+    }
     if (restrict_op)
         k_restrict_nv<C, NV><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N);
     else
