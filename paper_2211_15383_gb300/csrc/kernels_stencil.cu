@@ -1082,8 +1082,8 @@ static void rp_launch(bool restrict_op, C* xc_or_x, const C* in, const C* P, int
     if (G < 1) G = 1;
     const size_t sm = (size_t)ax * at * d * NV * sizeof(C);
     if (d == 2) {
-        if (restrict_op) k_restrict_nvd<C, NV, 2, 16><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
-        else k_prolong_nvd<C, NV, 2, 8><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
+        if (restrict_op) k_restrict_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
+        else k_prolong_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
         MG_LAUNCHED();
         return;
     }
