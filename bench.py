@@ -8,8 +8,10 @@ One step = one block of 256 samples on every term of the telescoping sum
 (two multigrid-preconditioned solves per difference-level sample, one solve
 plus the deflation projections for the coarsest term, FP64 sample assembly).
 The headline run solves every block in FP64 by iterative refinement around an
-FP32 multigrid cycle with a BF16 tensor-core coarsest solve; the all-FP64
-path and the plain FP64 single-rhs path are measured beside it, with the
+FP32 multigrid cycle with BF16 tensor-core smoothers and coarsest solve, and
+runs the terms of a step at once (one context and CUDA stream per term,
+mgmlmc_estimate_concurrent; the one-context sequential rate is reported too);
+the all-FP64 path and the plain FP64 single-rhs path are measured beside it, with the
 per-sample difference of the two batched runs on the same noise.  The line
 also carries the time to tr(D^-1) at relative error 1e-4 (the paper's
 tolerance) and the fine stencil's HBM bandwidth.
@@ -62,6 +64,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the comparison run in the other precision and the single-rhs FP64 run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="one context, terms one after another (default: the terms of a step at once, "
+                         "one context and CUDA stream per term, via mgmlmc_estimate_concurrent)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--ttt-tol", type=float, default=1e-4,
                     help="relative error of the time-to-trace run (0 = skip)")
@@ -299,19 +304,41 @@ def gpu_arm(args, rank, ws, local):
     nterms, _ = ctx.num_terms()
     K, W = args.steps, args.warmup
     seed = replica_seed(w, rank)
-    run_steps(ctx, w, nterms, 0, W, seed)                                   # warm-up
+    # the terms of a step are independent: one context (same inputs, same hierarchy) and
+    # CUDA stream per term, all terms at once through mgmlmc_estimate_concurrent
+    ctxs = [ctx]
+    if not args.sequential:
+        for t in range(1, nterms):
+            with torch.cuda.stream(torch.cuda.Stream()):
+                ctxs.append(make_ctx(pkg, w, args.precision)[0])
+
+    def steps(first, count, probes=None, outs=None):
+        for k in range(first, first + count):
+            if len(ctxs) > 1:
+                pkg.estimate_concurrent(ctxs, list(range(nterms)), k * w.nrhs, w.nrhs, seed,
+                                        probes=None if probes is None else probes[k - first],
+                                        samples=outs is not None, out=outs)
+            elif probes is None:
+                run_steps(ctx, w, nterms, k, 1, seed)
+            else:
+                for t in range(nterms):
+                    ctx.estimate_level_probes(t, probes[k - first][t], out=outs[t])
+
+    steps(0, W)                                                             # warm-up
     # timed region: no event profiling (it costs host time per launch); the launch
     # counter is reset so that the kernels launched inside it are counted
     ctx.profile(False, reset=True)
     clk = Clocks(local)
     clk.start()
     tag = "timed_f64" if args.precision == 64 else "timed_mixed"
-    sec = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W, K, seed), tag if args.nvtx else None)
+    sec = timed_region(torch, ws, lambda: steps(W, K), tag if args.nvtx else None)
     clocks = clk.stop()
     launches = int(ctx.profile_report().get("__launches__", {}).get("count", 0))
-    # the same K steps again with per-kernel-class CUDA events (roofline, class shares)
+    # for comparison: the same amount of work with the terms one after another on one context
+    sec_seq = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W + K, K, seed)) if len(ctxs) > 1 else sec
+    # K steps on one context with per-kernel-class CUDA events (roofline, class shares)
     ctx.profile(True, reset=True)
-    sec_prof = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W + K, K, seed))
+    sec_prof = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W + 2 * K, K, seed))
     ctx.profile(False)
     report = ctx.profile_report()
     report.pop("__launches__", None)
@@ -343,9 +370,13 @@ def gpu_arm(args, rank, ws, local):
            # device time inside profiled classes per step, against the profiled step: the
            # remainder is launch gaps and host round trips (convergence checks)
            "profiled_kernel_ms_per_step": sum(v["ms"] for v in report.values()) / K,
+           "terms_concurrent": len(ctxs) > 1,
+           "sequential": {"value": job_throughput(K * nterms * w.nrhs, ws, sec_seq), "unit": UNIT,
+                          "ms_per_step": sec_seq / K * 1e3,
+                          "what": "same steps, terms one after another on one context and stream"},
            "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
                      "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
-           "iters": {t: ctx.get_stats(t)["iters"] for t in range(nterms)}}
+           "iters": {t: sum(c.get_stats(t)["iters"] for c in ctxs) for t in range(nterms)}}
     out["gpu_launches"] = launches
     # end-to-end through the public C ABI with host probe vectors and host samples
     if not args.no_e2e:
@@ -361,19 +392,16 @@ def gpu_arm(args, rank, ws, local):
                 arr.numpy()[:] = np.where(u < 0.5, 1, -1).reshape(w.nrhs, n_of[t])
                 per.append(arr)
             probes.append(per)
-        outs = [torch.empty((w.nrhs, 2), dtype=torch.float64, pin_memory=True) for _ in range(nterms)]
+        outs = [torch.empty((w.nrhs, 2), dtype=torch.float64, pin_memory=True).numpy().view(np.complex128)
+                .reshape(-1) for _ in range(nterms)]
+        hprobes = [[probes[k][t].numpy() for t in range(nterms)] for k in range(K)]
 
-        def e2e_steps():
-            for k in range(K):
-                for t in range(nterms):
-                    o = outs[t].numpy().view(np.complex128).reshape(-1)
-                    ctx.estimate_level_probes(t, probes[k][t].numpy(), out=o)
-
-        sec_e2e = timed_region(torch, ws, e2e_steps, "timed_e2e" if args.nvtx else None)
+        sec_e2e = timed_region(torch, ws, lambda: steps(0, K, hprobes, outs), "timed_e2e" if args.nvtx else None)
         out["e2e"] = {"value": samples / sec_e2e, "unit": UNIT,
                       "h2d_bytes_per_step": int(sum(w.nrhs * n for n in n_of)),
                       "d2h_bytes_per_step": int(nterms * w.nrhs * 16),
-                      "path": "mgmlmc_estimate_level_probes: pinned host int8 probes in, host samples out"}
+                      "path": ("mgmlmc_estimate_concurrent" if len(ctxs) > 1 else "mgmlmc_estimate_level_probes")
+                              + ": pinned host int8 probes in, host samples out"}
     # time to tr(D^-1) at a fixed relative error (MLMC loop of the library)
     if args.ttt_tol > 0:
         t0 = time.time()
@@ -386,6 +414,8 @@ def gpu_arm(args, rank, ws, local):
                                 "samples_per_term": [t["nsamples"] for t in res["terms"]]}
     # the other precision on the same workload (error of the mixed run against FP64 on the
     # same noise), then the plain FP64 single-rhs path
+    for c_ in ctxs[1:]:
+        c_.close()
     if not args.no_mixed:
         other = 64 if args.precision != 64 else 32
         head_samples = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]

@@ -222,6 +222,23 @@ int mgmlmc_estimate_level(mgmlmc_ctx* ctx, int term, int64_t first_sample, int n
 int mgmlmc_estimate_level_probes(mgmlmc_ctx* ctx, int term, int nsamples, const int8_t* probes,
                                  double* samples_out, mgmlmc_level_stats* stats);
 
+/* Several terms at once: the terms of the telescoping sum are independent
+ * (Sect. 3.2), so entry i runs mgmlmc_estimate_level (probes NULL or probes[i]
+ * NULL) or mgmlmc_estimate_level_probes (probes[i] a host array [nsamples][n_a])
+ * for term terms[i] on contexts[i], each entry on its own host thread (entry 0
+ * on the calling one).  The contexts must be distinct (MGMLMC_EINVAL otherwise),
+ * built from the same gauge field, mass and hierarchy inputs if their samples
+ * are to be combined, and each created on its own CUDA stream: their kernels
+ * then overlap on the GPU, and the host round trips of one term (convergence
+ * checks) are covered by the others' work.  first_sample and seed apply to the
+ * device-noise entries.  samples_out (may be NULL; so may each samples_out[i])
+ * receives 2*nsamples doubles per entry; stats (may be NULL) n statistics.
+ * Returns MGMLMC_OK, or the status of the first entry that failed (that
+ * context holds its message); every entry runs to completion either way. */
+int mgmlmc_estimate_concurrent(mgmlmc_ctx* const* contexts, int n, const int* terms, int64_t first_sample,
+                               int nsamples, uint64_t seed, const int8_t* const* probes,
+                               double* const* samples_out, mgmlmc_level_stats* stats);
+
 /* Running totals of term t since the last mgmlmc_reset_stats. */
 int mgmlmc_get_stats(mgmlmc_ctx* ctx, int term, mgmlmc_level_stats* stats);
 int mgmlmc_reset_stats(mgmlmc_ctx* ctx);

@@ -78,6 +78,9 @@ SIGNATURES = [
     ("mgmlmc_estimate_level", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D, C.POINTER(LevelStats)]),
     ("mgmlmc_estimate_level_probes", C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int8), _D,
                                                C.POINTER(LevelStats)]),
+    ("mgmlmc_estimate_concurrent", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), C.c_int64, C.c_int,
+                                             C.c_uint64, C.POINTER(C.POINTER(C.c_int8)), C.POINTER(_D),
+                                             C.POINTER(LevelStats)]),
     ("mgmlmc_get_stats", C.c_int, [_P, C.c_int, C.POINTER(LevelStats)]),
     ("mgmlmc_reset_stats", C.c_int, [_P]),
     ("mgmlmc_estimate_trace", C.c_int, [_P, C.c_double, C.c_int64, C.c_uint64, _D, C.POINTER(TraceResult)]),
@@ -119,6 +122,37 @@ def _cplx(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
+def estimate_concurrent(contexts, terms, first_sample: int, nsamples: int, seed: int, probes=None,
+                        samples: bool = True, out=None):
+    """mgmlmc_estimate_concurrent: entry i estimates term terms[i] on contexts[i] (each
+    created on its own CUDA stream), all entries at once.  probes: None or a list with
+    None (device noise) or an int8 array [nsamples][n_a] per entry.  Returns the list of
+    sample arrays (or None) and the list of statistics dicts."""
+    n = len(contexts)
+    lib = contexts[0].lib
+    hs = (_P * n)(*[c.h for c in contexts])
+    ts = (C.c_int * n)(*terms)
+    keep = []
+    pp = None
+    if probes is not None:
+        pp = (C.POINTER(C.c_int8) * n)()
+        for i, p in enumerate(probes):
+            if p is not None:
+                a = np.ascontiguousarray(p, dtype=np.int8)
+                keep.append(a)
+                pp[i] = a.ctypes.data_as(C.POINTER(C.c_int8))
+    outs = None
+    if samples:
+        outs = out if out is not None else [np.zeros(nsamples, np.complex128) for _ in range(n)]
+    op = (_D * n)(*[o.ctypes.data_as(_D) for o in outs]) if outs is not None else None
+    st = (LevelStats * n)()
+    code = lib.mgmlmc_estimate_concurrent(hs, n, ts, first_sample, nsamples, seed, pp, op, st)
+    if code != 0:
+        bad = next((c for c in contexts if lib.mgmlmc_last_error(c.h)), contexts[0])
+        bad._check(code)
+    return outs, [s_.as_dict() for s_ in st]
+
+
 def fma_peak(precision: int) -> float:
     """Measured FMA throughput (FLOP/s) of the current device, precision 64 or 32."""
     v = C.c_double()
@@ -151,11 +185,16 @@ class Context:
         self.lib = load()
         self.options = options if options is not None else default_options(**kw)
         self._mem = {}
-        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        # the context works on the stream current at creation; its device memory is
+        # taken on that stream too, so that a block the library gives back is reused
+        # only in the order of that stream (whichever host thread calls in)
+        self._stream = torch.cuda.current_stream()
+        stream = C.c_void_p(self._stream.cuda_stream)
         if torch_memory:
             def _alloc(user, nbytes):
                 try:
-                    t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+                    with torch.cuda.stream(self._stream):
+                        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
                 except Exception:
                     return None
                 self._mem[t.data_ptr()] = t

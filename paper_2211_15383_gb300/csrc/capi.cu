@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "context.h"
@@ -402,6 +403,43 @@ int mgmlmc_estimate_level_probes(mgmlmc_ctx* h, int term, int nsamples, const in
         mg::launch_probes<double2>(X, dp, n, Nb, c.stream);
     });
     API_END
+}
+
+int mgmlmc_estimate_concurrent(mgmlmc_ctx* const* contexts, int n, const int* terms, int64_t first_sample,
+                               int nsamples, uint64_t seed, const int8_t* const* probes, double* const* samples_out,
+                               mgmlmc_level_stats* stats) {
+    if (!contexts || !terms || n < 1 || n > 64) return MGMLMC_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!contexts[i]) return MGMLMC_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (contexts[k] == contexts[i]) return MGMLMC_EINVAL;   // one host thread per context
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MGMLMC_ECUDA;
+    std::vector<int> rc(n, MGMLMC_OK);
+    auto run = [&](int i) {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            rc[i] = MGMLMC_ECUDA;
+            return;
+        }
+        double* out = samples_out ? samples_out[i] : nullptr;
+        mgmlmc_level_stats* st = stats ? stats + i : nullptr;
+        rc[i] = (probes && probes[i])
+                    ? mgmlmc_estimate_level_probes(contexts[i], terms[i], nsamples, probes[i], out, st)
+                    : mgmlmc_estimate_level(contexts[i], terms[i], first_sample, nsamples, seed, out, st);
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int i = 1; i < n; ++i) pool.emplace_back(run, i);
+    } catch (...) {
+        for (auto& t : pool) t.join();
+        return MGMLMC_ENOMEM;
+    }
+    run(0);
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < n; ++i)
+        if (rc[i] != MGMLMC_OK) return rc[i];
+    return MGMLMC_OK;
 }
 
 int mgmlmc_get_stats(mgmlmc_ctx* h, int term, mgmlmc_level_stats* stats) {

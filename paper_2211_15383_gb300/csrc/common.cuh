@@ -3,6 +3,8 @@
 // of the CPU oracle.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -28,7 +30,7 @@ struct Error : std::runtime_error {
     } while (0)
 
 // Kernel launches issued by this library (process-wide), for launch accounting.
-long long& launch_counter();
+std::atomic<long long>& launch_counter();   // all contexts, thread-safe
 
 #define MG_LAUNCHED()                                                                  \
     do {                                                                               \

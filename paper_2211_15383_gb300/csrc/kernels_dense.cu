@@ -276,7 +276,7 @@ void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s) {
         k_gj_pivot<C><<<1, 1024, 0, s>>>(A, n, k, w);
         k_gj_eliminate<C><<<dim3((n + 127) / 128, gy), 128, 0, s>>>(A, n, k, w);
     }
-    launch_counter() += 2LL * n - 1;
+    launch_counter().fetch_add(2LL * n - 1);
     MG_LAUNCHED();
     k_gj_unpermute<C><<<(n + 127) / 128, 128, 0, s>>>(A, n, w);
     MG_LAUNCHED();

@@ -105,8 +105,8 @@ void Ctx::sync() {
 }
 
 // ------------------------------------------------------------------ profiler
-long long& launch_counter() {
-    static long long n = 0;
+std::atomic<long long>& launch_counter() {
+    static std::atomic<long long> n{0};
     return n;
 }
 

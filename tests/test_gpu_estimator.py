@@ -209,3 +209,37 @@ def test_three_levels_with_wide_coarse_blocks(pkg, prec):
             got, _ = ctx.estimate_level(t, 0, 40, 21)
             ref = oest.noise_samples(H, term, 21, 0, 40, solvers)
             assert rel_sample_error(got, ref) < TOL64, (prec, term)
+
+
+def test_concurrent_terms_on_separate_streams(pkg, c1):
+    # the two terms of the 16x16 workload at once, each on its own context and CUDA
+    # stream (one entry with device noise, one with caller probes): the same samples
+    # as the one-term calls, and as the oracle's
+    import torch
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    ctxs = []
+    for s in streams:
+        with torch.cuda.stream(s):
+            ctx = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        ctxs.append(ctx)
+    try:
+        n1 = H.D[-1].shape[0]
+        probes = np.where(inputs.uniform(5, 1, 48 * n1).reshape(48, n1) < 0.5, 1, -1).astype(np.int8)
+        for rep in range(2):                                     # twice in a row
+            outs, stats = pkg.estimate_concurrent(ctxs, [0, 1], 16, 48, w.noise_seed, probes=[None, probes])
+            assert [s["nsamples"] for s in stats] == [48, 48]
+            seq0, _ = ctxs[0].estimate_level(0, 16, 48, w.noise_seed)
+            seq1, _ = ctxs[1].estimate_level_probes(1, probes)
+            assert np.array_equal(outs[0], seq0) and np.array_equal(outs[1], seq1)
+        ref0 = oest.noise_samples(H, (1, 2), w.noise_seed, 16, 48, solvers)
+        ref1 = oest.term_samples(H, (2, None), probes.astype(float), solvers, defl)
+        assert rel_sample_error(outs[0], ref0) < TOL64
+        assert rel_sample_error(outs[1], ref1) < TOL64
+        with pytest.raises(pkg.MgmlmcError):
+            pkg.estimate_concurrent([ctxs[0], ctxs[0]], [0, 1], 0, 8, 1)   # one context twice
+    finally:
+        for ctx in ctxs:
+            ctx.close()
