@@ -253,6 +253,14 @@ int mgmlmc_reset_stats(mgmlmc_ctx* ctx);
 int mgmlmc_estimate_trace(mgmlmc_ctx* ctx, double rel_tol, int64_t max_samples, uint64_t seed,
                           const double* costs, mgmlmc_trace_result* out);
 
+/* mgmlmc_estimate_trace with the terms drawn at once: contexts[t] (n = the number
+ * of terms, distinct contexts built from the same inputs, each created on its own
+ * CUDA stream) draws the samples of term t, on one host thread per term within
+ * each round of the loop; the allocation and the stopping rule see all terms'
+ * statistics, as in mgmlmc_estimate_trace.  Errors are reported in contexts[0]. */
+int mgmlmc_estimate_trace_concurrent(mgmlmc_ctx* const* contexts, int n, double rel_tol, int64_t max_samples,
+                                     uint64_t seed, const double* costs, mgmlmc_trace_result* out);
+
 /* Test hook: y = op(x) for nrhs host vectors [nrhs][n_in] -> [nrhs][n_out]. */
 int mgmlmc_apply(mgmlmc_ctx* ctx, int op, int level, int nrhs, const double* x, double* y);
 

@@ -4,5 +4,6 @@ the 2D Wilson-Schwinger operator (Frommer & Ramirez-Hidalgo, Lattice 2022).
 The computation lives in ``libmgmlmc.so`` (CUDA kernels behind the C ABI of
 ``include/mgmlmc.h``); ``Context`` is its thin Python binding.
 """
-from ._lib import (Context, MgmlmcError, Options, default_options, estimate_concurrent, fma_peak, load, LIB_PATH,  # noqa: F401
+from ._lib import (Context, MgmlmcError, Options, default_options, estimate_concurrent,
+                   estimate_trace_concurrent, fma_peak, load, LIB_PATH,  # noqa: F401
                    OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C, OP_SMOOTH)

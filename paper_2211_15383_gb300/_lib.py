@@ -84,6 +84,8 @@ SIGNATURES = [
     ("mgmlmc_get_stats", C.c_int, [_P, C.c_int, C.POINTER(LevelStats)]),
     ("mgmlmc_reset_stats", C.c_int, [_P]),
     ("mgmlmc_estimate_trace", C.c_int, [_P, C.c_double, C.c_int64, C.c_uint64, _D, C.POINTER(TraceResult)]),
+    ("mgmlmc_estimate_trace_concurrent", C.c_int, [C.POINTER(_P), C.c_int, C.c_double, C.c_int64, C.c_uint64, _D,
+                                                   C.POINTER(TraceResult)]),
     ("mgmlmc_apply", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D, _D]),
     ("mgmlmc_solve", C.c_int, [_P, C.c_int, C.c_int, _D, _D, _I]),
     ("mgmlmc_noise", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D]),
@@ -120,6 +122,28 @@ def _dptr(a: np.ndarray):
 
 def _cplx(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _trace_dict(res):
+    d = {k: getattr(res, k) for k, _ in TraceResult._fields_ if k != "term"}
+    d["terms"] = [res.term[t].as_dict() for t in range(res.nterms)]
+    d["trace"] = complex(res.trace_re, res.trace_im)
+    return d
+
+
+def estimate_trace_concurrent(contexts, rel_tol: float, max_samples: int, seed: int, costs=None):
+    """mgmlmc_estimate_trace_concurrent: the MLMC loop with term t drawn on contexts[t]
+    (one context and CUDA stream per term), the terms of each round at once."""
+    n = len(contexts)
+    hs = (_P * n)(*[c.h for c in contexts])
+    res = TraceResult()
+    cst = None
+    if costs is not None:
+        arr = np.ascontiguousarray(costs, dtype=np.float64)
+        cst = _dptr(arr)
+    contexts[0]._check(contexts[0].lib.mgmlmc_estimate_trace_concurrent(hs, n, float(rel_tol), int(max_samples),
+                                                                         C.c_uint64(seed), cst, C.byref(res)))
+    return _trace_dict(res)
 
 
 def estimate_concurrent(contexts, terms, first_sample: int, nsamples: int, seed: int, probes=None,
@@ -344,10 +368,7 @@ class Context:
             cst = _dptr(arr)
         self._check(self.lib.mgmlmc_estimate_trace(self.h, float(rel_tol), int(max_samples), C.c_uint64(seed),
                                                    cst, C.byref(res)))
-        d = {k: getattr(res, k) for k, _ in TraceResult._fields_ if k != "term"}
-        d["terms"] = [res.term[t].as_dict() for t in range(res.nterms)]
-        d["trace"] = complex(res.trace_re, res.trace_im)
-        return d
+        return _trace_dict(res)
 
     # ---------------------------------------------------------------- test hooks
     def apply(self, op: int, level: int, x: np.ndarray, n_out: int):

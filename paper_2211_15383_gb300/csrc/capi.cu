@@ -455,45 +455,84 @@ int mgmlmc_reset_stats(mgmlmc_ctx* h) {
     API_END
 }
 
-int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, uint64_t seed, const double* costs,
-                          mgmlmc_trace_result* out) {
-    API_BEGIN(h)
+namespace {
+
+// The MLMC loop (Sect. 3.2 with the cited allocation rule): term t draws its samples
+// on ctx_of[t]; with `concurrent` the draws of one round run on one host thread per
+// term (the contexts are then distinct, each on its own stream).
+void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol, int64_t max_samples, uint64_t seed,
+               const double* costs, mgmlmc_trace_result* out) {
     MG_REQUIRE(out && rel_tol > 0 && max_samples > 0, MGMLMC_EINVAL, "estimate_trace: bad argument");
-    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "estimate_trace: no hierarchy");
-    const int T = c.nterms;
-    for (auto& s : c.stats) s = mg::TermStats();
+    const int T = ctx_of[0]->nterms;
+    for (Ctx* ct : ctx_of) {
+        MG_REQUIRE(ct->have_hier, MGMLMC_ESTATE, "estimate_trace: no hierarchy");
+        MG_REQUIRE(ct->nterms == T, MGMLMC_EINVAL, "estimate_trace: contexts with different term lists");
+        for (auto& st : ct->stats) st = mg::TermStats();
+    }
     const int pilot = 16;
     auto draw = [&](int t, long long first, long long count) {
+        Ctx& ct = *ctx_of[t];
         while (count > 0) {
             const int cnt = (int)std::min<long long>(count, 1 << 20);
-            const TermLevels tl = term_levels(c, t);
-            const long long n = c.lev[tl.a].n;
-            estimate_term(c, t, cnt, nullptr, nullptr, [&](int off, int Nb, double2* X) {
-                mg::launch_noise<double2>(X, n, Nb, seed, (uint64_t)(tl.a + 1), first + off, c.stream);
+            const TermLevels tl = term_levels(ct, t);
+            const long long n = ct.lev[tl.a].n;
+            estimate_term(ct, t, cnt, nullptr, nullptr, [&](int off, int Nb, double2* X) {
+                mg::launch_noise<double2>(X, n, Nb, seed, (uint64_t)(tl.a + 1), first + off, ct.stream);
             });
             first += cnt;
             count -= cnt;
         }
     };
-    for (int t = 0; t < T; ++t) draw(t, 0, pilot);
+    // one round of draws: [first, first + count) of term t for every t with count > 0
+    auto round = [&](const std::vector<long long>& first, const std::vector<long long>& count) {
+        if (!concurrent) {
+            for (int t = 0; t < T; ++t)
+                if (count[t] > 0) draw(t, first[t], count[t]);
+            return;
+        }
+        int dev = 0;
+        MG_CUDA(cudaGetDevice(&dev));
+        std::vector<int> code(T, MGMLMC_OK);
+        std::vector<std::string> msg(T);
+        auto run = [&](int t) {
+            try {
+                MG_CUDA(cudaSetDevice(dev));
+                draw(t, first[t], count[t]);
+            } catch (const Error& e) {
+                code[t] = e.code;
+                msg[t] = e.what();
+            } catch (const std::exception& e) {
+                code[t] = MGMLMC_ECUDA;
+                msg[t] = e.what();
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < T; ++t)
+            if (count[t] > 0) pool.emplace_back(run, t);
+        if (count[0] > 0) run(0);
+        for (auto& th : pool) th.join();
+        for (int t = 0; t < T; ++t)
+            if (code[t] != MGMLMC_OK) throw Error(code[t], "term " + std::to_string(t) + ": " + msg[t]);
+    };
+    round(std::vector<long long>(T, 0), std::vector<long long>(T, pilot));
     int rounds = 0;
-    double est_re = 0, est_im = 0, rel = 0;
+    double est_re = 0, est_im = 0, rel = 0, tau_re = 0, tau_im = 0;
+    for (int t = 0; t < T; ++t) {
+        const TermLevels tl = term_levels(*ctx_of[t], t);
+        if (tl.defl) {
+            tau_re += tl.defl->tau_re;
+            tau_im += tl.defl->tau_im;
+        }
+    }
     bool converged = false;
     for (;;) {
         std::vector<double> N(T), V(T), C(T);
-        est_re = 0.0;
-        est_im = 0.0;
-        for (int t = 0; t < T; ++t) {
-            const TermLevels tl = term_levels(c, t);
-            if (tl.defl) {
-                est_re += tl.defl->tau_re;
-                est_im += tl.defl->tau_im;
-            }
-        }
+        est_re = tau_re;
+        est_im = tau_im;
         double err2 = 0;
         long long total = 0;
         for (int t = 0; t < T; ++t) {
-            const mg::TermStats& S = c.stats[t];
+            const mg::TermStats& S = ctx_of[t]->stats[t];
             N[t] = (double)S.n;
             const double mr = S.sum_re / S.n, mi = S.sum_im / S.n;
             V[t] = std::max(0.0, (S.sum_abs2 - S.n * (mr * mr + mi * mi)) / (S.n - 1));
@@ -528,25 +567,51 @@ int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, ui
                 if (V[t] / N[t] > V[worst] / N[worst]) worst = t;
             target[worst] = 2 * (long long)N[worst];
         }
-        for (int t = 0; t < T; ++t)
-            if (target[t] > (long long)N[t]) draw(t, (long long)N[t], target[t] - (long long)N[t]);
+        std::vector<long long> first(T), count(T);
+        for (int t = 0; t < T; ++t) {
+            first[t] = (long long)N[t];
+            count[t] = std::max(0LL, target[t] - (long long)N[t]);
+        }
+        round(first, count);
         ++rounds;
     }
     out->trace_re = est_re;
     out->trace_im = est_im;
     out->rel_err = rel;
-    out->deflated_part = 0.0;
-    for (int t = 0; t < T; ++t) {
-        const TermLevels tl = term_levels(c, t);
-        if (tl.defl) out->deflated_part += tl.defl->tau_re;
-    }
+    out->deflated_part = tau_re;
     out->nterms = T;
     out->converged = converged ? 1 : 0;
     out->rounds = rounds;
     for (int t = 0; t < MGMLMC_MAX_LEVELS; ++t) {
         std::memset(&out->term[t], 0, sizeof(mgmlmc_level_stats));
-        if (t < T) fill_stats(c.stats[t], &out->term[t]);
+        if (t < T) fill_stats(ctx_of[t]->stats[t], &out->term[t]);
     }
+}
+
+}  // namespace
+
+int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, uint64_t seed, const double* costs,
+                          mgmlmc_trace_result* out) {
+    API_BEGIN(h)
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "estimate_trace: no hierarchy");
+    mlmc_loop(std::vector<Ctx*>(c.nterms, &c), false, rel_tol, max_samples, seed, costs, out);
+    API_END
+}
+
+int mgmlmc_estimate_trace_concurrent(mgmlmc_ctx* const* contexts, int n, double rel_tol, int64_t max_samples,
+                                     uint64_t seed, const double* costs, mgmlmc_trace_result* out) {
+    if (!contexts || n < 1) return MGMLMC_EINVAL;
+    mgmlmc_ctx* h = contexts[0];
+    API_BEGIN(h)
+    MG_REQUIRE(c.have_hier && n == c.nterms, MGMLMC_EINVAL, "estimate_trace_concurrent: one context per term");
+    std::vector<Ctx*> ctx_of(n);
+    for (int t = 0; t < n; ++t) {
+        MG_REQUIRE(contexts[t], MGMLMC_EINVAL, "estimate_trace_concurrent: null context");
+        for (int k = 0; k < t; ++k)
+            MG_REQUIRE(contexts[k] != contexts[t], MGMLMC_EINVAL, "estimate_trace_concurrent: contexts must differ");
+        ctx_of[t] = &contexts[t]->c;
+    }
+    mlmc_loop(ctx_of, true, rel_tol, max_samples, seed, costs, out);
     API_END
 }
 

@@ -243,3 +243,29 @@ def test_concurrent_terms_on_separate_streams(pkg, c1):
     finally:
         for ctx in ctxs:
             ctx.close()
+
+
+def test_concurrent_mlmc_loop_matches_one_context(pkg, c1):
+    # the MLMC loop with each term drawn on its own context and stream: with fixed
+    # costs the allocation is deterministic, so every round, sample count and the
+    # estimate equal those of the one-context loop
+    import torch
+    w, theta, sv, H, defl = c1
+    ctxs = []
+    for s in [torch.cuda.current_stream(), torch.cuda.Stream()]:
+        with torch.cuda.stream(s):
+            ctx = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        ctxs.append(ctx)
+    try:
+        res = pkg.estimate_trace_concurrent(ctxs, 2e-2, 200000, 31, [1.0, 0.1])
+        one = ctxs[0].estimate_trace(2e-2, 200000, 31, [1.0, 0.1])
+        assert res["converged"] == 1 and one["converged"] == 1
+        assert res["rounds"] == one["rounds"]
+        assert [t["nsamples"] for t in res["terms"]] == [t["nsamples"] for t in one["terms"]]
+        assert abs(res["trace"] - one["trace"]) <= 1e-12 * abs(one["trace"])
+        exact = np.trace(np.linalg.inv(H.D[0].toarray()))
+        assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
+    finally:
+        for ctx in ctxs:
+            ctx.close()
