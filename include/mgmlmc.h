@@ -111,6 +111,16 @@ void mgmlmc_default_options(mgmlmc_options* opt);
 int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream,
                   mgmlmc_alloc_fn alloc, mgmlmc_free_fn free_fn, void* alloc_user);
 
+/* A second context holding device copies of src's state: gauge field, mass,
+ * options, hierarchy (test vectors, prolongators, coarse operators, smoother and
+ * coarsest data), term list and deflations (Sects. 2, 3.1) — none of the setup
+ * is computed again.  It runs on cuda_stream with its own work space and
+ * statistics; the intended use is one context per term for
+ * mgmlmc_estimate_concurrent / mgmlmc_estimate_trace_concurrent.  src's stream is
+ * synchronised first.  On failure *out is NULL and src holds the message. */
+int mgmlmc_create_copy(mgmlmc_ctx** out, mgmlmc_ctx* src, void* cuda_stream, mgmlmc_alloc_fn alloc,
+                       mgmlmc_free_fn free_fn, void* alloc_user);
+
 /* Release every device allocation of the context, then the context. */
 void mgmlmc_destroy(mgmlmc_ctx* ctx);
 

@@ -62,6 +62,7 @@ _I = C.POINTER(C.c_int)
 SIGNATURES = [
     ("mgmlmc_default_options", None, [C.POINTER(Options)]),
     ("mgmlmc_create", C.c_int, [C.POINTER(_P), C.POINTER(Options), _P, ALLOC_FN, FREE_FN, _P]),
+    ("mgmlmc_create_copy", C.c_int, [C.POINTER(_P), _P, C.c_void_p, ALLOC_FN, FREE_FN, C.c_void_p]),
     ("mgmlmc_destroy", None, [_P]),
     ("mgmlmc_last_error", C.c_char_p, [_P]),
     ("mgmlmc_set_gauge", C.c_int, [_P, C.c_int, C.c_int, _D]),
@@ -202,12 +203,15 @@ class Context:
     shape (nvec, n_l).
     """
 
-    def __init__(self, options: Options | None = None, torch_memory: bool = True, **kw):
+    def __init__(self, options: Options | None = None, torch_memory: bool = True, copy_of: "Context" = None, **kw):
+        """copy_of: build this context as a device copy of another one's state
+        (mgmlmc_create_copy), on the stream current now."""
         import torch
         if not torch.cuda.is_available():
             raise MgmlmcError(-5, "a CUDA device is required (this library has no CPU path)")
         self.lib = load()
-        self.options = options if options is not None else default_options(**kw)
+        self.options = copy_of.options if copy_of is not None else (
+            options if options is not None else default_options(**kw))
         self._mem = {}
         # the context works on the stream current at creation; its device memory is
         # taken on that stream too, so that a block the library gives back is reused
@@ -231,8 +235,13 @@ class Context:
         else:
             self._alloc_cb, self._free_cb = ALLOC_FN(), FREE_FN()
         h = C.c_void_p()
-        self._check(self.lib.mgmlmc_create(C.byref(h), C.byref(self.options), stream, self._alloc_cb,
-                                           self._free_cb, None), h)
+        if copy_of is not None:
+            code = self.lib.mgmlmc_create_copy(C.byref(h), copy_of.h, stream, self._alloc_cb, self._free_cb, None)
+            if code != 0:
+                copy_of._check(code)
+        else:
+            self._check(self.lib.mgmlmc_create(C.byref(h), C.byref(self.options), stream, self._alloc_cb,
+                                               self._free_cb, None), h)
         self.h = h
 
     # ---------------------------------------------------------------- plumbing

@@ -239,6 +239,26 @@ int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream
     return MGMLMC_OK;
 }
 
+int mgmlmc_create_copy(mgmlmc_ctx** out, mgmlmc_ctx* src, void* cuda_stream, mgmlmc_alloc_fn alloc,
+                       mgmlmc_free_fn free_fn, void* alloc_user) {
+    if (!out || !src) return MGMLMC_EINVAL;
+    *out = nullptr;
+    mgmlmc_ctx* h = nullptr;
+    const int rc = mgmlmc_create(&h, &src->c.opt, cuda_stream, alloc, free_fn, alloc_user);
+    if (rc != MGMLMC_OK) return rc;
+    Ctx& c = h->c;
+    try {
+        mg::copy_state(c, src->c);
+    } catch (const Error& e) {
+        const int code = e.code;
+        src->c.err = std::string("create_copy: ") + e.what();
+        mgmlmc_destroy(h);
+        return code;
+    }
+    *out = h;
+    return MGMLMC_OK;
+}
+
 void mgmlmc_destroy(mgmlmc_ctx* h) {
     if (!h) return;
     h->c.release_all();

@@ -166,6 +166,8 @@ void approx_inverse(Ctx& c, int l, const double2* b, double2* x, int N);
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);
 // Throws MGMLMC_ETIMEOUT if a kernel with bounded waits recorded a timeout.
 void check_device_error(Ctx& c);
+// d receives device copies of s's gauge field, mass, hierarchy, terms and deflations.
+void copy_state(Ctx& d, Ctx& s);
 
 // ---- setup (setup.cu)
 void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const int* nvec, int setup_iters,

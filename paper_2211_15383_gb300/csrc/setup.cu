@@ -158,6 +158,81 @@ ProfScope::~ProfScope() {
 }
 
 // ------------------------------------------------------------------ gauge
+// ------------------------------------------------------------------ copy of a context
+template <typename T>
+static T* dup(Ctx& d, const T* p, size_t count) {
+    if (!p) return nullptr;
+    T* q = d.alloc_n<T>(count);
+    MG_CUDA(cudaMemcpyAsync(q, p, count * sizeof(T), cudaMemcpyDeviceToDevice, d.stream));
+    return q;
+}
+
+static void dup_deflation(Ctx& d, const Ctx& s, const Deflation& from, Deflation& to) {
+    to = Deflation();
+    if (!from.Lv) return;
+    const size_t n = (size_t)s.lev[from.fine].n, k = (size_t)from.k;
+    to.k = from.k;
+    to.fine = from.fine;
+    to.coarse = from.coarse;
+    to.inexact = from.inexact;
+    to.lambda = from.lambda;
+    to.tau_re = from.tau_re;
+    to.tau_im = from.tau_im;
+    to.Lv = dup(d, from.Lv, n * k);
+    to.Rv = dup(d, from.Rv, n * k);
+    to.a = dup(d, from.a, k);
+}
+
+// d (fresh, on its own stream) receives s's gauge field, mass, hierarchy, term list
+// and deflations: device copies of every array, no setup computation repeated.
+void copy_state(Ctx& d, Ctx& s) {
+    MG_CUDA(cudaStreamSynchronize(s.stream));
+    d.Lx = s.Lx;
+    d.Lt = s.Lt;
+    d.have_gauge = s.have_gauge;
+    d.have_mass = s.have_mass;
+    d.have_hier = s.have_hier;
+    d.m0 = s.m0;
+    const size_t V = (size_t)s.Lx * s.Lt;
+    d.U64 = dup(d, s.U64, 2 * V);
+    d.U32 = dup(d, s.U32, 2 * V);
+    d.L = s.L;
+    for (int l = 0; l < s.L; ++l) {
+        const Level& b = s.lev[l];
+        Level& a = d.lev[l];
+        a = Level();
+        a.lx = b.lx;
+        a.lt = b.lt;
+        a.d = b.d;
+        a.nsites = b.nsites;
+        a.n = b.n;
+        a.ax = b.ax;
+        a.at = b.at;
+        a.nvec = b.nvec;
+        const size_t nb = (size_t)b.nsites * b.d * b.d;
+        a.A64 = dup(d, b.A64, 5 * nb);
+        a.A32 = dup(d, b.A32, 5 * nb);
+        a.Minv64 = dup(d, b.Minv64, nb);
+        a.Minv32 = dup(d, b.Minv32, nb);
+        a.Ahat64 = dup(d, b.Ahat64, 5 * nb);
+        a.Ahat32 = dup(d, b.Ahat32, 5 * nb);
+        a.Ahat16 = dup(d, b.Ahat16, 5 * nb * 4);
+        a.A16 = dup(d, b.A16, 5 * nb * 4);
+        a.P64 = dup(d, b.P64, (size_t)b.n * b.nvec);
+        a.P32 = dup(d, b.P32, (size_t)b.n * b.nvec);
+        a.tv = dup(d, b.tv, (size_t)b.n * b.nvec);
+        a.Dinv64 = dup(d, b.Dinv64, (size_t)b.n * b.n);
+        a.Dinv32 = dup(d, b.Dinv32, (size_t)b.n * b.n);
+        a.Dinv16 = dup(d, b.Dinv16, (size_t)b.n * 2 * b.n);
+    }
+    d.nterms = s.nterms;
+    for (int t = 0; t <= MGMLMC_MAX_LEVELS; ++t) d.term_level[t] = s.term_level[t];
+    d.skip = s.skip;
+    dup_deflation(d, s, s.defl, d.defl);
+    for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) dup_deflation(d, s, s.ddefl[l], d.ddefl[l]);
+    MG_CUDA(cudaStreamSynchronize(d.stream));
+}
+
 void upload_links(Ctx& c, const double* theta) {
     const int V = c.Lx * c.Lt;
     std::vector<double2> U((size_t)2 * V);

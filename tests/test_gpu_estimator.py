@@ -213,26 +213,27 @@ def test_three_levels_with_wide_coarse_blocks(pkg, prec):
 
 def test_concurrent_terms_on_separate_streams(pkg, c1):
     # the two terms of the 16x16 workload at once, each on its own context and CUDA
-    # stream (one entry with device noise, one with caller probes): the same samples
-    # as the one-term calls, and as the oracle's
+    # stream (one entry with device noise, one with caller probes): the second context
+    # is a device copy of the first (mgmlmc_create_copy), so every sample must equal the
+    # first context's bit for bit, and the oracle's within the bar
     import torch
     w, theta, sv, H, defl = c1
     solvers = oest.DirectSolvers(H)
-    streams = [torch.cuda.Stream() for _ in range(2)]
-    ctxs = []
-    for s in streams:
-        with torch.cuda.stream(s):
-            ctx = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
-        ctx.compute_deflation(w.k, 1e-10, 500)
-        ctxs.append(ctx)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        src = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
+    src.compute_deflation(w.k, 1e-10, 500)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        cpy = pkg.Context(copy_of=src)
+    assert cpy.get_deflation(w.k, 2)[-1] == src.get_deflation(w.k, 2)[-1]     # tau
+    ctxs = [src, cpy]
     try:
         n1 = H.D[-1].shape[0]
         probes = np.where(inputs.uniform(5, 1, 48 * n1).reshape(48, n1) < 0.5, 1, -1).astype(np.int8)
         for rep in range(2):                                     # twice in a row
             outs, stats = pkg.estimate_concurrent(ctxs, [0, 1], 16, 48, w.noise_seed, probes=[None, probes])
             assert [s["nsamples"] for s in stats] == [48, 48]
-            seq0, _ = ctxs[0].estimate_level(0, 16, 48, w.noise_seed)
-            seq1, _ = ctxs[1].estimate_level_probes(1, probes)
+            seq0, _ = src.estimate_level(0, 16, 48, w.noise_seed)
+            seq1, _ = src.estimate_level_probes(1, probes)
             assert np.array_equal(outs[0], seq0) and np.array_equal(outs[1], seq1)
         ref0 = oest.noise_samples(H, (1, 2), w.noise_seed, 16, 48, solvers)
         ref1 = oest.term_samples(H, (2, None), probes.astype(float), solvers, defl)
@@ -251,12 +252,11 @@ def test_concurrent_mlmc_loop_matches_one_context(pkg, c1):
     # estimate equal those of the one-context loop
     import torch
     w, theta, sv, H, defl = c1
-    ctxs = []
-    for s in [torch.cuda.current_stream(), torch.cuda.Stream()]:
-        with torch.cuda.stream(s):
-            ctx = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
-        ctx.compute_deflation(w.k, 1e-10, 500)
-        ctxs.append(ctx)
+    src = make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16)
+    src.compute_deflation(w.k, 1e-10, 500)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        cpy = pkg.Context(copy_of=src)
+    ctxs = [src, cpy]
     try:
         res = pkg.estimate_trace_concurrent(ctxs, 2e-2, 200000, 31, [1.0, 0.1])
         one = ctxs[0].estimate_trace(2e-2, 200000, 31, [1.0, 0.1])
