@@ -328,6 +328,10 @@ def gpu_arm(args, rank, ws, local):
                     ctx.estimate_level_probes(t, probes[k - first][t], out=outs[t])
 
     steps(0, W)                                                             # warm-up
+    if len(ctxs) > 1:
+        # the comparison below runs every term on the first context, which the concurrent
+        # steps only ran on term 0: warm its other terms too (workspaces, iteration counts)
+        run_steps(ctx, w, nterms, 0, 1, seed)
     # timed region: no event profiling (it costs host time per launch); the launch
     # counter is reset so that the kernels launched inside it are counted
     ctx.profile(False, reset=True)
