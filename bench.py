@@ -14,7 +14,9 @@ mgmlmc_estimate_concurrent; the one-context sequential rate is reported too);
 the all-FP64 path and the plain FP64 single-rhs path are measured beside it, with the
 per-sample difference of the two batched runs on the same noise.  The line
 also carries the time to tr(D^-1) at relative error 1e-4 (the paper's
-tolerance) and the fine stencil's HBM bandwidth.
+tolerance), the fine stencil's HBM bandwidth, and a serving run: whole trace
+requests of mixed lattice sizes through the request server, all at once and
+then as a Poisson stream, with p50/p99 time to trace.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -77,6 +79,12 @@ def parse():
                     help="mark the timed regions with NVTX ranges timed_f64 / timed_mixed / timed_e2e")
     ap.add_argument("--single-rhs-samples", type=int, default=2,
                     help="samples per term of the plain FP64 single-rhs comparison (0 = skip)")
+    ap.add_argument("--serving-requests", type=int, default=12,
+                    help="requests per phase of the serving run (0 = skip; 1 GPU only)")
+    ap.add_argument("--serving-slots", type=int, default=4, help="requests admitted at once by the server")
+    ap.add_argument("--serving-load", type=float, default=0.8,
+                    help="Poisson arrival rate of the second phase, as a fraction of the saturated rate")
+    ap.add_argument("--serving-tol", type=float, default=1e-3, help="relative error asked by each request")
     return ap.parse_args()
 
 
@@ -478,6 +486,12 @@ def gpu_arm(args, rank, ws, local):
             sctx.close()
     else:
         ctx.close()
+    if args.serving_requests > 0 and ws == 1:
+        torch.cuda.empty_cache()
+        try:
+            out["serving"] = serving_run(pkg, args)
+        except Exception as e:       # the headline line stands without it
+            out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     fine = {k: v for k, v in report.items() if k.startswith("D1.f32")}
     if fine:
         v = fine["D1.f32"]
@@ -487,6 +501,100 @@ def gpu_arm(args, rank, ws, local):
                               "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
                               "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"]}
     return out, w
+
+
+# ----------------------------------------------------------------------------- serving
+def serving_run(pkg, args):
+    """Trace requests of mixed lattices (64^2, 128^2), couplings (beta 3, 5) and masses
+    through the request server: first all at once (the saturated rate), then arriving
+    as a Poisson stream at args.serving_load x that rate.  Each request is a whole
+    problem (gauge field, 3-level hierarchy, deflation, MLMC loop to args.serving_tol);
+    its time to trace runs from submission to result.  Fixed per-term costs (level
+    sizes) make every request's result independent of the load."""
+    n = args.serving_requests
+    rng = np.random.default_rng(20221115)
+    t0 = time.time()
+    fields, starts = {}, {}
+    for L in (64, 128):
+        for beta in (3.0, 5.0):
+            fields[(L, beta)] = inputs.metropolis_u1(L, L, beta, 200, 5000 + L + int(10 * beta))
+        dims = [(L, L, 2), (L // 4, L // 4, 16)]
+        starts[L] = [inputs.start_vectors(7000 + L, i + 1, lx * lt * d, 8) for i, (lx, lt, d) in enumerate(dims)]
+    gen_s = time.time() - t0
+    masses = {3.0: (-0.09, -0.04), 5.0: (-0.03, 0.02)}
+
+    def make(i):
+        L = int(rng.choice([64, 128]))
+        beta = float(rng.choice([3.0, 5.0]))
+        m0 = float(rng.choice(masses[beta]))
+        n0, n1, n2 = 2 * L * L, L * L, L * L // 4
+        req = pkg.make_request(fields[(L, beta)], m0, ((4, 4), (2, 2)), (8, 8), starts[L], args.serving_tol,
+                               100 + i, k=32 if L == 64 else 64, setup_iters=4,
+                               costs=[(n0 + n1) / n0, (n1 + n2) / n0, n2 / n0], mg_precision=args.precision)
+        return L, req
+
+    deadline = time.time() + 300.0
+
+    def collect(srv, ids):
+        res = []
+        for i in ids:
+            r = srv.wait(i, max(1.0, deadline - time.time()))
+            if r is None:
+                raise TimeoutError("serving run exceeded 300 s")
+            res.append(r)
+        return res
+
+    def summary(rs, span):
+        ok = [r for r in rs if r["status"] == 0]
+        tt = np.array([r["total_s"] for r in ok]) if ok else np.zeros(1)
+        qq = np.array([r["queued_s"] for r in ok]) if ok else np.zeros(1)
+        smp = sum(sum(t["nsamples"] for t in r["result"]["terms"]) for r in ok)
+        return {"span_s": span, "requests_per_s": len(ok) / span, "samples_per_s": smp / span,
+                "p50_time_to_trace_s": float(np.percentile(tt, 50)),
+                "p99_time_to_trace_s": float(np.percentile(tt, 99)),
+                "p50_queue_s": float(np.percentile(qq, 50)), "p99_queue_s": float(np.percentile(qq, 99)),
+                "mean_setup_s": float(np.mean([r["setup_s"] for r in ok])) if ok else 0.0,
+                "mean_estimate_s": float(np.mean([r["estimate_s"] for r in ok])) if ok else 0.0}
+
+    with pkg.Server(max_active=args.serving_slots) as srv:
+        burst = [make(i) for i in range(n)]
+        t0 = time.perf_counter()
+        res1 = collect(srv, [srv.submit(r) for _, r in burst])
+        span1 = time.perf_counter() - t0
+        lam = args.serving_load * n / span1
+        stream = [make(n + i) for i in range(n)]
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n))
+        t0 = time.perf_counter()
+        ids = []
+        for a, (_, r) in zip(arrivals, stream):
+            wait = a - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(srv.submit(r))
+        res2 = collect(srv, ids)
+        span2 = time.perf_counter() - t0
+        st = srv.stats()
+    allr = res1 + res2
+    sizes = [L for L, _ in burst + stream]
+    by_L = {}
+    for L in (64, 128):
+        rs = [r for r, l in zip(res2, sizes[n:]) if l == L and r["status"] == 0]
+        peaks = [r["peak_bytes"] for r, l in zip(allr, sizes) if l == L and r["status"] == 0]
+        by_L[f"{L}x{L}"] = {"requests": sum(1 for l in sizes if l == L),
+                            "p50_time_to_trace_s_poisson": float(np.median([r["total_s"] for r in rs])) if rs else None,
+                            "device_peak_gb": max(peaks) / 1e9 if peaks else None}
+    return {"requests_per_phase": n, "slots": args.serving_slots, "rel_tol": args.serving_tol,
+            "mix": "lattices 64^2 and 128^2, beta 3 (m0 -0.09, -0.04) and 5 (m0 -0.03, 0.02), 3 levels "
+                   "(4x4 then 2x2, 8 test vectors), k = 32 / 64, mg_precision %d" % args.precision,
+            "saturated": summary(res1, span1),
+            "poisson": dict(summary(res2, span2), load=args.serving_load, arrival_rate_per_s=lam),
+            "by_lattice": by_L,
+            "all_converged": all(r["status"] == 0 and r["result"]["converged"] == 1 for r in allr),
+            "failures": [r["error"] for r in allr if r["status"] != 0],
+            "retries": sum(r["retries"] for r in allr),
+            "server": {"max_active_seen": st["max_active_seen"], "budget_gb": st["budget"] / 1e9,
+                       "max_reserved_gb": st["max_reserved"] / 1e9},
+            "inputs_s": gen_s}
 
 
 # ----------------------------------------------------------------------------- CPU (oracle)

@@ -42,7 +42,9 @@ typedef enum {
     MGMLMC_ECUDA = -5,           /* CUDA runtime error                                 */
     MGMLMC_ENOTIMPL = -6,        /* combination not implemented                        */
     MGMLMC_ENAN = -7,            /* NaN/Inf met in the data                            */
-    MGMLMC_ESTATE = -8           /* call out of order (e.g. estimate before hierarchy) */
+    MGMLMC_ESTATE = -8,          /* call out of order (e.g. estimate before hierarchy) */
+    MGMLMC_ECANCELLED = -9,      /* a served request was cancelled                     */
+    MGMLMC_PENDING = 1           /* mgmlmc_poll / mgmlmc_wait: request not finished    */
 } mgmlmc_status;
 
 typedef struct mgmlmc_ctx mgmlmc_ctx;
@@ -326,6 +328,127 @@ int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* ctx, int nrhs, const float* x, flo
 
 /* Level geometry: sites per direction, dof per site, n_l. */
 int mgmlmc_level_info(const mgmlmc_ctx* ctx, int level, int* lx, int* lt, int* d, int64_t* n);
+
+/* Device bytes the context holds now (*live) and has held at most (*peak) through
+ * its allocator (either may be NULL).  Pinned host scratch is not counted. */
+int mgmlmc_memory(const mgmlmc_ctx* ctx, size_t* live, size_t* peak);
+
+/* ---- Serving: trace requests admitted continuously on one GPU ----------------
+ * A server takes whole trace problems (gauge field, mass, hierarchy, deflation,
+ * target relative error: the estimation of tr(D^{-1}) of Sect. 3.2 with the
+ * deflated coarsest term of Sect. 2, one request each) and runs them on the current
+ * CUDA device.  A request is admitted when a slot is free and its estimated device
+ * footprint fits in the server's HBM budget beside the requests already admitted;
+ * each admitted request gets its own context (hierarchy, deflation space and Krylov
+ * work space stay on the device until it finishes) and CUDA stream, and its work
+ * overlaps on the device with that of the other admitted requests.  Inside a
+ * request all samples of a term in one round are solved as multi-rhs blocks of
+ * up to opt.max_block_rhs right-hand sides.  Queued requests are admitted in
+ * arrival order; a request that does not fit may be overtaken by later ones that
+ * do, at most max_bypass times, after which nothing behind it is admitted before
+ * it.  Device memory of the requests comes from a stream-ordered pool owned by the
+ * server (no device-wide synchronisation when a request frees its memory).
+ * All server calls are thread safe.  Results do not depend on what else runs:
+ * with fixed costs a request's rounds, sample counts and estimate are those it
+ * gets alone. */
+typedef struct mgmlmc_server mgmlmc_server;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes the admitted requests may reserve together
+                             (0: 3/4 of the free device memory at creation)    [0]  */
+    int max_active;       /* most requests admitted at once (1..64)            [4]  */
+    int max_bypass;       /* times a queued request may be overtaken           [4]  */
+} mgmlmc_server_options;
+
+typedef struct {
+    int Lx, Lt;           /* lattice (as mgmlmc_set_gauge)                          */
+    const double* theta;  /* host link angles [Lt][Lx][2]; copied by mgmlmc_submit  */
+    double m0;            /* Wilson mass                                            */
+    int nlevels;          /* multigrid levels (1..MGMLMC_MAX_LEVELS)                */
+    int agg_x[MGMLMC_MAX_LEVELS], agg_t[MGMLMC_MAX_LEVELS], nvec[MGMLMC_MAX_LEVELS];
+                          /* aggregates and test vectors per spin of levels
+                             1..nlevels-1 (as mgmlmc_set_hierarchy)                 */
+    const double* start_vectors[MGMLMC_MAX_LEVELS];
+                          /* host [nvec][n_l] complex start vectors of levels
+                             1..nlevels-1 (as mgmlmc_set_hierarchy); copied          */
+    int setup_iters;      /* inverse-iteration steps of the hierarchy setup         */
+    double setup_tol;     /* solve tolerance of those steps                          */
+    int k;                /* smallest triplets of the coarsest operator deflated (0: none) */
+    double defl_tol;      /* eigensolver tolerance (as mgmlmc_compute_deflation)     */
+    int defl_max_iters;
+    double rel_tol;       /* target relative error of the estimate (> 0)             */
+    int64_t max_samples;  /* cap on samples over all terms                           */
+    uint64_t seed;        /* noise seed of the estimate                              */
+    double costs[MGMLMC_MAX_LEVELS]; /* per-sample cost of each term for the sample
+                             allocation; all zero: measured device time (then the
+                             allocation depends on the load)                         */
+    mgmlmc_options opt;   /* context options (mgmlmc_default_options for defaults)  */
+} mgmlmc_request;
+
+typedef struct {
+    int status;           /* MGMLMC_OK, the failing call's status, or MGMLMC_ECANCELLED */
+    mgmlmc_trace_result result;
+    double queued_s;      /* submission -> admission                                 */
+    double setup_s;       /* admission -> hierarchy and deflation ready              */
+    double estimate_s;    /* the MLMC loop                                           */
+    double total_s;       /* submission -> result: the time to trace                 */
+    size_t reserved_bytes;/* footprint reserved at admission                         */
+    size_t peak_bytes;    /* device bytes the request's context held at most         */
+    int retries;          /* re-admissions after a refused device allocation         */
+    char error[160];      /* text of the failure ("" if none)                        */
+} mgmlmc_request_result;
+
+typedef struct {
+    int queued, active;   /* requests waiting / admitted now                        */
+    int64_t completed;    /* requests finished (any status) since creation           */
+    int max_active_seen;  /* most requests admitted at once so far                   */
+    size_t budget;        /* the HBM budget in force                                 */
+    size_t reserved;      /* bytes reserved by the admitted requests now             */
+    size_t max_reserved;  /* most bytes reserved at once so far (<= budget)          */
+} mgmlmc_server_stats;
+
+/* Upper estimate of the device bytes a request's context holds at most: the
+ * operators of every level, the dense coarsest inverse in each precision used, the
+ * deflation space and eigensolver blocks, and the Krylov, refinement, V-cycle and
+ * estimator blocks of opt.max_block_rhs right-hand sides.  MGMLMC_EINVAL if the
+ * lattice or hierarchy is malformed (as mgmlmc_set_gauge / mgmlmc_set_hierarchy). */
+int mgmlmc_request_footprint(const mgmlmc_request* req, size_t* bytes);
+
+/* Create a server on the current CUDA device (opt NULL: defaults).  MGMLMC_ECUDA
+ * without a device; MGMLMC_EINVAL for a bad option. */
+int mgmlmc_server_create(mgmlmc_server** out, const mgmlmc_server_options* opt);
+
+/* Cancel queued requests, stop running ones at their next check, wait for them,
+ * release the pool and the server.  Results not yet polled are lost. */
+void mgmlmc_server_destroy(mgmlmc_server* srv);
+
+/* Queue a request (the struct, theta and the start vectors are copied; the caller
+ * may free them on return).  *id identifies it for poll, wait and cancel.  The footprint reserved
+ * for it is mgmlmc_request_footprint while no request of the same shape (lattice,
+ * hierarchy, k, precision, block width, restart length) has finished, then 1.1 x
+ * the largest device peak of those that have.  MGMLMC_EINVAL for a malformed
+ * request, MGMLMC_ENOMEM if that footprint exceeds the whole budget. */
+int mgmlmc_submit(mgmlmc_server* srv, const mgmlmc_request* req, uint64_t* id);
+
+/* MGMLMC_OK and *out filled once the request has finished (its own outcome is
+ * out->status); the id is released then.  MGMLMC_PENDING while it is queued or
+ * running, MGMLMC_EINVAL for an unknown id. */
+int mgmlmc_poll(mgmlmc_server* srv, uint64_t id, mgmlmc_request_result* out);
+
+/* mgmlmc_poll after waiting at most timeout_s seconds (< 0: no limit) for the
+ * request to finish. */
+int mgmlmc_wait(mgmlmc_server* srv, uint64_t id, double timeout_s, mgmlmc_request_result* out);
+
+/* Cancel a request: a queued one finishes at once, a running one at its next check
+ * (between setup steps and between rounds of the MLMC loop), with status
+ * MGMLMC_ECANCELLED.  MGMLMC_EINVAL for an unknown or already finished id. */
+int mgmlmc_cancel(mgmlmc_server* srv, uint64_t id);
+
+/* Counters of the server (queue, admitted requests, reserved bytes). */
+int mgmlmc_get_server_stats(mgmlmc_server* srv, mgmlmc_server_stats* out);
+
+/* Text of the last server call that failed on the calling thread ("" if none). */
+const char* mgmlmc_server_last_error(const mgmlmc_server* srv);
 
 #ifdef __cplusplus
 }

@@ -2,8 +2,8 @@
 the 2D Wilson-Schwinger operator (Frommer & Ramirez-Hidalgo, Lattice 2022).
 
 The computation lives in ``libmgmlmc.so`` (CUDA kernels behind the C ABI of
-``include/mgmlmc.h``); ``Context`` is its thin Python binding.
+``include/mgmlmc.h``); ``Context`` and ``Server`` are its thin Python binding.
 """
-from ._lib import (Context, MgmlmcError, Options, default_options, estimate_concurrent,
-                   estimate_trace_concurrent, fma_peak, load, LIB_PATH,  # noqa: F401
-                   OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C, OP_SMOOTH)
+from ._lib import (Context, MgmlmcError, Options, Server, default_options, estimate_concurrent,  # noqa: F401
+                   estimate_trace_concurrent, fma_peak, load, make_request, request_footprint, LIB_PATH,
+                   ECANCELLED, PENDING, OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C, OP_SMOOTH)

@@ -21,7 +21,8 @@ OP_D, OP_PH, OP_P, OP_G5, OP_PREC, OP_DINV_C, OP_SMOOTH = range(7)
 
 STATUS = {0: "MGMLMC_OK", -1: "MGMLMC_EINVAL", -2: "MGMLMC_ENOMEM", -3: "MGMLMC_ENOTCONVERGED",
           -4: "MGMLMC_ETIMEOUT", -5: "MGMLMC_ECUDA", -6: "MGMLMC_ENOTIMPL", -7: "MGMLMC_ENAN",
-          -8: "MGMLMC_ESTATE"}
+          -8: "MGMLMC_ESTATE", -9: "MGMLMC_ECANCELLED", 1: "MGMLMC_PENDING"}
+ECANCELLED, PENDING = -9, 1
 
 
 class MgmlmcError(RuntimeError):
@@ -49,6 +50,30 @@ class TraceResult(C.Structure):
     _fields_ = [("trace_re", C.c_double), ("trace_im", C.c_double), ("rel_err", C.c_double),
                 ("deflated_part", C.c_double), ("nterms", C.c_int), ("converged", C.c_int),
                 ("rounds", C.c_int), ("term", LevelStats * MAX_LEVELS)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("max_bypass", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Lt", C.c_int), ("theta", C.POINTER(C.c_double)), ("m0", C.c_double),
+                ("nlevels", C.c_int), ("agg_x", C.c_int * MAX_LEVELS), ("agg_t", C.c_int * MAX_LEVELS),
+                ("nvec", C.c_int * MAX_LEVELS), ("start_vectors", C.POINTER(C.c_double) * MAX_LEVELS),
+                ("setup_iters", C.c_int), ("setup_tol", C.c_double), ("k", C.c_int), ("defl_tol", C.c_double),
+                ("defl_max_iters", C.c_int), ("rel_tol", C.c_double), ("max_samples", C.c_int64),
+                ("seed", C.c_uint64), ("costs", C.c_double * MAX_LEVELS), ("opt", Options)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("result", TraceResult), ("queued_s", C.c_double), ("setup_s", C.c_double),
+                ("estimate_s", C.c_double), ("total_s", C.c_double), ("reserved_bytes", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("retries", C.c_int), ("error", C.c_char * 160)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("completed", C.c_int64), ("max_active_seen", C.c_int),
+                ("budget", C.c_size_t), ("reserved", C.c_size_t), ("max_reserved", C.c_size_t)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -96,6 +121,16 @@ SIGNATURES = [
     ("mgmlmc_profile_report", C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("mgmlmc_fma_peak", C.c_int, [C.c_int, _D]),
     ("mgmlmc_coarse_inverse_noalloc", C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("mgmlmc_memory", C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    ("mgmlmc_request_footprint", C.c_int, [C.POINTER(Request), C.POINTER(C.c_size_t)]),
+    ("mgmlmc_server_create", C.c_int, [C.POINTER(_P), C.POINTER(ServerOptions)]),
+    ("mgmlmc_server_destroy", None, [_P]),
+    ("mgmlmc_submit", C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    ("mgmlmc_poll", C.c_int, [_P, C.c_uint64, C.POINTER(RequestResult)]),
+    ("mgmlmc_wait", C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(RequestResult)]),
+    ("mgmlmc_cancel", C.c_int, [_P, C.c_uint64]),
+    ("mgmlmc_get_server_stats", C.c_int, [_P, C.POINTER(ServerStats)]),
+    ("mgmlmc_server_last_error", C.c_char_p, [_P]),
 ]
 
 _lib = None
@@ -417,8 +452,130 @@ class Context:
         self._check(self.lib.mgmlmc_coarse_inverse_noalloc(self.h, int(nrhs), C.c_void_p(x_ptr), C.c_void_p(y_ptr),
                                                            C.c_void_p(stream)))
 
+    def memory(self):
+        """(live, peak) device bytes held through the context's allocator."""
+        live, peak = C.c_size_t(), C.c_size_t()
+        self._check(self.lib.mgmlmc_memory(self.h, C.byref(live), C.byref(peak)))
+        return live.value, peak.value
+
     def get_test_vectors(self, level: int, nvec: int):
         n = self.level_info(level)[3]
         v = np.zeros((nvec, n), np.complex128)
         self._check(self.lib.mgmlmc_get_test_vectors(self.h, level, v.ctypes.data_as(_D)))
         return v
+
+
+# ------------------------------------------------------------------------- serving
+def make_request(theta, m0: float, agg, nvec, start_vectors, rel_tol: float, seed: int, k: int = 0,
+                 setup_iters: int = 4, setup_tol: float = 1e-12, defl_tol: float = 1e-9, defl_max_iters: int = 400,
+                 max_samples: int = 1 << 40, costs=None, options: Options | None = None, **kw):
+    """A trace request (mgmlmc_request) for Server.submit.  theta [Lt][Lx][2], agg a list
+    of (ax, at) per coarse level, start_vectors one complex array (nvec, n_l) per coarse
+    level; costs: fixed per-sample costs of the terms (None: measured device time).
+    The arrays are kept alive on the returned object until it is submitted."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    Lt, Lx, two = th.shape
+    assert two == 2
+    r = Request()
+    r.Lx, r.Lt, r.m0 = Lx, Lt, float(m0)
+    r.theta = th.ctypes.data_as(_D)
+    r.nlevels = len(agg) + 1
+    keep = [th]
+    for l, (a, nv, sv) in enumerate(zip(agg, nvec, start_vectors)):
+        r.agg_x[l], r.agg_t[l], r.nvec[l] = int(a[0]), int(a[1]), int(nv)
+        v = _cplx(sv)
+        keep.append(v)
+        r.start_vectors[l] = v.ctypes.data_as(_D)
+    r.setup_iters, r.setup_tol = int(setup_iters), float(setup_tol)
+    r.k, r.defl_tol, r.defl_max_iters = int(k), float(defl_tol), int(defl_max_iters)
+    r.rel_tol, r.max_samples, r.seed = float(rel_tol), int(max_samples), int(seed)
+    for t, c in enumerate(costs or []):
+        r.costs[t] = float(c)
+    r.opt = options if options is not None else default_options(**kw)
+    r._keep = keep
+    return r
+
+
+def request_footprint(req: Request) -> int:
+    """mgmlmc_request_footprint: upper estimate of the request's device bytes."""
+    lib = load()
+    b = C.c_size_t()
+    code = lib.mgmlmc_request_footprint(C.byref(req), C.byref(b))
+    if code != 0:
+        raise MgmlmcError(code, lib.mgmlmc_server_last_error(None).decode())
+    return b.value
+
+
+def _result_dict(rr: RequestResult):
+    d = {k: getattr(rr, k) for k, _ in RequestResult._fields_ if k not in ("result", "error")}
+    d["error"] = rr.error.decode()
+    d["result"] = _trace_dict(rr.result)
+    return d
+
+
+class Server:
+    """A request server on the current CUDA device (mgmlmc_server_*): trace requests are
+    admitted by footprint against an HBM budget and run on their own contexts and
+    streams, overlapping on the device."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 4, max_bypass: int = 4):
+        import torch
+        if not torch.cuda.is_available():
+            raise MgmlmcError(-5, "a CUDA device is required (this library has no CPU path)")
+        self.lib = load()
+        o = ServerOptions(int(hbm_budget), int(max_active), int(max_bypass))
+        h = C.c_void_p()
+        self._check(self.lib.mgmlmc_server_create(C.byref(h), C.byref(o)))
+        self.h = h
+
+    def _check(self, code):
+        if code != 0:
+            raise MgmlmcError(code, self.lib.mgmlmc_server_last_error(None).decode())
+
+    def submit(self, req: Request) -> int:
+        i = C.c_uint64()
+        self._check(self.lib.mgmlmc_submit(self.h, C.byref(req), C.byref(i)))
+        return i.value
+
+    def poll(self, rid: int):
+        """The result dict once finished, else None."""
+        rr = RequestResult()
+        code = self.lib.mgmlmc_poll(self.h, C.c_uint64(rid), C.byref(rr))
+        if code == PENDING:
+            return None
+        self._check(code)
+        return _result_dict(rr)
+
+    def wait(self, rid: int, timeout: float = -1.0):
+        """The result dict, waiting at most timeout seconds (< 0: no limit); None on timeout."""
+        rr = RequestResult()
+        code = self.lib.mgmlmc_wait(self.h, C.c_uint64(rid), float(timeout), C.byref(rr))
+        if code == PENDING:
+            return None
+        self._check(code)
+        return _result_dict(rr)
+
+    def cancel(self, rid: int):
+        self._check(self.lib.mgmlmc_cancel(self.h, C.c_uint64(rid)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._check(self.lib.mgmlmc_get_server_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgmlmc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

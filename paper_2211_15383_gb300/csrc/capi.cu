@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <thread>
 #include <vector>
@@ -475,13 +476,18 @@ int mgmlmc_reset_stats(mgmlmc_ctx* h) {
     API_END
 }
 
-namespace {
+}  // extern "C"
+
+namespace mg {
 
 // The MLMC loop (Sect. 3.2 with the cited allocation rule): term t draws its samples
 // on ctx_of[t]; with `concurrent` the draws of one round run on one host thread per
 // term (the contexts are then distinct, each on its own stream).
 void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol, int64_t max_samples, uint64_t seed,
-               const double* costs, mgmlmc_trace_result* out) {
+               const double* costs, mgmlmc_trace_result* out, const std::atomic<bool>* cancel) {
+    auto check_cancel = [&] {
+        if (cancel && cancel->load()) throw Error(MGMLMC_ECANCELLED, "estimate_trace: cancelled");
+    };
     MG_REQUIRE(out && rel_tol > 0 && max_samples > 0, MGMLMC_EINVAL, "estimate_trace: bad argument");
     const int T = ctx_of[0]->nterms;
     for (Ctx* ct : ctx_of) {
@@ -546,6 +552,7 @@ void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol,
     }
     bool converged = false;
     for (;;) {
+        check_cancel();
         std::vector<double> N(T), V(T), C(T);
         est_re = tau_re;
         est_im = tau_im;
@@ -608,7 +615,11 @@ void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol,
     }
 }
 
-}  // namespace
+}  // namespace mg
+
+using mg::mlmc_loop;
+
+extern "C" {
 
 int mgmlmc_estimate_trace(mgmlmc_ctx* h, double rel_tol, int64_t max_samples, uint64_t seed, const double* costs,
                           mgmlmc_trace_result* out) {
@@ -754,6 +765,13 @@ int mgmlmc_profile_report(mgmlmc_ctx* h, char* buf, size_t cap, size_t* needed) 
         buf[m] = 0;
     }
     API_END
+}
+
+int mgmlmc_memory(const mgmlmc_ctx* h, size_t* live, size_t* peak) {
+    if (!h) return MGMLMC_EINVAL;
+    if (live) *live = h->c.live_bytes;
+    if (peak) *peak = h->c.peak_bytes;
+    return MGMLMC_OK;
 }
 
 int mgmlmc_level_info(const mgmlmc_ctx* h, int level, int* lx, int* lt, int* d, int64_t* n) {

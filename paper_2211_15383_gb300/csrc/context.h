@@ -2,8 +2,10 @@
 // deflation space, per-term statistics and a named work-space pool.
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
@@ -129,7 +131,8 @@ struct Ctx {
     // ---- memory
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     std::map<std::string, Buf> ws;
-    std::vector<void*> owned;
+    std::unordered_map<void*, size_t> owned;   // device allocations and their sizes
+    size_t live_bytes = 0, peak_bytes = 0;     // device bytes held now and at most
 
     void* dev_alloc(size_t bytes);
     void dev_free(void* p);
@@ -168,6 +171,11 @@ void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);
 void check_device_error(Ctx& c);
 // d receives device copies of s's gauge field, mass, hierarchy, terms and deflations.
 void copy_state(Ctx& d, Ctx& s);
+// The MLMC loop of mgmlmc_estimate_trace(_concurrent): term t draws its samples on
+// ctx_of[t] (one host thread per term with `concurrent`); when *cancel becomes true
+// the loop stops at its next round with MGMLMC_ECANCELLED.
+void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol, int64_t max_samples, uint64_t seed,
+               const double* costs, mgmlmc_trace_result* out, const std::atomic<bool>* cancel = nullptr);
 
 // ---- setup (setup.cu)
 void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const int* nvec, int setup_iters,

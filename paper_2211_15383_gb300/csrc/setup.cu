@@ -25,14 +25,17 @@ void* Ctx::dev_alloc(size_t bytes) {
             throw Error(MGMLMC_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         }
     }
-    owned.push_back(p);
+    owned[p] = bytes;
+    live_bytes += bytes;
+    peak_bytes = std::max(peak_bytes, live_bytes);
     return p;
 }
 
 void Ctx::dev_free(void* p) {
     if (!p) return;
-    auto it = std::find(owned.begin(), owned.end(), p);
+    auto it = owned.find(p);
     if (it == owned.end()) return;
+    live_bytes -= it->second;
     owned.erase(it);
     if (free_fn) free_fn(alloc_user, p);
     else cudaFree(p);
@@ -52,11 +55,12 @@ void* Ctx::scratch_bytes(const std::string& name, size_t bytes) {
 
 void Ctx::release_all() {
     if (stream) cudaStreamSynchronize(stream);
-    for (void* p : owned) {
-        if (free_fn) free_fn(alloc_user, p);
-        else cudaFree(p);
+    for (auto& kv : owned) {
+        if (free_fn) free_fn(alloc_user, kv.first);
+        else cudaFree(kv.first);
     }
     owned.clear();
+    live_bytes = 0;
     ws.clear();
     dev_err = nullptr;
     for (auto& L : lev) L = Level();
