@@ -165,19 +165,32 @@ void launch_gemm_hn(double2* Cm, const C* A, const C* B, long long n, int ka, in
 }
 
 // ---------------------------------------------------------------- Gauss-Jordan
-// In-place inversion with partial pivoting (Gauss-Jordan elimination written
-// out in its textbook in-place form): for each k pick the largest |A[i][k]|,
-// i >= k, swap it to row k, scale row k by 1/pivot (with A[k][k] = 1 first),
-// eliminate column k from every other row (with A[i][k] = 0 first); at the end
-// undo the row swaps as column swaps in reverse order.
+// In-place inversion with partial pivoting (Gauss-Jordan elimination in its
+// textbook in-place form: for each k pick the largest |A[i][k]|, i >= k, swap it to
+// row k, scale row k by 1/pivot with A[k][k] = 1 first, eliminate column k from every
+// other row with A[i][k] = 0 first; at the end undo the row swaps as column swaps in
+// reverse order), blocked by panels of GJPanel<C>::B columns S = [k0, k0 + kb).
+// The steps of a panel touch only its own columns; their product T is the identity
+// outside the columns S, and its columns S are what the panel columns hold after
+// those steps.  The other columns then take the panel's row swaps and
+// A[:, c] <- T A[:, c] = A[:, c] (rows S zeroed) + A[:, S] A[S, c], one complex GEMM
+// of depth kb, so the whole matrix is streamed once per panel instead of once per
+// column.
 struct GJWork {
     int* perm;       // n
     double2* fcol;   // n   column k before elimination
     int* status;     // 1 = zero pivot met
+    void* rows;      // B x n copy of the panel's pivot rows (type C)
 };
 
+template <typename C> struct GJPanel;
+template <> struct GJPanel<float2> { static constexpr int B = 32; };
+template <> struct GJPanel<double2> { static constexpr int B = 16; };
+
+// Step k of the panel [k0, k0 + kb): pivot search in column k (rows >= k), swap rows
+// k and p within the panel columns, scale the panel part of row k, save column k.
 template <typename C>
-__global__ void k_gj_pivot(C* A, int n, int k, GJWork w) {
+__global__ void __launch_bounds__(1024) k_gj_pivot(C* A, int n, int k, int k0, int kb, GJWork w) {
     __shared__ double best[1024];
     __shared__ int bidx[1024];
     double bv = -1.0;
@@ -206,43 +219,108 @@ __global__ void k_gj_pivot(C* A, int n, int k, GJWork w) {
         w.perm[k] = p;
         if (!(best[0] > 0.0)) *w.status = 1;
     }
-    // swap rows k and p
     if (p != k)
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int c = k0 + threadIdx.x; c < k0 + kb; c += blockDim.x) {
             const C t = A[(long long)k * n + c];
             A[(long long)k * n + c] = A[(long long)p * n + c];
             A[(long long)p * n + c] = t;
         }
     __syncthreads();
-    // scale row k: A[k][k] = 1, then row /= pivot
     C piv = A[(long long)k * n + k];
     if (!(best[0] > 0.0)) piv = mk((decltype(piv.x))1, (decltype(piv.x))0);
     const double2 pd = to_d(piv);
     const double den = pd.x * pd.x + pd.y * pd.y;
     const C inv = cvt<C>(make_double2(pd.x / den, -pd.y / den));
     __syncthreads();
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int c = k0 + threadIdx.x; c < k0 + kb; c += blockDim.x) {
         C v = (c == k) ? mk((decltype(piv.x))1, (decltype(piv.x))0) : A[(long long)k * n + c];
         A[(long long)k * n + c] = cmul(v, inv);
     }
     __syncthreads();
-    // save column k (after the swap) for the elimination
     for (int i = threadIdx.x; i < n; i += blockDim.x) w.fcol[i] = to_d(A[(long long)i * n + k]);
 }
 
+// Elimination of column k from every other row, within the panel columns: one warp
+// per row, lanes over the columns.
 template <typename C>
-__global__ void k_gj_eliminate(C* A, int n, int k, GJWork w) {
+__global__ void __launch_bounds__(256) k_gj_eliminate(C* A, int n, int k, int k0, int kb, GJWork w) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n || i == k) return;
+    const C f = cvt<C>(w.fcol[i]);
+    for (int c = k0 + lane; c < k0 + kb; c += 32) {
+        const C pk = A[(long long)k * n + c];
+        const long long idx = (long long)i * n + c;
+        const C v = (c == k) ? czero<C>() : A[idx];
+        A[idx] = csub(v, cmul(f, pk));
+    }
+}
+
+// The panel's row swaps on the other columns (in the order they were taken), then a
+// copy of the pivot rows R[s][c] = A[k0 + s][c]: one thread per column.
+template <typename C>
+__global__ void __launch_bounds__(256) k_gj_swap_rows(C* A, int n, int k0, int kb, GJWork w) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
-    const C pk = A[(long long)k * n + c];
-    for (int i = blockIdx.y; i < n; i += gridDim.y) {
-        if (i == k) continue;
-        const C f = cvt<C>(w.fcol[i]);
-        const long long idx = (long long)i * n + c;
-        C v = (c == k) ? czero<C>() : A[idx];
-        v = csub(v, cmul(f, pk));
-        A[idx] = v;
+    C* R = reinterpret_cast<C*>(w.rows);
+    const bool in_panel = c >= k0 && c < k0 + kb;
+    for (int j = k0; j < k0 + kb; ++j) {
+        const int p = w.perm[j];
+        if (!in_panel && p != j) {
+            const C t = A[(long long)j * n + c];
+            A[(long long)j * n + c] = A[(long long)p * n + c];
+            A[(long long)p * n + c] = t;
+        }
+        R[(long long)(j - k0) * n + c] = A[(long long)j * n + c];
     }
+}
+
+// A[i][c] = [i outside S] A[i][c] + sum_s A[i][k0 + s] R[s][c] for every column c
+// outside the panel.  Tile 64 x 64, thread (tx, ty) owns rows ty + 16a and columns
+// tx + 16b (a, b < 4); the panel columns are read, never written.
+template <typename C, int B>
+__global__ void __launch_bounds__(256) k_gj_update(C* A, int n, int k0, int kb, GJWork w) {
+    __shared__ C Ts[64][B + 1];
+    __shared__ C Rs[B][64];
+    const C* R = reinterpret_cast<const C*>(w.rows);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    for (int e = threadIdx.x; e < 64 * B; e += 256) {
+        const int r = e / B, s = e % B, gr = row0 + r;
+        Ts[r][s] = (gr < n && s < kb) ? A[(long long)gr * n + k0 + s] : czero<C>();
+    }
+    for (int e = threadIdx.x; e < B * 64; e += 256) {
+        const int s = e / 64, cc = e % 64, gc = col0 + cc;
+        Rs[s][cc] = (s < kb && gc < n) ? R[(long long)s * n + gc] : czero<C>();
+    }
+    __syncthreads();
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = czero<C>();
+#pragma unroll 4
+    for (int s = 0; s < B; ++s) {
+        C t[4], r[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = Ts[ty + 16 * a][s];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r[b] = Rs[s][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cfma(acc[a][b], t[a], r[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = row0 + ty + 16 * a, c = col0 + tx + 16 * b;
+            if (i >= n || c >= n || (c >= k0 && c < k0 + kb)) continue;
+            const long long idx = (long long)i * n + c;
+            const C old = (i >= k0 && i < k0 + kb) ? czero<C>() : A[idx];
+            A[idx] = cadd(old, acc[a][b]);
+        }
 }
 
 template <typename C>
@@ -260,23 +338,34 @@ __global__ void k_gj_unpermute(C* A, int n, GJWork w) {
     }
 }
 
-size_t gauss_jordan_work_bytes(int n) { return (size_t)n * sizeof(double2) + (size_t)n * sizeof(int) + 64; }
+// fcol (n double2) | perm (n int) | status | pad to 256 B | pivot rows (B x n, 256 n bytes
+// for both instances: 32 x 8 B and 16 x 16 B per column)
+static size_t gj_rows_offset(int n) { return (((size_t)n * sizeof(double2) + (size_t)n * sizeof(int) + 64) + 255) / 256 * 256; }
+size_t gauss_jordan_work_bytes(int n) { return gj_rows_offset(n) + (size_t)n * 256 + 256; }
 
 template <typename C>
 void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s) {
+    constexpr int B = GJPanel<C>::B;
+    static_assert(B * sizeof(C) == 256, "pivot-row buffer is 256 bytes per column");
     GJWork w;
     w.fcol = reinterpret_cast<double2*>(work);
     w.perm = reinterpret_cast<int*>(w.fcol + n);
     w.status = w.perm + n;
+    w.rows = reinterpret_cast<char*>(work) + gj_rows_offset(n);
     MG_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s));
-    const int rows_per = 1;
-    int gy = n / rows_per;
-    if (gy > 4096) gy = 4096;
-    for (int k = 0; k < n; ++k) {
-        k_gj_pivot<C><<<1, 1024, 0, s>>>(A, n, k, w);
-        k_gj_eliminate<C><<<dim3((n + 127) / 128, gy), 128, 0, s>>>(A, n, k, w);
+    long long launches = 0;
+    const dim3 tiles((n + 63) / 64, (n + 63) / 64);
+    for (int k0 = 0; k0 < n; k0 += B) {
+        const int kb = n - k0 < B ? n - k0 : B;
+        for (int k = k0; k < k0 + kb; ++k) {
+            k_gj_pivot<C><<<1, 1024, 0, s>>>(A, n, k, k0, kb, w);
+            k_gj_eliminate<C><<<(n + 7) / 8, 256, 0, s>>>(A, n, k, k0, kb, w);
+        }
+        k_gj_swap_rows<C><<<(n + 255) / 256, 256, 0, s>>>(A, n, k0, kb, w);
+        k_gj_update<C, B><<<tiles, 256, 0, s>>>(A, n, k0, kb, w);
+        launches += 2LL * kb + 2;
     }
-    launch_counter().fetch_add(2LL * n - 1);
+    launch_counter().fetch_add(launches - 1);
     MG_LAUNCHED();
     k_gj_unpermute<C><<<(n + 127) / 128, 128, 0, s>>>(A, n, w);
     MG_LAUNCHED();

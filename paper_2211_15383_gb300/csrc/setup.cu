@@ -319,12 +319,12 @@ static void coarsest_inverse(Ctx& c) {
     if (c.opt.mg_precision == 64) {
         if (!L.Dinv64) L.Dinv64 = c.alloc_n<double2>((size_t)n * n);
         MG_CUDA(cudaMemcpyAsync(L.Dinv64, Dd, sizeof(double2) * n * n, cudaMemcpyDeviceToDevice, c.stream));
-        ProfScope ps(c, "setup.gauss_jordan.f64", 2.0 * n * n * 16 * n, 8.0 * n * n * n);
+        ProfScope ps(c, "setup.gauss_jordan.f64", 2.0 * n * n * 16 * std::ceil(n / 16.0), 8.0 * n * n * n);
         launch_gauss_jordan<double2>(L.Dinv64, (int)n, work, c.stream);
     } else {
         if (!L.Dinv32) L.Dinv32 = c.alloc_n<float2>((size_t)n * n);
         launch_convert<float2, double2>(L.Dinv32, Dd, n * n, c.stream);
-        ProfScope ps(c, "setup.gauss_jordan.f32", 2.0 * n * n * 8 * n, 8.0 * n * n * n);
+        ProfScope ps(c, "setup.gauss_jordan.f32", 2.0 * n * n * 8 * std::ceil(n / 32.0), 8.0 * n * n * n);
         launch_gauss_jordan<float2>(L.Dinv32, (int)n, work, c.stream);
         if (tc_coarse_supported((int)n)) {
             if (!L.Dinv16) L.Dinv16 = c.alloc_n<__nv_bfloat16>((size_t)n * 2 * n);
