@@ -411,7 +411,9 @@ typedef struct {
  * operators of every level, the dense coarsest inverse in each precision used, the
  * deflation space and eigensolver blocks, and the Krylov, refinement, V-cycle and
  * estimator blocks of opt.max_block_rhs right-hand sides.  MGMLMC_EINVAL if the
- * lattice or hierarchy is malformed (as mgmlmc_set_gauge / mgmlmc_set_hierarchy). */
+ * lattice or hierarchy is malformed (as mgmlmc_set_gauge / mgmlmc_set_hierarchy),
+ * MGMLMC_ENOTIMPL if the coarsest level has more than 16384 unknowns.  Host only:
+ * needs no device. */
 int mgmlmc_request_footprint(const mgmlmc_request* req, size_t* bytes);
 
 /* Create a server on the current CUDA device (opt NULL: defaults).  MGMLMC_ECUDA
@@ -419,7 +421,9 @@ int mgmlmc_request_footprint(const mgmlmc_request* req, size_t* bytes);
 int mgmlmc_server_create(mgmlmc_server** out, const mgmlmc_server_options* opt);
 
 /* Cancel queued requests, stop running ones at their next check, wait for them,
- * release the pool and the server.  Results not yet polled are lost. */
+ * release the pool and the server.  Results not yet polled are lost.  No other call
+ * on this server may be in progress or follow (a thread blocked in mgmlmc_wait
+ * must have returned first). */
 void mgmlmc_server_destroy(mgmlmc_server* srv);
 
 /* Queue a request (the struct, theta and the start vectors are copied; the caller
