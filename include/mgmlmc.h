@@ -380,8 +380,9 @@ typedef struct {
     int64_t max_samples;  /* cap on samples over all terms                           */
     uint64_t seed;        /* noise seed of the estimate                              */
     double costs[MGMLMC_MAX_LEVELS]; /* per-sample cost of each term for the sample
-                             allocation; all zero: measured device time (then the
-                             allocation depends on the load)                         */
+                             allocation, > 0 for each of the nlevels terms; all zero:
+                             measured device time (then the allocation depends on
+                             the load)                                               */
     mgmlmc_options opt;   /* context options (mgmlmc_default_options for defaults)  */
 } mgmlmc_request;
 

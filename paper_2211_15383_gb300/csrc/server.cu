@@ -411,8 +411,13 @@ int mgmlmc_submit(mgmlmc_server* srv, const mgmlmc_request* req, uint64_t* id) {
         if (!r.start_vectors[l]) return fail(MGMLMC_EINVAL, "submit: missing start vectors");
     if (!(r.rel_tol > 0) || r.max_samples < 1 || r.k < 0 || (r.k > 0 && r.k > g.n[g.L - 1]))
         return fail(MGMLMC_EINVAL, "submit: rel_tol > 0, max_samples >= 1, 0 <= k <= n_L");
-    for (int t = 0; t < MGMLMC_MAX_LEVELS; ++t)
+    int positive = 0;
+    for (int t = 0; t < MGMLMC_MAX_LEVELS; ++t) {
         if (!(r.costs[t] >= 0) || !std::isfinite(r.costs[t])) return fail(MGMLMC_EINVAL, "submit: costs >= 0");
+        positive += t < r.nlevels && r.costs[t] > 0;
+    }
+    if (positive != 0 && positive != r.nlevels)   // the allocation divides by every term's cost
+        return fail(MGMLMC_EINVAL, "submit: costs all zero (measured) or > 0 for each of the nlevels terms");
     if (r.opt.max_block_rhs < 1 || r.opt.fgmres_restart < 1)
         return fail(MGMLMC_EINVAL, "submit: max_block_rhs and fgmres_restart >= 1");
     std::shared_ptr<Job> job;
