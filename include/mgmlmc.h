@@ -412,7 +412,8 @@ typedef struct {
  * operators of every level, the dense coarsest inverse in each precision used, the
  * deflation space and eigensolver blocks, and the Krylov, refinement, V-cycle and
  * estimator blocks of opt.max_block_rhs right-hand sides.  MGMLMC_EINVAL if the
- * lattice or hierarchy is malformed (as mgmlmc_set_gauge / mgmlmc_set_hierarchy),
+ * lattice, hierarchy or options are malformed (as mgmlmc_set_gauge /
+ * mgmlmc_set_hierarchy / mgmlmc_create),
  * MGMLMC_ENOTIMPL if the coarsest level has more than 16384 unknowns.  Host only:
  * needs no device. */
 int mgmlmc_request_footprint(const mgmlmc_request* req, size_t* bytes);

@@ -35,7 +35,7 @@ using mg::Error;
     }                                                            \
     return MGMLMC_OK;
 
-namespace {
+namespace mg {
 
 void check_options(const mgmlmc_options& o) {
     MG_REQUIRE(o.mg_precision == 64 || o.mg_precision == 32 || o.mg_precision == 16, MGMLMC_EINVAL,
@@ -47,6 +47,12 @@ void check_options(const mgmlmc_options& o) {
                "options: smoothing steps");
     MG_REQUIRE(o.max_block_rhs >= 1 && o.max_block_rhs <= 4096, MGMLMC_EINVAL, "options: 1 <= max_block_rhs <= 4096");
 }
+
+}  // namespace mg
+
+using mg::check_options;
+
+namespace {
 
 void require_level(const Ctx& c, int level) {
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "no hierarchy: call mgmlmc_set_hierarchy first");

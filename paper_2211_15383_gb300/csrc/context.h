@@ -171,6 +171,8 @@ void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);
 void check_device_error(Ctx& c);
 // d receives device copies of s's gauge field, mass, hierarchy, terms and deflations.
 void copy_state(Ctx& d, Ctx& s);
+// Throws MGMLMC_EINVAL for options outside their documented ranges.
+void check_options(const mgmlmc_options& o);
 // The MLMC loop of mgmlmc_estimate_trace(_concurrent): term t draws its samples on
 // ctx_of[t] (one host thread per term with `concurrent`); when *cancel becomes true
 // the loop stops at its next round with MGMLMC_ECANCELLED.

@@ -45,6 +45,12 @@ struct Geometry {
 };
 
 int geometry(const mgmlmc_request& r, Geometry& g, std::string& why) {
+    try {
+        mg::check_options(r.opt);
+    } catch (const mg::Error& e) {
+        why = std::string("request: ") + e.what();
+        return e.code;
+    }
     if (r.Lx < 2 || r.Lt < 2 || r.Lx % 2 || r.Lt % 2 || (long long)r.Lx * r.Lt > (1LL << 26)) {
         why = "request: Lx, Lt even, >= 2, Lx*Lt <= 2^26";
         return MGMLMC_EINVAL;
@@ -418,8 +424,6 @@ int mgmlmc_submit(mgmlmc_server* srv, const mgmlmc_request* req, uint64_t* id) {
     }
     if (positive != 0 && positive != r.nlevels)   // the allocation divides by every term's cost
         return fail(MGMLMC_EINVAL, "submit: costs all zero (measured) or > 0 for each of the nlevels terms");
-    if (r.opt.max_block_rhs < 1 || r.opt.fgmres_restart < 1)
-        return fail(MGMLMC_EINVAL, "submit: max_block_rhs and fgmres_restart >= 1");
     std::shared_ptr<Job> job;
     try {
         job = std::make_shared<Job>();

@@ -109,6 +109,9 @@ def test_request_footprint_checks_and_grows(pkg):
     with pytest.raises(pkg.MgmlmcError) as e:
         pkg.request_footprint(_request(pkg, 256, [(4, 4)], [8]))            # coarsest 64^2 * 16 > 16384
     assert e.value.code == -6
+    with pytest.raises(pkg.MgmlmcError) as e:
+        pkg.request_footprint(_request(pkg, 64, [(4, 4)], [8], mg_precision=8))   # options as mgmlmc_create
+    assert e.value.code == -1 and "mg_precision" in str(e.value)
 
 
 def test_server_calls_without_a_device(pkg):
