@@ -6,6 +6,10 @@ oracle is used: sigma_min comes from inverse iteration on (D^H D)^{-1} with a
 sparse LU of D.  Writes tests/golden/mass_<L>.json.
 
     python -m oracle.tune_mass schwinger-128x128 1e-3
+    python -m oracle.tune_mass schwinger-128x128 1e-3 --at -0.141406
+
+With --at the bisection is skipped: sigma_min is evaluated (to the default,
+certified residual) at the given m0, which is recorded with it.
 """
 from __future__ import annotations
 
@@ -21,24 +25,44 @@ import inputs
 from oracle import wilson
 
 
-def sigma_min(D, iters: int = 60, seed: int = 0) -> float:
+def sigma_min(D, iters: int = 5000, seed: int = 0, tol: float = 1e-13) -> float:
+    """Smallest singular value of D by inverse iteration on A = (D^H D)^{-1}.
+
+    A is Hermitian positive definite with largest eigenvalue 1/sigma_min^2.  Each
+    step forms w = D^{-H} x and y = D^{-1} w = A x (two solves with one LU of D);
+    theta = x^H A x = ||w||^2 is the Rayleigh quotient of the unit vector x.  The
+    iteration stops once the residual ||A x - theta x|| is at most tol * theta:
+    for Hermitian A an eigenvalue then lies within that distance of theta, so the
+    stop certifies the estimate (a stop on the change of successive estimates
+    does not: it ends early on nearly degenerate singular values).
+    """
     lu = spla.splu(sp.csc_matrix(D))
     x = np.random.default_rng(seed).standard_normal(D.shape[0]).astype(np.complex128)
     x /= np.linalg.norm(x)
-    est = 0.0
+    theta = 0.0
     for _ in range(iters):
-        y = lu.solve(lu.solve(x, trans="H"))        # (D^H D)^{-1} x = D^{-1} D^{-H} x
-        nrm = np.linalg.norm(y)
-        new = 1.0 / np.sqrt(nrm)
-        x = y / nrm
-        if abs(new - est) < 1e-10 * new:
-            return new
-        est = new
-    return est
+        w = lu.solve(x, trans="H")                  # D^{-H} x
+        y = lu.solve(w)                             # D^{-1} D^{-H} x = (D^H D)^{-1} x
+        theta = float(np.vdot(w, w).real)           # x^H (D^H D)^{-1} x
+        if np.linalg.norm(y - theta * x) <= tol * theta:
+            break
+        x = y / np.linalg.norm(y)
+    return 1.0 / np.sqrt(theta)
+
+
+_sigma_min = sigma_min
 
 
 def tune(theta, target: float, m_hi: float = 0.0, step: float = 0.02, tol: float = 0.02):
-    """Largest-sigma side bracket then bisection on m0 (sigma_min decreases towards m_c)."""
+    """Largest-sigma side bracket then bisection on m0 (sigma_min decreases towards m_c).
+
+    The bisection needs sigma_min to about 1e-4 relative, so its estimates stop at a
+    residual of 1e-6 (the Rayleigh quotient's error is of the order of the squared
+    residual over the relative gap)."""
+
+    def sigma_min(D):
+        return _sigma_min(D, tol=1e-6)
+
     s_hi = sigma_min(wilson.wilson_dirac(theta, m_hi))
     m_lo = m_hi
     while True:
@@ -62,10 +86,19 @@ def tune(theta, target: float, m_hi: float = 0.0, step: float = 0.02, tol: float
 
 
 def main(argv):
+    at = None
+    if "--at" in argv:
+        i = argv.index("--at")
+        at = float(argv[i + 1])
+        argv = argv[:i] + argv[i + 2:]
     name = argv[1] if len(argv) > 1 else "schwinger-128x128"
     target = float(argv[2]) if len(argv) > 2 else 1e-3
     w = inputs.workload(name)
-    m0, s = tune(w.gauge(), target)
+    if at is None:
+        m0, _ = tune(w.gauge(), target)
+    else:
+        m0 = at
+    s = sigma_min(wilson.wilson_dirac(w.gauge(), m0))
     out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                        "tests", "golden", f"mass_{w.Lx}.json")
     with open(out, "w") as f:
