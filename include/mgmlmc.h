@@ -306,24 +306,28 @@ int mgmlmc_profile_report(mgmlmc_ctx* ctx, char* buf, size_t cap, size_t* needed
 int mgmlmc_fma_peak(int precision, double* flops_per_s);
 
 /* Allocation-free coarsest solve (the paper has no counterpart; this is a service
- * for callers that must not allocate device memory, e.g. code running under a host
- * framework that owns a fixed device-memory budget or forbids allocation while it
- * is recording or replaying work, or a real-time loop that cannot take the
- * synchronisation that cudaMalloc/cudaFree imply).
- * y = D_L^{-1} x with the stored BF16 inverse on the tensor cores, exactly the
- * computation of mgmlmc_apply(MGMLMC_OP_DINV_C) in the mixed mode.  x and y are
- * caller-owned device arrays of nrhs FP32 complex vectors laid out [n_L][nrhs]
- * (row-major, rhs fastest, interleaved re/im); y must not alias x.
- * Needs mg_precision = 32 and n_L % 128 == 0 (MGMLMC_ESTATE otherwise); nrhs a
- * multiple of 32 with n_L * nrhs <= 2^20 (MGMLMC_EINVAL otherwise).
+ * for callers that must not allocate device memory while they run, e.g. code
+ * running under a host framework that owns a fixed device-memory budget, or a
+ * real-time loop that cannot take the synchronisation that cudaMalloc/cudaFree
+ * imply).
+ * y = D_L^{-1} x with the stored BF16 inverse on the tensor cores: the computation
+ * of mgmlmc_apply(MGMLMC_OP_DINV_C) in the mixed modes.  The results agree with
+ * that call within FP32 accumulation rounding, not bit for bit: this call sums
+ * over the whole of n_L in one pass, the context path may split the sum.  x and y
+ * are caller-owned device arrays of nrhs FP32 complex vectors laid out
+ * [n_L][nrhs] (row-major, rhs fastest, interleaved re/im); y must not alias x,
+ * y must be 16-byte aligned and x 8-byte aligned (MGMLMC_EINVAL otherwise).
+ * Needs mg_precision 32 or 16 and n_L % 128 == 0 (MGMLMC_ESTATE otherwise); nrhs
+ * a multiple of 32 with n_L * nrhs <= 2^20 (MGMLMC_EINVAL otherwise).
  * Work space: a file-scope 8 MiB device array, present on every GPU that loads
  * the library until the process exits; every call overwrites it entirely (no
  * part needs to start at zero), so calls that overlap on the GPU (different
  * streams or threads) race and must be serialised by the caller.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress) and
  * should come before any stream capture.  The call runs on `stream` (a
- * cudaStream_t, NULL = default stream) and synchronises it before returning;
- * MGMLMC_ETIMEOUT if a bounded wait inside the kernel gave up. */
+ * cudaStream_t, NULL = default stream) and synchronises it before returning, to
+ * read the kernel's status; MGMLMC_ETIMEOUT if a bounded wait inside the kernel
+ * gave up. */
 int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* ctx, int nrhs, const float* x, float* y, void* stream);
 
 /* Level geometry: sites per direction, dof per site, n_l. */

@@ -874,8 +874,11 @@ extern "C" int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* h, int nrhs, const floa
         MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "coarse_inverse_noalloc: no hierarchy");
         const mg::Level& L = c.lev[c.L - 1];
         MG_REQUIRE(L.Dinv16 != nullptr, MGMLMC_ESTATE,
-                   "coarse_inverse_noalloc: needs mg_precision = 32 and a coarsest level with n_L % 128 == 0");
+                   "coarse_inverse_noalloc: needs mg_precision 32 or 16 and a coarsest level with n_L % 128 == 0");
         MG_REQUIRE(x && y && x != y, MGMLMC_EINVAL, "coarse_inverse_noalloc: x, y must be distinct device pointers");
+        // the kernel stores y with 16-byte vector stores and reads x as 8-byte pairs
+        MG_REQUIRE(((uintptr_t)y & 15) == 0 && ((uintptr_t)x & 7) == 0, MGMLMC_EINVAL,
+                   "coarse_inverse_noalloc: y must be 16-byte and x 8-byte aligned");
         MG_REQUIRE(nrhs >= 32 && nrhs % 32 == 0, MGMLMC_EINVAL, "coarse_inverse_noalloc: nrhs must be a multiple of 32");
         const int n = (int)L.n;
         const size_t need = (size_t)2 * nrhs * 2 * n * sizeof(__nv_bfloat16);

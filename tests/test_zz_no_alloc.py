@@ -1,8 +1,8 @@
 """The allocation-free coarsest solve (mgmlmc_coarse_inverse_noalloc).
 
 Some callers cannot allocate device memory while they run (a host framework that
-owns a fixed memory budget or records work for later replay, a real-time loop
-that cannot take cudaMalloc's synchronisation).  The entry point gives them the
+owns a fixed memory budget, a real-time loop that cannot take cudaMalloc's
+synchronisation).  The entry point gives them the
 mixed-precision coarsest solve with its work space in a static device array; the
 caller passes device input and output.  Checked against mgmlmc_apply(OP_DINV_C),
 which runs the same tensor-core kernel with context work space, on two calls in
@@ -18,7 +18,8 @@ import inputs
 
 pytestmark = pytest.mark.gpu
 
-# Same computation on the same FP32 input: identical up to FP32 rounding of the
+# Same computation on the same FP32 input: equal up to FP32 rounding of the
+# accumulation order (the context path may split the sum over n_L) and of the
 # returned values (the host path converts to FP64 and back).
 TOL = 1e-6
 
@@ -43,10 +44,10 @@ def _ctx(pkg, precision):
     return ctx
 
 
-@pytest.mark.parametrize("nrhs", [64, 256])
-def test_noalloc_matches_existing_entry_point(env, nrhs):
+@pytest.mark.parametrize("precision,nrhs", [(32, 64), (32, 256), (16, 64)])
+def test_noalloc_matches_existing_entry_point(env, precision, nrhs):
     torch, pkg = env
-    with _ctx(pkg, 32) as ctx:
+    with _ctx(pkg, precision) as ctx:
         n = ctx.level_info(2)[3]
         rng = np.random.default_rng(nrhs)
         x = (rng.standard_normal((nrhs, n)) + 1j * rng.standard_normal((nrhs, n))).astype(np.complex64)
@@ -75,6 +76,10 @@ def test_noalloc_limits(env):
         too_many = 32 * ((2 ** 20 // n) // 32 + 1)           # n_L * nrhs above 2^20
         with pytest.raises(pkg.MgmlmcError) as e:
             ctx.coarse_inverse_noalloc(too_many, buf.data_ptr(), out.data_ptr())
+        assert e.value.code == -1
+        # y off its 16-byte alignment (one complex64 in): refused on the host, no kernel runs
+        with pytest.raises(pkg.MgmlmcError) as e:
+            ctx.coarse_inverse_noalloc(32, buf.data_ptr(), out.data_ptr() + 8)
         assert e.value.code == -1
     with _ctx(pkg, 64) as ctx:                              # FP64 mode keeps no BF16 inverse
         n = ctx.level_info(2)[3]
