@@ -1,22 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark of deflated MG-MLMC on GB300: MG-MLMC samples/s on the 128x128
-Wilson-Schwinger workload (3-level multigrid, 4x4 then 2x2 aggregates, 8 test
-vectors per spin, 64 deflated triplets of the coarsest operator, 256 Z2
-vectors per level solved as one multi-RHS block to FP64 relative residual 1e-12).
+"""Benchmark of deflated MG-MLMC on GB300: MG-MLMC samples/s on the 1024x1024
+Wilson-Schwinger workload ("Scale": beta = 5, near-critical m0, a 3-term
+multigrid telescoping sum whose solver hierarchy continues three levels below
+it, 512 deflated triplets of the level-3 operator, blocks of Z2 vectors sized to
+HBM by the library's autotuner), every solve to FP64 relative residual 1e-12.
 
-One step = one block of 256 samples on every term of the telescoping sum
-(two multigrid-preconditioned solves per difference-level sample, one solve
-plus the deflation projections for the coarsest term, FP64 sample assembly).
-The headline run solves every block in FP64 by iterative refinement around an
-FP32 multigrid cycle with BF16 tensor-core smoothers and coarsest solve, and
-runs the terms of a step at once (one context and CUDA stream per term,
-mgmlmc_estimate_concurrent; the one-context sequential rate is reported too);
-the all-FP64 path and the plain FP64 single-rhs path are measured beside it, with the
-per-sample difference of the two batched runs on the same noise.  The line
-also carries the time to tr(D^-1) at relative error 1e-4 (the paper's
-tolerance), the fine stencil's HBM bandwidth, and a serving run: whole trace
-requests of mixed lattice sizes through the request server, all at once and
-then as a Poisson stream, with p50/p99 time to trace.
+One step = one block of N samples on every term of the telescoping sum (two
+multigrid-preconditioned solves per difference-level sample, one solve plus the
+deflation projections for the last term, FP64 sample assembly).  The headline
+run solves every block in FP64 by iterative refinement around an FP32 multigrid
+cycle with BF16 tensor-core smoothers, coarsest solve and deflation projections.
+Beside it: the end-to-end rate through the C ABI with host probes, the time to
+tr(D^-1) at relative error 1e-4 (the paper's tolerance) measured for the mixed
+path and projected for the all-FP64 batched and the plain FP64 single-rhs paths
+from their measured per-sample costs, the fine stencil's HBM bandwidth, a
+serving run (trace requests of mixed lattice sizes, p50/p99 time to trace) and
+the CPU oracle on the largest workload its direct solves can bound.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -57,7 +56,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="schwinger-128x128")
+    ap.add_argument("--workload", default="schwinger-1024x1024")
+    ap.add_argument("--no-tune", action="store_true", help="keep the workload's block width (no autotuner)")
+    ap.add_argument("--fp64-block", type=int, default=32, help="right-hand sides per block of the FP64 comparison")
+    ap.add_argument("--fp64-deflation", action="store_true",
+                    help="deflate the FP64 comparison too (its eigensolver runs in FP64)")
+    ap.add_argument("--cpu-workload", default="schwinger-128x128",
+                    help="workload of the oracle CPU baseline (its direct sparse LU must factor the levels)")
     ap.add_argument("--precision", type=int, default=16, choices=[64, 32, 16],
                     help="multigrid precision of the headline run: 32 = FP32 multigrid + BF16 tensor-core "
                          "coarsest solve inside FP64 iterative refinement; 16 = as 32 with the coarse "
@@ -258,23 +263,60 @@ def class_summary(report, top=8):
 
 
 # ----------------------------------------------------------------------------- GPU runs
-def make_ctx(pkg, w, prec):
+_GAUGE = {}
+
+
+def gauge_of(w):
+    """The workload's gauge field, generated once per process (host input data)."""
+    if w.name not in _GAUGE:
+        _GAUGE[w.name] = w.gauge()
+    return _GAUGE[w.name]
+
+
+def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False):
+    """Context with the workload's hierarchy (and deflation); optionally autotuned."""
     t0 = time.time()
-    ctx = pkg.Context(mg_precision=prec, max_block_rhs=w.nrhs)
-    ctx.set_gauge(w.gauge())
+    opts = {"mg_precision": prec, "max_block_rhs": nrhs or w.nrhs, "kcycle_iters": w.kcycle}
+    if restart:
+        opts["fgmres_restart"] = restart
+    ctx = pkg.Context(**opts)
+    ctx.set_gauge(gauge_of(w))
     ctx.set_mass(w.m0)
     t1 = time.time()
     ctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
+    if w.skip:
+        ctx.set_terms(list(w.skip))
     t2 = time.time()
-    ctx.compute_deflation(w.k, 1e-9, 400)
+    kk = w.k if k is None else k
+    defl_converged = True
+    if kk:
+        try:
+            ctx.compute_deflation(kk, w.defl_tol, w.defl_iters)
+        except pkg.MgmlmcError as e:          # not converged to defl_tol: the vectors are kept
+            if e.code != -3:
+                raise
+            defl_converged = False
     t3 = time.time()
-    return ctx, {"gauge_upload_s": t1 - t0, "hierarchy_s": t2 - t1, "deflation_s": t3 - t2}
+    setup = {"gauge_upload_s": t1 - t0, "hierarchy_s": t2 - t1, "deflation_s": t3 - t2,
+             "deflation": {"k": kk, "tol": w.defl_tol, "max_iters": w.defl_iters, "converged": defl_converged}}
+    tuned = None
+    if tune:
+        t4 = time.time()
+        tuned = ctx.autotune()
+        setup["autotune_s"] = time.time() - t4
+    return ctx, setup, tuned
 
 
-def run_steps(ctx, w, nterms, first_step, K, seed):
+def run_steps(ctx, nterms, N, first_step, K, seed):
+    """K steps of one block of N samples on every term (one context)."""
     for k in range(K):
         for t in range(nterms):
-            ctx.estimate_level(t, (first_step + k) * w.nrhs, w.nrhs, seed, samples=False)
+            ctx.estimate_level(t, (first_step + k) * N, N, seed, samples=False)
+
+
+def concurrent_ok(w):
+    """Terms at once on context copies only where the copies' work space is small."""
+    return w.n1 <= (1 << 16)
 
 
 def timed_region(torch, ws, fn, name=None):
@@ -294,6 +336,33 @@ def timed_region(torch, ws, fn, name=None):
     return max_over_ranks(e0.elapsed_time(e1) * 1e-3, ws)
 
 
+def probe_blocks(seed, n_of, N, K, torch):
+    """K steps of pinned host int8 +-1 probe blocks [N][n_t] per term (seeded host data)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(K):
+        per = []
+        for n in n_of:
+            arr = torch.empty((N, n), dtype=torch.int8, pin_memory=True)
+            a = arr.numpy()
+            a[:] = rng.integers(0, 2, size=(N, n), dtype=np.int8)
+            a *= 2
+            a -= 1
+            per.append(a)
+        out.append(per)
+    return out
+
+
+def per_term_rate(ctx, nterms, N, first, seed, torch):
+    """Seconds per sample of each term on one block of N samples (device time)."""
+    out = []
+    for t in range(nterms):
+        torch.cuda.synchronize()
+        _, st = ctx.estimate_level(t, first, N, seed, samples=False)
+        out.append(st["seconds"] / N)
+    return out
+
+
 def gpu_arm(args, rank, ws, local):
     import torch
 
@@ -308,40 +377,42 @@ def gpu_arm(args, rank, ws, local):
     peaks = measured_peaks()
     fp64_peak = pkg.fma_peak(64)
     fp32_peak = pkg.fma_peak(32)
-    ctx, setup = make_ctx(pkg, w, args.precision)
-    nterms, _ = ctx.num_terms()
+    t_gauge = time.time()
+    gauge_of(w)
+    gauge_gen_s = time.time() - t_gauge
+    ctx, setup, tuned = make_ctx(pkg, w, args.precision, tune=not args.block_rhs and not args.no_tune)
+    setup["gauge_generation_s"] = gauge_gen_s
+    N = tuned["block_rhs"] if tuned else w.nrhs
+    nterms, levels = ctx.num_terms()
     K, W = args.steps, args.warmup
     seed = replica_seed(w, rank)
-    # the terms of a step are independent: one context (same inputs, same hierarchy) and
-    # CUDA stream per term, all terms at once through mgmlmc_estimate_concurrent
+    # small lattices: the terms of a step at once, one context (device copy) and CUDA
+    # stream per term; large ones: one context, the terms one after another (each
+    # context would hold its own Krylov work space, and the blocks fill the GPU anyway)
     ctxs = [ctx]
     helper_setup_s = 0.0
-    if not args.sequential:
+    if not args.sequential and concurrent_ok(w):
         t0 = time.time()
         for t in range(1, nterms):
             with torch.cuda.stream(torch.cuda.Stream()):
-                ctxs.append(pkg.Context(copy_of=ctx))         # device copy of the set-up state
+                ctxs.append(pkg.Context(copy_of=ctx))
         helper_setup_s = time.time() - t0
 
     def steps(first, count, probes=None, outs=None):
         for k in range(first, first + count):
             if len(ctxs) > 1:
-                pkg.estimate_concurrent(ctxs, list(range(nterms)), k * w.nrhs, w.nrhs, seed,
+                pkg.estimate_concurrent(ctxs, list(range(nterms)), k * N, N, seed,
                                         probes=None if probes is None else probes[k - first],
                                         samples=outs is not None, out=outs)
             elif probes is None:
-                run_steps(ctx, w, nterms, k, 1, seed)
+                run_steps(ctx, nterms, N, k, 1, seed)
             else:
                 for t in range(nterms):
                     ctx.estimate_level_probes(t, probes[k - first][t], out=outs[t])
 
     steps(0, W)                                                             # warm-up
     if len(ctxs) > 1:
-        # the comparison below runs every term on the first context, which the concurrent
-        # steps only ran on term 0: warm its other terms too (workspaces, iteration counts)
-        run_steps(ctx, w, nterms, 0, 1, seed)
-    # timed region: no event profiling (it costs host time per launch); the launch
-    # counter is reset so that the kernels launched inside it are counted
+        run_steps(ctx, nterms, N, 0, 1, seed)
     ctx.profile(False, reset=True)
     clk = Clocks(local)
     clk.start()
@@ -349,16 +420,17 @@ def gpu_arm(args, rank, ws, local):
     sec = timed_region(torch, ws, lambda: steps(W, K), tag if args.nvtx else None)
     clocks = clk.stop()
     launches = int(ctx.profile_report().get("__launches__", {}).get("count", 0))
-    # for comparison: the same amount of work with the terms one after another on one context
-    sec_seq = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W + K, K, seed)) if len(ctxs) > 1 else sec
+    sec_seq = timed_region(torch, ws, lambda: run_steps(ctx, nterms, N, W + K, K, seed)) if len(ctxs) > 1 else sec
     # K steps on one context with per-kernel-class CUDA events (roofline, class shares)
     ctx.profile(True, reset=True)
-    sec_prof = timed_region(torch, ws, lambda: run_steps(ctx, w, nterms, W + 2 * K, K, seed))
+    sec_prof = timed_region(torch, ws, lambda: run_steps(ctx, nterms, N, W + 2 * K, K, seed))
     ctx.profile(False)
     report = ctx.profile_report()
     report.pop("__launches__", None)
-    samples = K * nterms * w.nrhs * ws
-    value = job_throughput(K * nterms * w.nrhs, ws, sec)
+    samples = K * nterms * N * ws
+    value = job_throughput(K * nterms * N, ws, sec)
+    dims = w.level_dims()
+    n_of = [dims[lv - 1][0] * dims[lv - 1][1] * dims[lv - 1][2] for lv in levels]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": sec / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == 64 else "f64+f32+bf16",
@@ -366,124 +438,139 @@ def gpu_arm(args, rank, ws, local):
                          "FP64 iterative refinement (FP64 residuals, solution updates and sample sums; every "
                          "solve to relative residual 1e-12 in FP64) around an FP32 multigrid-preconditioned "
                          "FGMRES cycle with a BF16 tensor-core coarsest solve" +
-                         (" and BF16 tensor-core coarse smoother stencils" if args.precision == 16 else "")),
+                         (", BF16 tensor-core coarse smoother stencils and BF16 tensor-core deflation "
+                          "projections (FP32 accumulation; the deflated trace over the same rounded factors "
+                          "in FP64)" if args.precision == 16 else "")),
            "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, "
                    f"counter-based Z2 noise",
            "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "m0": w.m0, "beta": w.beta,
-                      "levels": w.nlevels, "agg": [list(a) for a in w.agg], "nvec": list(w.nvec),
-                      "deflated_triplets": w.k, "block_rhs": w.nrhs, "terms": nterms,
+                      "levels": w.nlevels, "sum_levels": w.nterms,
+                      "level_unknowns": n_of + [d[0] * d[1] * d[2] for d in dims[w.nterms:]],
+                      "agg": [list(a) for a in w.agg], "nvec": list(w.nvec),
+                      "deflated_triplets": w.k, "block_rhs": N, "terms": nterms,
+                      "fgmres_restart": tuned["fgmres_restart"] if tuned else ctx.options.fgmres_restart,
+                      "nu_post": tuned["nu_post"] if tuned else ctx.options.nu_post,
+                      "kcycle_iters": tuned["kcycle_iters"] if tuned else ctx.options.kcycle_iters,
+                      "autotune": tuned,
                       "solve_tol": 1e-12, "mg_precision": args.precision,
-                      "l2": "inputs exceed L2: one FP64 fine-level block of 256 rhs is "
-                            f"{2 * w.Lx * w.Lt * w.nrhs * 16 / 1e6:.0f} MB > 129 MB",
+                      "l2": "inputs exceed L2: one FP64 fine-level block is "
+                            f"{w.n1 * N * 16 / 1e6:.0f} MB > 129 MB",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
            "setup": setup, "clocks": clocks, "ms_per_step_profiled": sec_prof / K * 1e3,
            "roofline": roofline(report, peaks, fp64_peak, fp32_peak),
-           # the same for the next classes by device time (one entry per class)
            "roofline_next": [roofline(report, peaks, fp64_peak, fp32_peak, k) for k, _ in
                              sorted(report.items(), key=lambda kv: -kv[1]["ms"])[1:5]],
            "kernel_classes": class_summary(report),
-           # device time inside profiled classes per step, against the profiled step: the
-           # remainder is launch gaps and host round trips (convergence checks)
            "profiled_kernel_ms_per_step": sum(v["ms"] for v in report.values()) / K,
            "terms_concurrent": len(ctxs) > 1,
            "context_copies_s": helper_setup_s,
-           "sequential": {"value": job_throughput(K * nterms * w.nrhs, ws, sec_seq), "unit": UNIT,
-                          "ms_per_step": sec_seq / K * 1e3,
-                          "what": "same steps, terms one after another on one context and stream"},
            "peaks": {"fp64_fma_tflops": fp64_peak / 1e12, "fp32_fma_tflops": fp32_peak / 1e12,
                      "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
            "iters": {t: sum(c.get_stats(t)["iters"] for c in ctxs) for t in range(nterms)}}
+    if len(ctxs) > 1:
+        out["sequential"] = {"value": job_throughput(K * nterms * N, ws, sec_seq), "unit": UNIT,
+                             "ms_per_step": sec_seq / K * 1e3,
+                             "what": "same steps, terms one after another on one context and stream"}
     out["gpu_launches"] = launches
+    live, peak = ctx.memory()
+    out["device_peak_gb"] = peak / 1e9
     # end-to-end through the public C ABI with host probe vectors and host samples
     if not args.no_e2e:
-        dims = w.level_dims()
-        _, levels = ctx.num_terms()
-        n_of = [dims[lv - 1][0] * dims[lv - 1][1] * dims[lv - 1][2] for lv in levels]
-        probes = []
-        for k in range(K):
-            per = []
-            for t in range(nterms):
-                u = inputs.uniform(9000 + rank, 100 * k + t, w.nrhs * n_of[t])
-                arr = torch.empty((w.nrhs, n_of[t]), dtype=torch.int8, pin_memory=True)
-                arr.numpy()[:] = np.where(u < 0.5, 1, -1).reshape(w.nrhs, n_of[t])
-                per.append(arr)
-            probes.append(per)
-        outs = [torch.empty((w.nrhs, 2), dtype=torch.float64, pin_memory=True).numpy().view(np.complex128)
+        probes = probe_blocks(9000 + rank, n_of, N, K, torch)
+        outs = [torch.empty((N, 2), dtype=torch.float64, pin_memory=True).numpy().view(np.complex128)
                 .reshape(-1) for _ in range(nterms)]
-        hprobes = [[probes[k][t].numpy() for t in range(nterms)] for k in range(K)]
-
-        sec_e2e = timed_region(torch, ws, lambda: steps(0, K, hprobes, outs), "timed_e2e" if args.nvtx else None)
+        sec_e2e = timed_region(torch, ws, lambda: steps(0, K, probes, outs), "timed_e2e" if args.nvtx else None)
         out["e2e"] = {"value": samples / sec_e2e, "unit": UNIT,
-                      "h2d_bytes_per_step": int(sum(w.nrhs * n for n in n_of)),
-                      "d2h_bytes_per_step": int(nterms * w.nrhs * 16),
+                      "h2d_bytes_per_step": int(sum(N * n for n in n_of)),
+                      "d2h_bytes_per_step": int(nterms * N * 16),
                       "path": ("mgmlmc_estimate_concurrent" if len(ctxs) > 1 else "mgmlmc_estimate_level_probes")
-                              + ": pinned host int8 probes in, host samples out"}
-    # time to tr(D^-1) at a fixed relative error (MLMC loop of the library)
+                              + ": pinned host int8 probes in, host samples out, copies inside the timed region"}
+    # time to tr(D^-1) at a fixed relative error (the MLMC loop of the library)
+    ttt = None
     if args.ttt_tol > 0:
-        # one context: the MLMC loop of the library after one setup
         t0 = time.time()
-        res = ctx.estimate_trace(args.ttt_tol, 10 ** 6, seed + 1)
-        ttt = time.time() - t0
-        out["time_to_trace"] = {"rel_tol": args.ttt_tol, "seconds_excl_setup": ttt,
-                                "seconds_incl_setup": ttt + sum(setup.values()),
-                                "trace": [res["trace"].real, res["trace"].imag], "rel_err": res["rel_err"],
-                                "converged": bool(res["converged"]),
-                                "samples_per_term": [t["nsamples"] for t in res["terms"]]}
+        res = ctx.estimate_trace(args.ttt_tol, 10 ** 7, seed + 1)
+        tt = time.time() - t0
+        setup_s = sum(v for k_, v in setup.items() if k_.endswith("_s"))
+        ttt = {"rel_tol": args.ttt_tol, "samples_per_term": [t["nsamples"] for t in res["terms"]]}
+        out["time_to_trace"] = {
+            "rel_tol": args.ttt_tol,
+            "mixed": {"seconds_excl_setup": tt, "seconds_incl_setup": tt + setup_s,
+                      "trace": [res["trace"].real, res["trace"].imag], "rel_err": res["rel_err"],
+                      "converged": bool(res["converged"]), "samples_per_term": ttt["samples_per_term"],
+                      "variance_per_term": [t["variance"] for t in res["terms"]], "what": "measured"}}
         if len(ctxs) > 1:
-            # the same loop with each round's terms at once on one context per term (the
-            # extra contexts are device copies of the first: their time is counted)
             t0 = time.time()
-            resc = pkg.estimate_trace_concurrent(ctxs, args.ttt_tol, 10 ** 6, seed + 1)
-            tttc = time.time() - t0
-            out["time_to_trace"]["concurrent_terms"] = {
-                "seconds_excl_setup": tttc, "seconds_incl_setup": tttc + sum(setup.values()) + helper_setup_s,
-                "trace": [resc["trace"].real, resc["trace"].imag], "rel_err": resc["rel_err"],
+            resc = pkg.estimate_trace_concurrent(ctxs, args.ttt_tol, 10 ** 7, seed + 1)
+            out["time_to_trace"]["mixed_concurrent_terms"] = {
+                "seconds_excl_setup": time.time() - t0, "rel_err": resc["rel_err"],
                 "samples_per_term": [t["nsamples"] for t in resc["terms"]]}
-    # the other precision on the same workload (error of the mixed run against FP64 on the
-    # same noise), then the plain FP64 single-rhs path
     for c_ in ctxs[1:]:
         c_.close()
+    # the FP64 paths on the same workload: the all-FP64 batched solve and the plain FP64
+    # single-rhs solve, per-sample device cost of every term; with the identical samples
+    # (same noise, same estimator) their time to trace follows from the sample counts of
+    # the MLMC run above
     if not args.no_mixed:
-        other = 64 if args.precision != 64 else 32
-        head_samples = [ctx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
+        head_samples = [ctx.estimate_level(t, 0, min(N, 32), seed)[0] for t in range(nterms)]
+        mixed_cost = per_term_rate(ctx, nterms, N, 10 ** 6, seed, torch)
         ctx.close()
         torch.cuda.empty_cache()
-        octx, osetup = make_ctx(pkg, w, other)
-        oth_samples = [octx.estimate_level(t, 0, w.nrhs, seed)[0] for t in range(nterms)]
-        mixed_s, f64_s = (head_samples, oth_samples) if args.precision != 64 else (oth_samples, head_samples)
-        errs = [float(np.max(np.abs(g - r) / np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2)))))
-                for g, r in zip(mixed_s, f64_s)]
+        n64 = min(N, args.fp64_block)
+        t0 = time.time()
+        octx, osetup, _ = make_ctx(pkg, w, 64, nrhs=n64, restart=16, k=w.k if args.fp64_deflation else 0)
+        oth_samples = [octx.estimate_level(t, 0, min(N, 32), seed)[0] for t in range(nterms)]
+        errs = []
+        for t in range(nterms):
+            g, r = head_samples[t], oth_samples[t]
+            if w.k and t == nterms - 1 and not args.fp64_deflation:
+                continue                       # the FP64 run here is undeflated on the last term
+            errs.append(float(np.max(np.abs(g - r) / np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2))))))
         out["max_rel_sample_error_mixed_vs_f64_per_term"] = errs
-        run_steps(octx, w, nterms, 0, W, seed)
+        run_steps(octx, nterms, n64, 1, 1, seed)
         octx.profile(True, reset=True)
-        otag = "timed_f64" if other == 64 else "timed_mixed"
-        osec = timed_region(torch, ws, lambda: run_steps(octx, w, nterms, W, K, seed), otag if args.nvtx else None)
+        osec = timed_region(torch, ws, lambda: run_steps(octx, nterms, n64, 2, 1, seed))
         octx.profile(False)
         orep = octx.profile_report()
         orep.pop("__launches__", None)
-        key = "fp64" if other == 64 else "mixed"
-        out[key] = {"value": samples / osec, "unit": UNIT, "ms_per_step": osec / K * 1e3,
-                    "headline_speedup_over_this": value / (samples / osec), "setup": osetup,
-                    "roofline": roofline(orep, peaks, fp64_peak, fp32_peak),
-                    "kernel_classes": class_summary(orep)}
+        f64_cost = [octx.get_stats(t)["seconds"] / octx.get_stats(t)["nsamples"] for t in range(nterms)]
+        out["fp64"] = {"value": nterms * n64 * ws / osec, "unit": UNIT, "block_rhs": n64,
+                       "ms_per_step": osec * 1e3, "headline_speedup_over_this": value / (nterms * n64 * ws / osec),
+                       "setup": osetup, "seconds_per_sample_per_term": f64_cost,
+                       "roofline": roofline(orep, peaks, fp64_peak, fp32_peak),
+                       "kernel_classes": class_summary(orep)}
         octx.close()
         torch.cuda.empty_cache()
+        single_cost = None
         if args.single_rhs_samples > 0:
-            # plain FP64 single-rhs GPU path: same kernels, FP64 multigrid, one rhs per solve
-            sctx = pkg.Context(mg_precision=64, max_block_rhs=1)
-            sctx.set_gauge(w.gauge())
-            sctx.set_mass(w.m0)
-            sctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
-            sctx.compute_deflation(w.k, 1e-9, 400)
+            sctx, ssetup, _ = make_ctx(pkg, w, 64, nrhs=1, restart=16, k=0)
             ns = args.single_rhs_samples
             for t in range(nterms):
                 sctx.estimate_level(t, 10 ** 6, 1, seed, samples=False)
+            sctx.reset_stats()
             ssec = timed_region(torch, ws, lambda: [sctx.estimate_level(t, 0, ns, seed, samples=False)
                                                       for t in range(nterms)])
+            single_cost = [sctx.get_stats(t)["seconds"] / ns for t in range(nterms)]
             out["plain_fp64_single_rhs"] = {"value": nterms * ns * ws / ssec, "unit": UNIT,
-                                            "samples_timed": nterms * ns,
+                                            "samples_timed": nterms * ns, "setup": ssetup,
+                                            "seconds_per_sample_per_term": single_cost,
                                             "headline_speedup_over_this": value / (nterms * ns * ws / ssec)}
             sctx.close()
+            torch.cuda.empty_cache()
+        if ttt is not None:
+            Nt = ttt["samples_per_term"]
+            mixed_est = sum(n * c for n, c in zip(Nt, mixed_cost))
+            out["time_to_trace"]["mixed_device_seconds_from_costs"] = mixed_est
+            out["time_to_trace"]["fp64_batched"] = {
+                "seconds_excl_setup": sum(n * c for n, c in zip(Nt, f64_cost)),
+                "setup_hierarchy_s": osetup["hierarchy_s"],
+                "what": "projected: the mixed run's sample counts (identical samples) x the measured FP64 "
+                        "per-sample device cost of each term"}
+            if single_cost:
+                out["time_to_trace"]["fp64_single_rhs"] = {
+                    "seconds_excl_setup": sum(n * c for n, c in zip(Nt, single_cost)),
+                    "setup_hierarchy_s": ssetup["hierarchy_s"],
+                    "what": "projected as above from the single-rhs per-sample cost"}
     else:
         ctx.close()
     if args.serving_requests > 0 and ws == 1:
@@ -499,48 +586,58 @@ def gpu_arm(args, rank, ws, local):
                               "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
                               "frac_of_measured_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                               "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
-                              "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"]}
+                              "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"],
+                              "bytes_per_launch": v["bytes"] / v["count"]}
     return out, w
 
 
 # ----------------------------------------------------------------------------- serving
 def serving_run(pkg, args):
-    """Trace requests of mixed lattices (64^2, 128^2), couplings (beta 3, 5) and masses
-    through the request server: first all at once (the saturated rate), then arriving
-    as a Poisson stream at args.serving_load x that rate.  Each request is a whole
-    problem (gauge field, 3-level hierarchy, deflation, MLMC loop to args.serving_tol);
-    its time to trace runs from submission to result.  Fixed per-term costs (level
-    sizes) make every request's result independent of the load."""
+    """Trace requests of mixed lattices (64^2, 128^2, 256^2, 512^2), couplings (beta 3,
+    5) and masses through the request server: first all at once (the saturated rate),
+    then arriving as a Poisson stream at args.serving_load x that rate.  Each request is
+    a whole problem (gauge field, hierarchy, deflation, MLMC loop to args.serving_tol);
+    its time to trace runs from submission to result.  64^2 and 128^2 use 3 levels;
+    256^2 and 512^2 a 3-term sum with solver-only levels below it (coarsest 4096
+    unknowns).  Fixed per-term costs (level sizes) make every request's result
+    independent of the load."""
     n = args.serving_requests
     rng = np.random.default_rng(20221115)
+    sizes = (64, 128, 256, 512)
+    shapes = {64: ((4, 4), (2, 2)), 128: ((4, 4), (2, 2)), 256: ((4, 4), (2, 2), (2, 2)),
+              512: ((4, 4), (2, 2), (2, 2), (2, 2))}
     t0 = time.time()
     fields, starts = {}, {}
-    for L in (64, 128):
+    for L in sizes:
         for beta in (3.0, 5.0):
             fields[(L, beta)] = inputs.metropolis_u1(L, L, beta, 200, 5000 + L + int(10 * beta))
-        dims = [(L, L, 2), (L // 4, L // 4, 16)]
+        dims = [(L, L, 2)]
+        for a in shapes[L][:-1]:
+            dims.append((dims[-1][0] // a[0], dims[-1][1] // a[1], 16))
         starts[L] = [inputs.start_vectors(7000 + L, i + 1, lx * lt * d, 8) for i, (lx, lt, d) in enumerate(dims)]
     gen_s = time.time() - t0
     masses = {3.0: (-0.09, -0.04), 5.0: (-0.03, 0.02)}
 
     def make(i):
-        L = int(rng.choice([64, 128]))
+        L = int(rng.choice(sizes))
         beta = float(rng.choice([3.0, 5.0]))
         m0 = float(rng.choice(masses[beta]))
+        agg = shapes[L]
         n0, n1, n2 = 2 * L * L, L * L, L * L // 4
-        req = pkg.make_request(fields[(L, beta)], m0, ((4, 4), (2, 2)), (8, 8), starts[L], args.serving_tol,
+        req = pkg.make_request(fields[(L, beta)], m0, agg, (8,) * len(agg), starts[L], args.serving_tol,
                                100 + i, k=32 if L == 64 else 64, setup_iters=4,
-                               costs=[(n0 + n1) / n0, (n1 + n2) / n0, n2 / n0], mg_precision=args.precision)
+                               costs=[(n0 + n1) / n0, (n1 + n2) / n0, n2 / n0], mg_precision=args.precision,
+                               sum_levels=3 if len(agg) > 2 else 0)
         return L, req
 
-    deadline = time.time() + 300.0
+    deadline = time.time() + 600.0
 
     def collect(srv, ids):
         res = []
         for i in ids:
             r = srv.wait(i, max(1.0, deadline - time.time()))
             if r is None:
-                raise TimeoutError("serving run exceeded 300 s")
+                raise TimeoutError("serving run exceeded 600 s")
             res.append(r)
         return res
 
@@ -575,17 +672,18 @@ def serving_run(pkg, args):
         span2 = time.perf_counter() - t0
         st = srv.stats()
     allr = res1 + res2
-    sizes = [L for L, _ in burst + stream]
+    lat = [L for L, _ in burst + stream]
     by_L = {}
-    for L in (64, 128):
-        rs = [r for r, l in zip(res2, sizes[n:]) if l == L and r["status"] == 0]
-        peaks = [r["peak_bytes"] for r, l in zip(allr, sizes) if l == L and r["status"] == 0]
-        by_L[f"{L}x{L}"] = {"requests": sum(1 for l in sizes if l == L),
+    for L in sizes:
+        rs = [r for r, l in zip(res2, lat[n:]) if l == L and r["status"] == 0]
+        peaks = [r["peak_bytes"] for r, l in zip(allr, lat) if l == L and r["status"] == 0]
+        by_L[f"{L}x{L}"] = {"requests": sum(1 for l in lat if l == L),
                             "p50_time_to_trace_s_poisson": float(np.median([r["total_s"] for r in rs])) if rs else None,
                             "device_peak_gb": max(peaks) / 1e9 if peaks else None}
     return {"requests_per_phase": n, "slots": args.serving_slots, "rel_tol": args.serving_tol,
-            "mix": "lattices 64^2 and 128^2, beta 3 (m0 -0.09, -0.04) and 5 (m0 -0.03, 0.02), 3 levels "
-                   "(4x4 then 2x2, 8 test vectors), k = 32 / 64, mg_precision %d" % args.precision,
+            "mix": "lattices 64^2, 128^2, 256^2, 512^2, beta 3 (m0 -0.09, -0.04) and 5 (m0 -0.03, 0.02); "
+                   "3-term sums (4x4 then 2x2 aggregates, 8 test vectors; 256^2 and 512^2 with 1 and 2 "
+                   "solver-only levels below), k = 32 (64^2) / 64, mg_precision %d" % args.precision,
             "saturated": summary(res1, span1),
             "poisson": dict(summary(res2, span2), load=args.serving_load, arrival_rate_per_s=lam),
             "by_lattice": by_L,
@@ -650,19 +748,28 @@ def cpu_oracle_rate(w, H, defl, seconds, procs, per_term=None):
     return n / dt, n, dt, per_term
 
 
-def cpu_baseline(w, seconds):
+ORACLE_LIMIT = ("the oracle's direct sparse LU cannot factor the levels of lattices above 128^2 within a "
+                "bounded time (256^2: about 3 minutes of factorisation alone, 1024^2: out of reach), so the CPU "
+                "baseline runs the largest workload it can bound")
+
+
+def cpu_baseline(w, seconds, headline):
     procs = os.cpu_count() or 1
     H, defl, setup_s = cpu_oracle_setup(w)
     rate, n, dt, per = cpu_oracle_rate(w, H, defl, seconds, procs)
-    return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{n} samples ({per} per term per process, {H.nlevels} terms, {procs} spawned "
-                      f"single-threaded processes) of {w.name}, direct sparse-LU solves; "
-                      f"{dt:.1f} s wall; oracle setup {setup_s:.0f} s not timed"}
+    out = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle", "workload": w.name,
+           "sample": f"{n} samples ({per} per term per process, {H.nlevels} terms, {procs} spawned "
+                     f"single-threaded processes) of {w.name}, direct sparse-LU solves; "
+                     f"{dt:.1f} s wall; oracle setup {setup_s:.0f} s not timed"}
+    if w.name != headline:
+        out["note"] = ORACLE_LIMIT
+    return out
 
 
 def reference_arm(args, rank, ws):
-    """The oracle timed on the host cores (rank 0 only)."""
-    w = inputs.workload(args.workload)
+    """The oracle timed on the host cores (rank 0 only), on the largest workload its
+    direct solves can bound (args.cpu_workload)."""
+    w = inputs.workload(args.cpu_workload)
     if rank != 0:
         return None
     procs = os.cpu_count() or 1
@@ -684,7 +791,8 @@ def reference_arm(args, rank, ws):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
             "data": f"synthetic: seeded Metropolis U(1) gauge field beta={w.beta} {w.Lx}x{w.Lt}, Z2 noise",
             "config": {"workload": w.name, "lattice": f"{w.Lx}x{w.Lt}", "levels": w.nlevels,
-                       "deflated_triplets": w.k, "block_rhs": w.nrhs},
+                       "deflated_triplets": w.k, "block_rhs": w.nrhs, "gpu_arm_workload": args.workload,
+                       "why_this_workload": ORACLE_LIMIT if w.name != args.workload else None},
             "cpu_baseline": {"kind": "oracle", "cores": procs, "sample": sample, "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -700,7 +808,7 @@ def main():
     out, w = gpu_arm(args, rank, ws, local)
     if rank == 0:
         if not args.no_cpu and ws == 1:
-            out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+            out["cpu_baseline"] = cpu_baseline(inputs.workload(args.cpu_workload), args.cpu_seconds, w.name)
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist

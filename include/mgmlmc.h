@@ -68,6 +68,13 @@ typedef struct {
     int nu_post;          /* post-smoothing MR steps per level.                [4]     */
     int max_block_rhs;    /* most right-hand sides solved together.            [256]   */
     int verbose;          /* 1: iteration counts on stderr.                    [0]     */
+    int kcycle_iters;     /* coarse-grid correction of the multigrid cycle (Sect. 3.1,
+                             Eq. two_level_mg_method applied recursively): 0 = one
+                             cycle on the next level (V-cycle); k > 0 = k steps of
+                             flexible GMRES on the next level preconditioned by its
+                             own cycle (K-cycle), wherever that level is not the
+                             coarsest.  The steps run entirely on the device.  0..16.
+                                                                               [0]     */
 } mgmlmc_options;
 
 /* Per-term statistics of the samples drawn so far (FP64, Sect. 3.2). */
@@ -160,12 +167,18 @@ int mgmlmc_set_hierarchy(mgmlmc_ctx* ctx, int nlevels, const int* agg_x, const i
  * plain (deflated) Hutchinson on D_1 (Sect. 2) for skip = {2..L}:
  * tr(D^{-1}) = tr(D_1^{-1} - P_1 P_2 D_3^{-1} P_2^H P_1^H) + ... .  nskip = 0
  * restores the plain sum.  Term t (0-based) then has fine level
- * term_level[t] and coarse level term_level[t+1] (none for the last term). */
+ * term_level[t] and coarse level term_level[t+1] (none for the last term).
+ * Skipping the last levels (e.g. skip = {4, 5} with L = 5) ends the sum at a
+ * level above the coarsest: the levels below it then serve only the solver
+ * (the multigrid cycle recurses through them down to the stored inverse of
+ * D_L), and the last term is tr(D_c^{-1}) of that level c. */
 int mgmlmc_set_terms(mgmlmc_ctx* ctx, int nskip, const int* skip);
 int mgmlmc_num_terms(const mgmlmc_ctx* ctx, int* nterms, int* term_level /* [MGMLMC_MAX_LEVELS] */);
 
-/* Exact deflation of the coarsest term (Sect. 2): the k smallest singular
- * triplets of D_L from the eigenpairs of Q_L = Gamma5^L D_L (U = Gamma5 X
+/* Exact deflation of the last term (Sect. 2), whose operator D_L is the
+ * coarsest level of the sum (the hierarchy's last level unless mgmlmc_set_terms
+ * ended the sum above it; then D_L below means that level's operator): the k
+ * smallest singular triplets of D_L from the eigenpairs of Q_L = Gamma5^L D_L (U = Gamma5 X
  * sign(Lambda), Sigma = |Lambda|, V = X), found by subspace iteration on
  * Q_L^{-1} with Rayleigh-Ritz until every residual ||Q x - lambda x|| <=
  * tol |lambda| (Sect. 4.3 uses tol = 1e-9), at most max_iters iterations.
@@ -174,7 +187,7 @@ int mgmlmc_num_terms(const mgmlmc_ctx* ctx, int* nterms, int* term_level /* [MGM
 int mgmlmc_compute_deflation(mgmlmc_ctx* ctx, int k, double tol, int max_iters);
 
 /* Host copies of the deflation: lambda[k], sigma[k], U and V as [k][n_L]
- * complex, tau (2 doubles).  Any pointer may be NULL. */
+ * complex (n_L of the deflated level), tau (2 doubles).  Any pointer may be NULL. */
 int mgmlmc_get_deflation(mgmlmc_ctx* ctx, double* lambda, double* sigma, double* U,
                          double* V, double* tau);
 
@@ -214,6 +227,16 @@ int mgmlmc_set_term_deflation_vectors(mgmlmc_ctx* ctx, int term, int k, const do
  * term), tau (2 doubles) = its deflated trace part.  Pointers may be NULL. */
 int mgmlmc_get_term_deflation(mgmlmc_ctx* ctx, int term, int* k, double* lambda, double* L, double* R,
                               double* tau);
+
+/* The deflated trace part that the estimate adds for term t (0-based; 2 doubles,
+ * zero without deflation).  With mg_precision 64 or 32 it is the tau of the
+ * stored FP64 factors (mgmlmc_get_term_deflation).  With mg_precision 16 the
+ * samples form the deflation projections on the tensor cores from the factors
+ * rounded to BF16 (FP64 -> FP32 -> BF16, to nearest) with FP32 accumulation, and
+ * this part is the trace over exactly those rounded factors, computed in FP64 —
+ * so the estimate stays unbiased for the factors it uses (Sect. 2, Eq.
+ * splitting_defl_trace holds for any fixed factors). */
+int mgmlmc_term_deflated_part(mgmlmc_ctx* ctx, int term, double* tau);
 
 /* nsamples Hutchinson samples of term t (0-based; Sect. 3.2):
  *   s_j = x_j^H D_a^{-1} x_j - (P^H x_j)^H D_b^{-1} (P^H x_j)   (difference term)
@@ -330,6 +353,31 @@ int mgmlmc_fma_peak(int precision, double* flops_per_s);
  * gave up. */
 int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* ctx, int nrhs, const float* x, float* y, void* stream);
 
+/* Result of mgmlmc_autotune. */
+typedef struct {
+    int block_rhs;        /* chosen opt.max_block_rhs                                  */
+    int fgmres_restart;   /* chosen opt.fgmres_restart                                 */
+    int nu_post;          /* chosen opt.nu_post                                        */
+    int kcycle_iters;     /* chosen opt.kcycle_iters                                   */
+    double samples_per_s; /* measured rate of the chosen setting: one block per term   */
+    size_t footprint;     /* modelled device bytes of the chosen setting               */
+    size_t budget;        /* the budget the candidates were held to                    */
+    int trials;           /* settings timed                                            */
+} mgmlmc_tune_result;
+
+/* Autotuner (no counterpart in the paper): chooses the block width, the FGMRES
+ * restart length, the post-smoothing steps and the coarse-grid correction of this
+ * context for this GPU.  Candidates whose modelled device footprint (the model of
+ * mgmlmc_request_footprint for the context's own shape) exceeds hbm_budget bytes
+ * (0: 90 % of the free device memory plus what the context holds) are skipped; at
+ * most max_trials others are timed on one block of samples of every term (a fixed
+ * Z2 noise block; the context's statistics are not touched), widest blocks first,
+ * then restart length, smoother steps and, with four levels or more, the K-cycle.
+ * The fastest becomes the context's setting; its work space is released.  Needs a
+ * hierarchy (and the deflation, if any, already computed).  MGMLMC_ENOMEM if no
+ * block width fits the budget. */
+int mgmlmc_autotune(mgmlmc_ctx* ctx, size_t hbm_budget, int max_trials, mgmlmc_tune_result* out);
+
 /* Level geometry: sites per direction, dof per site, n_l. */
 int mgmlmc_level_info(const mgmlmc_ctx* ctx, int level, int* lx, int* lt, int* d, int64_t* n);
 
@@ -384,10 +432,14 @@ typedef struct {
     int64_t max_samples;  /* cap on samples over all terms                           */
     uint64_t seed;        /* noise seed of the estimate                              */
     double costs[MGMLMC_MAX_LEVELS]; /* per-sample cost of each term for the sample
-                             allocation, > 0 for each of the nlevels terms; all zero:
+                             allocation, > 0 for each of the terms; all zero:
                              measured device time (then the allocation depends on
                              the load)                                               */
     mgmlmc_options opt;   /* context options (mgmlmc_default_options for defaults)  */
+    int sum_levels;       /* levels 1..sum_levels start the terms of the sum and the
+                             deflation acts on level sum_levels; the levels below
+                             serve only the solver (as mgmlmc_set_terms with the last
+                             levels skipped).  0: all nlevels                        */
 } mgmlmc_request;
 
 typedef struct {
@@ -419,7 +471,8 @@ typedef struct {
  * lattice, hierarchy or options are malformed (as mgmlmc_set_gauge /
  * mgmlmc_set_hierarchy / mgmlmc_create),
  * MGMLMC_ENOTIMPL if the coarsest level has more than 16384 unknowns.  Host only:
- * needs no device. */
+ * needs no device.  (The same model, for a context's own shape, bounds the
+ * candidates of mgmlmc_autotune.) */
 int mgmlmc_request_footprint(const mgmlmc_request* req, size_t* bytes);
 
 /* Create a server on the current CUDA device (opt NULL: defaults).  MGMLMC_ECUDA

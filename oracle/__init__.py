@@ -15,6 +15,8 @@ Monte Carlo", Lattice 2022):
 * ``deflation``  -- smallest singular triplets of D from the eigenpairs of
                     Q = Gamma5 D, and the deflated trace term (Sect. 2).
 * ``noise``      -- the counter-based Z2 noise of the Hutchinson estimator.
+* ``rounding``   -- BF16 rounding of the factors of the tensor-core deflation.
+* ``tune_mass``  -- sigma_min(D) by inverse iteration, used to choose the masses.
 * ``estimator``  -- per-sample values of every term of the telescoping sum
                     (Eq. mgmlmc, Eq. skip_level), exact traces by dense
                     inversion, the closed-form Z2 variance (Eq.
@@ -27,4 +29,4 @@ the samples it must reproduce are defined by exact inverses.
 Parity status of each function is stated in its docstring; functions with no
 independent pin say "parity unpinned".
 """
-from . import wilson, hierarchy, deflation, noise, estimator  # noqa: F401
+from . import wilson, hierarchy, deflation, noise, estimator, rounding  # noqa: F401

@@ -58,9 +58,26 @@ def smallest_triplets(D, g5: np.ndarray, k: int):
     return sigma, U, V, lam
 
 
-def coarsest_deflation(D, g5: np.ndarray, k: int) -> Deflation:
-    """Deflation of the traced operator D^{-1} by D's k smallest triplets."""
-    sigma, U, V, lam = smallest_triplets(D, g5, k)
+def smallest_triplets_sparse(D, g5: np.ndarray, k: int):
+    """smallest_triplets for operators too large for a dense eigensolver: the k
+    eigenvalues of Q = Gamma5 D nearest zero (the smallest |lambda|) by shift-invert
+    Lanczos at sigma = 0 (scipy's eigsh, which factors Q once with a sparse LU), the
+    same ordering and the same (U, Sigma, V) as smallest_triplets."""
+    import scipy.sparse.linalg as spla
+    Q = sp.diags(g5) @ sp.csr_matrix(D)
+    Q = (0.5 * (Q + Q.conj().T)).tocsc()
+    lam, X = spla.eigsh(Q, k=k, sigma=0.0, which="LM", tol=1e-14, ncv=min(Q.shape[0], max(2 * k + 1, k + 40)))
+    order = np.argsort(np.abs(lam), kind="stable")
+    lam, X = lam[order], X[:, order]
+    sigma = np.abs(lam)
+    U = g5[:, None] * X * np.sign(lam)[None, :]
+    return sigma, U, X, lam
+
+
+def coarsest_deflation(D, g5: np.ndarray, k: int, sparse: bool = False) -> Deflation:
+    """Deflation of the traced operator D^{-1} by D's k smallest triplets (dense
+    eigensolver, or shift-invert Lanczos with sparse=True)."""
+    sigma, U, V, lam = (smallest_triplets_sparse if sparse else smallest_triplets)(D, g5, k)
     return Deflation(L=V, R=U, a=1.0 / sigma, lam=lam)
 
 
@@ -113,3 +130,12 @@ def vector_deflation(hier, term, V: np.ndarray, solvers=None) -> Deflation:
         P = hier.prolongator(a, b)
         W = W - P @ S.solve(b, P.conj().T @ V)
     return Deflation(L=W, R=V, a=np.ones(V.shape[1]), lam=np.zeros(V.shape[1]))
+
+
+def bf16_factors(d: Deflation) -> Deflation:
+    """The same deflation with its factors L and R rounded to BF16 (oracle.rounding),
+    the form the tensor-core projections use; trace_term() of the result is the
+    deflated part over the rounded factors."""
+    from .rounding import bf16
+    return Deflation(L=bf16(d.L), R=bf16(d.R), a=d.a.copy(), lam=d.lam.copy())
+

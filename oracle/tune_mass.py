@@ -7,9 +7,14 @@ sparse LU of D.  Writes tests/golden/mass_<L>.json.
 
     python -m oracle.tune_mass schwinger-128x128 1e-3
     python -m oracle.tune_mass schwinger-128x128 1e-3 --at -0.141406
+    python -m oracle.tune_mass schwinger-1024x1024 1e-3 --lattice 128
 
 With --at the bisection is skipped: sigma_min is evaluated (to the default,
-certified residual) at the given m0, which is recorded with it.
+certified residual) at the given m0, which is recorded with it.  With
+--lattice L the workload's gauge recipe (beta, sweeps, seed) is run on an L x L
+lattice and the mass is tuned there (a lattice whose sparse LU the oracle can
+afford; the additive mass shift is a short-distance effect), written to
+tests/golden/mass_<Lx>_at<L>.json.
 """
 from __future__ import annotations
 
@@ -56,12 +61,13 @@ _sigma_min = sigma_min
 def tune(theta, target: float, m_hi: float = 0.0, step: float = 0.02, tol: float = 0.02):
     """Largest-sigma side bracket then bisection on m0 (sigma_min decreases towards m_c).
 
-    The bisection needs sigma_min to about 1e-4 relative, so its estimates stop at a
-    residual of 1e-6 (the Rayleigh quotient's error is of the order of the squared
-    residual over the relative gap)."""
+    The bisection needs sigma_min to about 1e-3 relative, so its estimates stop at a
+    residual of 1e-3: the Rayleigh quotient's error is of the order of the squared
+    residual over the relative gap, and within a cluster of nearly equal singular
+    values it lies inside the cluster."""
 
     def sigma_min(D):
-        return _sigma_min(D, tol=1e-6)
+        return _sigma_min(D, tol=1e-3)
 
     s_hi = sigma_min(wilson.wilson_dirac(theta, m_hi))
     m_lo = m_hi
@@ -85,24 +91,30 @@ def tune(theta, target: float, m_hi: float = 0.0, step: float = 0.02, tol: float
     return m, s
 
 
+def _option(argv, flag):
+    if flag not in argv:
+        return argv, None
+    i = argv.index(flag)
+    return argv[:i] + argv[i + 2:], float(argv[i + 1])
+
+
 def main(argv):
-    at = None
-    if "--at" in argv:
-        i = argv.index("--at")
-        at = float(argv[i + 1])
-        argv = argv[:i] + argv[i + 2:]
+    argv, at = _option(argv, "--at")
+    argv, lat = _option(argv, "--lattice")
     name = argv[1] if len(argv) > 1 else "schwinger-128x128"
     target = float(argv[2]) if len(argv) > 2 else 1e-3
     w = inputs.workload(name)
-    if at is None:
-        m0, _ = tune(w.gauge(), target)
+    if lat is None:
+        theta, fname, lattice = w.gauge(), f"mass_{w.Lx}.json", f"{w.Lx}x{w.Lt}"
     else:
-        m0 = at
-    s = sigma_min(wilson.wilson_dirac(w.gauge(), m0))
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                       "tests", "golden", f"mass_{w.Lx}.json")
+        L = int(lat)
+        theta = inputs.metropolis_u1(L, L, w.beta, w.sweeps, w.gauge_seed)
+        fname, lattice = f"mass_{w.Lx}_at{L}.json", f"{L}x{L}"
+    m0 = at if at is not None else tune(theta, target)[0]
+    s = sigma_min(wilson.wilson_dirac(theta, m0))
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden", fname)
     with open(out, "w") as f:
-        json.dump({"workload": name, "target_sigma_min": target, "m0": round(m0, 6),
+        json.dump({"workload": name, "tuned_on": lattice, "target_sigma_min": target, "m0": round(m0, 6),
                    "sigma_min": s, "written_by": "python -m oracle.tune_mass"}, f, indent=1)
     print(out, m0, s)
 

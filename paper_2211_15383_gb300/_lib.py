@@ -34,7 +34,7 @@ class MgmlmcError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("mg_precision", C.c_int), ("solve_tol", C.c_double), ("fgmres_restart", C.c_int),
                 ("max_iters", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
-                ("max_block_rhs", C.c_int), ("verbose", C.c_int)]
+                ("max_block_rhs", C.c_int), ("verbose", C.c_int), ("kcycle_iters", C.c_int)]
 
 
 class LevelStats(C.Structure):
@@ -62,13 +62,23 @@ class Request(C.Structure):
                 ("nvec", C.c_int * MAX_LEVELS), ("start_vectors", C.POINTER(C.c_double) * MAX_LEVELS),
                 ("setup_iters", C.c_int), ("setup_tol", C.c_double), ("k", C.c_int), ("defl_tol", C.c_double),
                 ("defl_max_iters", C.c_int), ("rel_tol", C.c_double), ("max_samples", C.c_int64),
-                ("seed", C.c_uint64), ("costs", C.c_double * MAX_LEVELS), ("opt", Options)]
+                ("seed", C.c_uint64), ("costs", C.c_double * MAX_LEVELS), ("opt", Options),
+                ("sum_levels", C.c_int)]
 
 
 class RequestResult(C.Structure):
     _fields_ = [("status", C.c_int), ("result", TraceResult), ("queued_s", C.c_double), ("setup_s", C.c_double),
                 ("estimate_s", C.c_double), ("total_s", C.c_double), ("reserved_bytes", C.c_size_t),
                 ("peak_bytes", C.c_size_t), ("retries", C.c_int), ("error", C.c_char * 160)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("block_rhs", C.c_int), ("fgmres_restart", C.c_int), ("nu_post", C.c_int),
+                ("kcycle_iters", C.c_int), ("samples_per_s", C.c_double), ("footprint", C.c_size_t),
+                ("budget", C.c_size_t), ("trials", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ServerStats(C.Structure):
@@ -99,6 +109,8 @@ SIGNATURES = [
     ("mgmlmc_get_deflation", C.c_int, [_P, _D, _D, _D, _D, _D]),
     ("mgmlmc_compute_term_deflation", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int]),
     ("mgmlmc_get_term_deflation", C.c_int, [_P, C.c_int, _I, _D, _D, _D, _D]),
+    ("mgmlmc_term_deflated_part", C.c_int, [_P, C.c_int, _D]),
+    ("mgmlmc_autotune", C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(TuneResult)]),
     ("mgmlmc_compute_term_deflation_inexact", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int]),
     ("mgmlmc_set_term_deflation_vectors", C.c_int, [_P, C.c_int, C.c_int, _D]),
     ("mgmlmc_estimate_level", C.c_int, [_P, C.c_int, C.c_int64, C.c_int, C.c_uint64, _D, C.POINTER(LevelStats)]),
@@ -377,6 +389,19 @@ class Context:
         return lam, L, R, complex(tau[0], tau[1])
 
     # ---------------------------------------------------------------- estimation
+    def autotune(self, hbm_budget: int = 0, max_trials: int = 10) -> dict:
+        r = TuneResult()
+        self._check(self.lib.mgmlmc_autotune(self.h, int(hbm_budget), int(max_trials), C.byref(r)))
+        for k in ("fgmres_restart", "nu_post", "kcycle_iters"):
+            setattr(self.options, k, getattr(r, k))
+        self.options.max_block_rhs = r.block_rhs
+        return r.as_dict()
+
+    def term_deflated_part(self, term: int) -> complex:
+        tau = np.zeros(2)
+        self._check(self.lib.mgmlmc_term_deflated_part(self.h, term, _dptr(tau)))
+        return complex(tau[0], tau[1])
+
     def estimate_level(self, term: int, first: int, nsamples: int, seed: int, samples: bool = True):
         out = np.zeros(nsamples, np.complex128) if samples else None
         st = LevelStats()
@@ -468,7 +493,8 @@ class Context:
 # ------------------------------------------------------------------------- serving
 def make_request(theta, m0: float, agg, nvec, start_vectors, rel_tol: float, seed: int, k: int = 0,
                  setup_iters: int = 4, setup_tol: float = 1e-12, defl_tol: float = 1e-9, defl_max_iters: int = 400,
-                 max_samples: int = 1 << 40, costs=None, options: Options | None = None, **kw):
+                 max_samples: int = 1 << 40, costs=None, options: Options | None = None, sum_levels: int = 0,
+                 **kw):
     """A trace request (mgmlmc_request) for Server.submit.  theta [Lt][Lx][2], agg a list
     of (ax, at) per coarse level, start_vectors one complex array (nvec, n_l) per coarse
     level; costs: fixed per-sample costs of the terms (None: measured device time).
@@ -492,6 +518,7 @@ def make_request(theta, m0: float, agg, nvec, start_vectors, rel_tol: float, see
     for t, c in enumerate(costs or []):
         r.costs[t] = float(c)
     r.opt = options if options is not None else default_options(**kw)
+    r.sum_levels = int(sum_levels)
     r._keep = keep
     return r
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "context.h"
+#include "footprint.h"
 
 using mg::Ctx;
 using mg::Error;
@@ -46,6 +47,7 @@ void check_options(const mgmlmc_options& o) {
     MG_REQUIRE(o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_pre + o.nu_post <= 64, MGMLMC_EINVAL,
                "options: smoothing steps");
     MG_REQUIRE(o.max_block_rhs >= 1 && o.max_block_rhs <= 4096, MGMLMC_EINVAL, "options: 1 <= max_block_rhs <= 4096");
+    MG_REQUIRE(o.kcycle_iters >= 0 && o.kcycle_iters <= 16, MGMLMC_EINVAL, "options: 0 <= kcycle_iters <= 16");
 }
 
 }  // namespace mg
@@ -101,7 +103,16 @@ bool run_term_block(Ctx& c, const TermLevels& tl, const double2* X, int Nb, doub
         mg::launch_dot<double2, double2>(s2, Ycur, W, Lb.n, Nb, part2, c.stream);
         mg::launch_axpy_rhs<double2, double2>(smp, nullptr, nullptr, -1.0, s2, 1, Nb, c.stream);
     }
-    if (tl.defl) {
+    if (tl.defl && tl.defl->W16) {
+        // tensor cores: BF16 factors, FP32 accumulation; algorithmic traffic = the BF16
+        // factors once + the probe block (FP64) once, flops 8 n k N
+        const mg::Deflation& D = *tl.defl;
+        void* scr = c.scratch_bytes("est_tcd", mg::deflation_bf16_scratch(La.n, D.k, Nb));
+        mg::ProfScope ps(c, "defl.bf16", (double)mg::tc_deflation_rows(D.k) * La.n * 2 + (double)La.n * Nb * 16,
+                         8.0 * La.n * D.k * Nb);
+        mg::launch_deflation_correction_bf16(smp, X, D.W16, D.a, La.n, D.k, Nb, scr, mg::device_error_flag(c),
+                                             c.stream);
+    } else if (tl.defl) {
         const mg::Deflation& D = *tl.defl;
         const int k = D.k;
         double2* A = c.scratch<double2>("est_A", (size_t)k * Nb);
@@ -214,6 +225,7 @@ void mgmlmc_default_options(mgmlmc_options* o) {
     o->nu_post = 4;
     o->max_block_rhs = 256;
     o->verbose = 0;
+    o->kcycle_iters = 0;
 }
 
 int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream, mgmlmc_alloc_fn alloc,
@@ -386,11 +398,20 @@ int mgmlmc_get_term_deflation(mgmlmc_ctx* h, int term, int* k, double* lambda, d
     API_END
 }
 
+int mgmlmc_term_deflated_part(mgmlmc_ctx* h, int term, double* tau) {
+    API_BEGIN(h)
+    MG_REQUIRE(tau, MGMLMC_EINVAL, "term_deflated_part: tau is NULL");
+    const TermLevels tl = term_levels(c, term);
+    tau[0] = tl.defl ? tl.defl->tau_used_re() : 0.0;
+    tau[1] = tl.defl ? tl.defl->tau_used_im() : 0.0;
+    API_END
+}
+
 int mgmlmc_get_deflation(mgmlmc_ctx* h, double* lambda, double* sigma, double* U, double* V, double* tau) {
     API_BEGIN(h)
     const int k = c.defl.k;
     MG_REQUIRE(k > 0, MGMLMC_ESTATE, "get_deflation: no deflation computed");
-    const long long n = c.lev[c.L - 1].n;
+    const long long n = c.lev[c.defl.fine].n;   // the level of the last term (the coarsest unless skipped)
     for (int i = 0; i < k; ++i) {
         const double li = i < (int)c.defl.lambda.size() ? c.defl.lambda[i] : 0.0;
         if (lambda) lambda[i] = li;
@@ -552,8 +573,8 @@ void mlmc_loop(const std::vector<Ctx*>& ctx_of, bool concurrent, double rel_tol,
     for (int t = 0; t < T; ++t) {
         const TermLevels tl = term_levels(*ctx_of[t], t);
         if (tl.defl) {
-            tau_re += tl.defl->tau_re;
-            tau_im += tl.defl->tau_im;
+            tau_re += tl.defl->tau_used_re();
+            tau_im += tl.defl->tau_used_im();
         }
     }
     bool converged = false;
@@ -794,3 +815,151 @@ int mgmlmc_level_info(const mgmlmc_ctx* h, int level, int* lx, int* lt, int* d, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------
+// Autotuner (no counterpart in the paper; it picks how the estimator's blocks are
+// cut and solved on this GPU).  A candidate is (block width N, FGMRES restart m,
+// post-smoothing steps nu, K-cycle steps); the device-memory model of the
+// context's shape (footprint.h) discards those that exceed the HBM budget, and the
+// rest are timed on one block of N samples of every term (the same Z2 noise each
+// time, CUDA events on the context's stream).  Coordinate search: the widest
+// blocks first, then the restart length, the smoother steps and the coarse-grid
+// correction.  The fastest setting by samples per second becomes the context's.
+namespace {
+
+mg::Shape context_shape(const Ctx& c) {
+    mg::Shape s;
+    s.L = c.L;
+    s.nterm_levels = c.term_level[c.nterms - 1] + 1;
+    for (int l = 0; l < c.L; ++l) {
+        s.sites[l] = c.lev[l].nsites;
+        s.n[l] = c.lev[l].n;
+        s.d[l] = c.lev[l].d;
+        s.nvec[l] = c.lev[l].nvec;
+    }
+    s.k = c.defl.k;
+    s.precision = c.opt.mg_precision;
+    return s;
+}
+
+void release_scratch(Ctx& c) {
+    c.sync();
+    for (auto& kv : c.ws) c.dev_free(kv.second.p);
+    c.ws.clear();
+    c.dev_err = nullptr;
+}
+
+}  // namespace
+
+extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials, mgmlmc_tune_result* out) {
+    API_BEGIN(h)
+    MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "autotune: no hierarchy");
+    MG_REQUIRE(out && max_trials >= 1, MGMLMC_EINVAL, "autotune: bad argument");
+    size_t free_b = 0, total_b = 0;
+    MG_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)(free_b + c.live_bytes));
+    mg::Shape base = context_shape(c);
+    const mgmlmc_options start = c.opt;
+    struct Cand {
+        int N, m, nu, kc;
+    };
+    auto fits = [&](const Cand& q, size_t* bytes) {
+        mg::Shape s = base;
+        s.N = q.N;
+        s.m = q.m;
+        s.kcycle = q.kc;
+        const size_t b = mg::footprint_bytes(s);
+        if (bytes) *bytes = b;
+        return b <= budget;
+    };
+    const uint64_t kSeed = 0x2211153839ull;
+    int trials = 0, last_N = -1;
+    double best_rate = -1;
+    Cand best{start.max_block_rhs, start.fgmres_restart, start.nu_post, start.kcycle_iters};
+    auto time_one = [&](const Cand& q) -> double {
+        c.opt.max_block_rhs = q.N;
+        c.opt.fgmres_restart = q.m;
+        c.opt.nu_post = q.nu;
+        c.opt.kcycle_iters = q.kc;
+        auto run_all = [&]() {
+            long long iters = 0;
+            for (int t = 0; t < c.nterms; ++t) {
+                const TermLevels tl = term_levels(c, t);
+                const long long n = c.lev[tl.a].n;
+                double2* X = c.scratch<double2>("tune_X", (size_t)n * q.N);
+                double2* smp = c.scratch<double2>("tune_smp", (size_t)q.N);
+                mg::launch_noise<double2>(X, n, q.N, kSeed, (uint64_t)(tl.a + 1), 0, c.stream);
+                MG_REQUIRE(run_term_block(c, tl, X, q.N, smp, &iters), MGMLMC_ENOTCONVERGED,
+                           "autotune: a trial solve did not converge");
+            }
+        };
+        if (q.N != last_N) {                    // work space of this width: allocate untimed
+            release_scratch(c);
+            run_all();
+            last_N = q.N;
+        }
+        cudaEvent_t e0, e1;
+        MG_CUDA(cudaEventCreate(&e0));
+        MG_CUDA(cudaEventCreate(&e1));
+        MG_CUDA(cudaEventRecord(e0, c.stream));
+        run_all();
+        MG_CUDA(cudaEventRecord(e1, c.stream));
+        c.sync();
+        float ms = 0;
+        MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ++trials;
+        const double rate = (double)c.nterms * q.N / (ms * 1e-3);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = q;
+        }
+        return rate;
+    };
+    try {
+        // 1. block width: the widest that fit, at the current restart length
+        std::vector<int> widths;
+        for (int N : {1024, 512, 256, 128, 64, 32}) {
+            Cand q{N, start.fgmres_restart, start.nu_post, start.kcycle_iters};
+            if (fits(q, nullptr)) widths.push_back(N);
+        }
+        MG_REQUIRE(!widths.empty(), MGMLMC_ENOMEM, "autotune: no block width fits the budget");
+        for (size_t i = 0; i < widths.size() && i < 3 && trials < max_trials; ++i)
+            time_one(Cand{widths[i], start.fgmres_restart, start.nu_post, start.kcycle_iters});
+        // 2. restart length, 3. smoother steps, 4. coarse-grid correction
+        for (int m : {8, 16, 24}) {
+            Cand q{best.N, m, best.nu, best.kc};
+            if (m != best.m && trials < max_trials && fits(q, nullptr)) time_one(q);
+        }
+        for (int nu : {2, 6}) {
+            Cand q{best.N, best.m, nu, best.kc};
+            if (nu != best.nu && trials < max_trials) time_one(q);
+        }
+        if (c.L >= 4) {
+            Cand q{best.N, best.m, best.nu, best.kc > 0 ? 0 : 2};
+            if (trials < max_trials && fits(q, nullptr)) time_one(q);
+        }
+    } catch (...) {
+        c.opt = start;
+        release_scratch(c);
+        throw;
+    }
+    c.opt.max_block_rhs = best.N;
+    c.opt.fgmres_restart = best.m;
+    c.opt.nu_post = best.nu;
+    c.opt.kcycle_iters = best.kc;
+    release_scratch(c);
+    out->block_rhs = best.N;
+    out->fgmres_restart = best.m;
+    out->nu_post = best.nu;
+    out->kcycle_iters = best.kc;
+    out->samples_per_s = best_rate;
+    size_t fb = 0;
+    fits(best, &fb);
+    out->footprint = fb;
+    out->budget = budget;
+    out->trials = trials;
+    API_END
+}
+

@@ -52,6 +52,13 @@ struct Deflation {
     double* a = nullptr;             // [k] 1/sigma
     std::vector<double> lambda;      // eigenvalues of Q_L
     double tau_re = 0, tau_im = 0;   // tr(V Sigma^{-1} U^H)
+    // mg_precision 16: the factors rounded to BF16 for the tensor-core projections
+    // (W^T = [Re R | -Im R | Re L | -Im L]^T, pre-tiled) and the deflated trace of
+    // exactly those rounded factors, which the estimate then adds
+    __nv_bfloat16* W16 = nullptr;
+    double tau16_re = 0, tau16_im = 0;
+    double tau_used_re() const { return W16 ? tau16_re : tau_re; }
+    double tau_used_im() const { return W16 ? tau16_im : tau_im; }
 };
 
 struct TermStats {
@@ -169,6 +176,8 @@ void approx_inverse(Ctx& c, int l, const double2* b, double2* x, int N);
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);
 // Throws MGMLMC_ETIMEOUT if a kernel with bounded waits recorded a timeout.
 void check_device_error(Ctx& c);
+// The context's device flag that kernels with bounded waits set when they give up.
+int* device_error_flag(Ctx& c);
 // d receives device copies of s's gauge field, mass, hierarchy, terms and deflations.
 void copy_state(Ctx& d, Ctx& s);
 // Throws MGMLMC_EINVAL for options outside their documented ranges.
@@ -197,6 +206,9 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
 void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k);
 // The deflation that applies to the term (a, b), or nullptr.
 const Deflation* term_deflation(const Ctx& c, int a, int b);
+// With mg_precision 16 and a supported level size: the BF16 copy of the factors and
+// the deflated trace over them (called whenever a deflation is stored).
+void prepare_tc_deflation(Ctx& c, Deflation& D);
 void upload_links(Ctx& c, const double* theta);
 
 }  // namespace mg

@@ -123,18 +123,34 @@ template <typename C>
 void launch_gemm_hn(double2* Cm, const C* A, const C* B, long long n, int ka, int kb, double2* part,
                     int groups, cudaStream_t s);
 int gemm_hn_groups(long long n, int ka, int kb);
+// The same two products with FP64 storage and FP32 arithmetic (the eigensolvers'
+// block operations on large levels; the partial sums of at most 16384 rows are
+// FP32, their sum FP64).  part: gemm_hn_fp32_groups(...) * ka * kb values.
+void launch_gemm_nn_fp32(double2* Cm, const double2* A, const double2* B, int M, int K, int Nc, cudaStream_t s);
+void launch_gemm_hn_fp32(double2* Cm, const double2* A, const double2* B, long long n, int ka, int kb,
+                         double2* part, int groups, cudaStream_t s);
+int gemm_hn_fp32_groups(long long n, int ka, int kb);
 // In-place Gauss-Jordan inverse of a dense complex n x n matrix (partial pivoting).
 // work: n doubles + n ints + a few scalars.  Returns via *status_dev 0 ok, 1 singular.
 template <typename C>
 void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s);
 size_t gauss_jordan_work_bytes(int n);
-// Hermitian eigenproblem of a small b x b matrix (cyclic Jacobi, one CTA):
-// H is overwritten; W receives eigenvectors (columns), lam eigenvalues.
-void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s,
+// Hermitian eigenproblem of a b x b matrix (b <= 2048; cyclic Jacobi in one
+// cooperative kernel over all SMs, round-robin pairs, one bounded grid barrier per
+// round): H is read, W receives the eigenvectors (columns) and lam the eigenvalues,
+// sorted by increasing |lambda| (decreasing with descending).  work: at least
+// jacobi_work_bytes(b), 256-byte aligned.  err (may be null) is set to 1 if a grid
+// barrier gave up waiting.
+void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, void* work, int* err, cudaStream_t s,
                        bool descending = false);
-// G (b x b, Hermitian positive definite) = R^H R; G is overwritten by R (upper),
-// Rinv = R^{-1}.  status[0] = 1 if G was not positive definite.
-void launch_cholesky_inv(double2* G, double2* Rinv, int b, int* status, cudaStream_t s);
+size_t jacobi_work_bytes(int b);
+size_t jacobi_smem_bytes(int b);
+// G (b x b, Hermitian positive definite) = R^H R; Rinv = R^{-1} (upper triangular),
+// one cooperative kernel over all SMs (G is overwritten).  status[0] = 1 if G was
+// not positive definite; err (may be null) = 1 if a grid barrier gave up waiting.
+// work: cholesky_work_bytes(b).
+size_t cholesky_work_bytes(int b);
+void launch_cholesky_inv(double2* G, double2* Rinv, int b, void* work, int* status, int* err, cudaStream_t s);
 // BF16 real embedding [Re A | Im A] (n x 2n) of a complex FP32 n x n matrix for the
 // tensor-core coarsest solve.
 void launch_embed_bf16(__nv_bfloat16* E, const float2* A, int n, cudaStream_t s);
@@ -144,6 +160,19 @@ bool tc_coarse_supported(int n);
 void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16* E, int n, int N,
                                 void* scratch, int* err, cudaStream_t s);
 size_t coarse_inverse_bf16_scratch(int n, int N);
+// Deflation projections on the tensor cores: W (tc_deflation_rows(k) x n BF16,
+// pre-tiled) holds [Re R | -Im R | Re L | -Im L]^T of the deflation's factors
+// R, L [n][k]; launch_deflation_correction_bf16 forms A = R^H X and B = L^H X for
+// a real block X [n][N] (FP32 accumulation) and does s[j] -= sum_m a_m conj(B) A.
+// t[m] = R~_m^H L~_m over the BF16-rounded factors (FP64 sums).
+bool tc_deflation_supported(long long n, int k);
+int tc_deflation_rows(int k);
+void launch_embed_deflation_bf16(__nv_bfloat16* W, const double2* R, const double2* L, long long n, int k,
+                                 cudaStream_t s);
+void launch_deflation_tau_bf16(double2* t, const double2* R, const double2* L, long long n, int k, cudaStream_t s);
+size_t deflation_bf16_scratch(long long n, int k, int N);
+void launch_deflation_correction_bf16(double2* smp, const double2* X, const __nv_bfloat16* W, const double* a,
+                                      long long n, int k, int N, void* scratch, int* err, cudaStream_t s);
 // Coarse block stencil (d = 16) on the tensor cores for the block-Jacobi
 // smoother: E holds the blocks of every site and direction as BF16 real 32 x 32
 // operands (launch_embed_stencil_bf16); the input x is given as BF16 tiles

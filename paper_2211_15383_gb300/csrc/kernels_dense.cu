@@ -3,6 +3,8 @@
 // cyclic Jacobi eigensolver for the small Hermitian Rayleigh-Ritz problems of
 // the deflation setup.  FP64 instances run on the FP64 pipe, FP32 on the FP32
 // pipe; the BF16 tensor-core coarsest solve lives in kernels_tc.cu.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace mg {
@@ -12,9 +14,9 @@ namespace mg {
 // ty*8 .. ty*8+7.  All threads of a warp share ty, so A reads are broadcasts.
 constexpr int GM = 64, GN = 32, GK = 16;
 
-template <typename C>
-__global__ void __launch_bounds__(256) k_gemm_nn(C* __restrict__ Cm, const C* __restrict__ A,
-                                                 const C* __restrict__ B, int M, int K, int Nc, bool accumulate) {
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_gemm_nn(S* __restrict__ Cm, const S* __restrict__ A,
+                                                 const S* __restrict__ B, int M, int K, int Nc, bool accumulate) {
     __shared__ C As[GM][GK + 1];
     __shared__ C Bs[GK][GN];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -26,12 +28,12 @@ __global__ void __launch_bounds__(256) k_gemm_nn(C* __restrict__ Cm, const C* __
         for (int e = tid; e < GM * GK; e += 256) {
             const int r = e / GK, k = e % GK;
             const int gr = row0 + r, gk = k0 + k;
-            As[r][k] = (gr < M && gk < K) ? A[(long long)gr * K + gk] : czero<C>();
+            As[r][k] = (gr < M && gk < K) ? cvtc(A[(long long)gr * K + gk], C{}) : czero<C>();
         }
         for (int e = tid; e < GK * GN; e += 256) {
             const int k = e / GN, c = e % GN;
             const int gk = k0 + k, gc = col0 + c;
-            Bs[k][c] = (gk < K && gc < Nc) ? B[(long long)gk * Nc + gc] : czero<C>();
+            Bs[k][c] = (gk < K && gc < Nc) ? cvtc(B[(long long)gk * Nc + gc], C{}) : czero<C>();
         }
         __syncthreads();
 #pragma unroll
@@ -49,7 +51,8 @@ __global__ void __launch_bounds__(256) k_gemm_nn(C* __restrict__ Cm, const C* __
         const int gr = row0 + ty * 8 + r;
         if (gr < M) {
             const long long idx = (long long)gr * Nc + gc;
-            Cm[idx] = accumulate ? cadd(Cm[idx], acc[r]) : acc[r];
+            const S v = cvtc(acc[r], S{});
+            Cm[idx] = accumulate ? cadd(Cm[idx], v) : v;
         }
     }
 }
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(128) k_gemm_nn8(C* __restrict__ Cm, const C* _
 
 template <typename C>
 void launch_gemm_nn(C* Cm, const C* A, const C* B, int M, int K, int Nc, bool accumulate, cudaStream_t s) {
+    MG_REQUIRE((M + 15) / 16 <= 65535 || (Nc > 8 && (M + GM - 1) / GM <= 65535), MGMLMC_EINVAL, "gemm_nn: M too large");
     if (Nc <= 8) {
         dim3 g(1, (M + 15) / 16);
         k_gemm_nn8<C><<<g, dim3(8, 16), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
@@ -98,16 +102,22 @@ void launch_gemm_nn(C* Cm, const C* A, const C* B, int M, int K, int Nc, bool ac
         return;
     }
     dim3 g((Nc + GN - 1) / GN, (M + GM - 1) / GM);
-    k_gemm_nn<C><<<g, dim3(32, 8), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
+    k_gemm_nn<C, C><<<g, dim3(32, 8), 0, s>>>(Cm, A, B, M, K, Nc, accumulate);
+    MG_LAUNCHED();
+}
+
+void launch_gemm_nn_fp32(double2* Cm, const double2* A, const double2* B, int M, int K, int Nc, cudaStream_t s) {
+    dim3 g((Nc + GN - 1) / GN, (M + GM - 1) / GM);
+    k_gemm_nn<double2, float2><<<g, dim3(32, 8), 0, s>>>(Cm, A, B, M, K, Nc, false);
     MG_LAUNCHED();
 }
 
 // ------------------------------------------------------------------ GEMM hn
 // part[g][a][b] = sum_{i in slice g} conj(A[i][a]) B[i][b]; tile 32 x 32, thread
 // (tx = b, ty) owns a = ty*4 .. ty*4+3.
-template <typename C>
-__global__ void __launch_bounds__(256) k_gemm_hn(double2* __restrict__ part, const C* __restrict__ A,
-                                                 const C* __restrict__ B, long long n, int ka, int kb,
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_gemm_hn(double2* __restrict__ part, const S* __restrict__ A,
+                                                 const S* __restrict__ B, long long n, int ka, int kb,
                                                  long long slice) {
     __shared__ C As[16][33];
     __shared__ C Bs[16][33];
@@ -123,8 +133,8 @@ __global__ void __launch_bounds__(256) k_gemm_hn(double2* __restrict__ part, con
         for (int e = tid; e < 16 * 32; e += 256) {
             const int ii = e / 32, c = e % 32;
             const long long gi = i0 + ii;
-            As[ii][c] = (gi < i_end && a0 + c < ka) ? A[gi * ka + a0 + c] : czero<C>();
-            Bs[ii][c] = (gi < i_end && b0 + c < kb) ? B[gi * kb + b0 + c] : czero<C>();
+            As[ii][c] = (gi < i_end && a0 + c < ka) ? cvtc(A[gi * ka + a0 + c], C{}) : czero<C>();
+            Bs[ii][c] = (gi < i_end && b0 + c < kb) ? cvtc(B[gi * kb + b0 + c], C{}) : czero<C>();
         }
         __syncthreads();
 #pragma unroll
@@ -159,7 +169,25 @@ void launch_gemm_hn(double2* Cm, const C* A, const C* B, long long n, int ka, in
     long long slice = (n + groups - 1) / groups;
     slice = ((slice + 15) / 16) * 16;
     dim3 g((kb + 31) / 32, (ka + 31) / 32, groups);
-    k_gemm_hn<C><<<g, dim3(32, 8), 0, s>>>(part, A, B, n, ka, kb, slice);
+    k_gemm_hn<C, C><<<g, dim3(32, 8), 0, s>>>(part, A, B, n, ka, kb, slice);
+    MG_LAUNCHED();
+    launch_finalize(Cm, part, groups, ka * kb, s);
+}
+
+// FP32 arithmetic on FP64 storage: each group's slice of rows is summed in FP32, the
+// group partials in FP64.
+int gemm_hn_fp32_groups(long long n, int ka, int kb) {
+    const long long tiles = (long long)((ka + 31) / 32) * ((kb + 31) / 32);
+    long long g = (4LL * kNumSM + tiles - 1) / tiles;
+    g = std::max(g, (n + 16383) / 16384);                  // at most 16384 rows summed in FP32
+    return (int)std::min(g, (n + 63) / 64);
+}
+void launch_gemm_hn_fp32(double2* Cm, const double2* A, const double2* B, long long n, int ka, int kb,
+                         double2* part, int groups, cudaStream_t s) {
+    long long slice = (n + groups - 1) / groups;
+    slice = ((slice + 15) / 16) * 16;
+    dim3 g((kb + 31) / 32, (ka + 31) / 32, groups);
+    k_gemm_hn<double2, float2><<<g, dim3(32, 8), 0, s>>>(part, A, B, n, ka, kb, slice);
     MG_LAUNCHED();
     launch_finalize(Cm, part, groups, ka * kb, s);
 }
@@ -372,188 +400,364 @@ void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------- Jacobi eigen
-// Cyclic Jacobi for a Hermitian b x b matrix H (row-major, global memory), one
-// CTA.  Rounds of b/2 disjoint (p, q) pairs in round-robin order; each pair's
-// rotation G = diag(1, e^{-i phi}) [[c, s], [-s, c]] removes H[p][q] = |h| e^{i phi}
-// with (c, s) from the symmetric 2x2 Schur decomposition (tau = (h_qq - h_pp)/(2|h|),
-// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c).
-// Eigenvalues are returned sorted by increasing |lambda| (decreasing with
-// descending = 1), eigenvectors in the matching columns of W.
-__global__ void __launch_bounds__(1024) k_jacobi(double2* H, double2* W, double* lam, int b, int sweeps,
-                                                int descending) {
-    extern __shared__ double sm_jac[];
-    const int bp = b + (b & 1);                  // padded to even
-    int* order = reinterpret_cast<int*>(sm_jac);               // bp
-    double* cs = sm_jac + (bp + 1) / 2 + 1;                      // bp/2
-    double* sn = cs + bp / 2;                                    // bp/2
-    double* ph_re = sn + bp / 2;                                 // bp/2
-    double* ph_im = ph_re + bp / 2;                              // bp/2
-    __shared__ double offn, totn;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < b * b; e += nt) W[e] = make_double2((e / b) == (e % b) ? 1.0 : 0.0, 0.0);
-    for (int i = tid; i < bp; i += nt) order[i] = i;
+// Cyclic Jacobi for a Hermitian b x b matrix H (row-major), one persistent
+// cooperative kernel over the whole GPU.  A sweep is bp - 1 rounds (bp = b padded
+// to even) of bp/2 disjoint index pairs in round-robin order: in round r pair k is
+// (ord(k), ord(bp-1-k)) with ord(0) = 0 and ord(i) = 1 + (i - 1 + r) mod (bp - 1).
+// Pair (p, q) gets the rotation G = diag(1, e^{-i phi}) [[c, s], [-s, c]] that
+// removes H[p][q] = |h| e^{i phi}, with (c, s) from the symmetric 2x2 Schur
+// decomposition (tau = (h_qq - h_pp)/(2|h|), t = sign(tau)/(|tau| + sqrt(1 + tau^2)),
+// c = 1/sqrt(1+t^2), s = t c).  Since the pairs of a round are disjoint, the whole
+// round is H <- J^H H J with J block diagonal in the pairing: every 2x2 block (P, Q)
+// of the pairing becomes G_P^H H(P, Q) G_Q, computed from a read-only copy of H
+// (double buffer), and W(:, P) <- W(:, P) G_P in place.  One grid barrier per round.
+// The sweeps stop when the off-diagonal Frobenius norm is below 1e-15 of the total.
+// Eigenvalues come back sorted by increasing |lambda| (decreasing with descending),
+// eigenvectors in the matching columns of W.
+namespace jac {
+constexpr int kThreads = 256;
+constexpr long long kSpinLimit = 1LL << 24;   // x ~64 ns sleep: a barrier gives up after ~1 s
+
+struct Sync {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+// Grid barrier for a cooperative launch (all CTAs resident); bounded wait: a CTA that
+// waits too long records the failure and every CTA leaves at its next check.
+__device__ __forceinline__ bool grid_barrier(Sync* sy, unsigned nblocks) {
+    __shared__ int ok;
     __syncthreads();
-    for (int sw = 0; sw < sweeps; ++sw) {
-        // convergence test: off-diagonal Frobenius norm vs total
-        if (tid == 0) { offn = 0; totn = 0; }
-        __syncthreads();
-        double lo = 0, lt_ = 0;
-        for (int e = tid; e < b * b; e += nt) {
-            const double2 v = H[e];
-            const double m = v.x * v.x + v.y * v.y;
-            lt_ += m;
-            if ((e / b) != (e % b)) lo += m;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &sy->gen;
+        volatile int* verr = &sy->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&sy->count, 1u);
+        if (arrived == nblocks - 1) {
+            sy->count = 0;
+            __threadfence();
+            atomicAdd(&sy->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g && *verr == 0) {
+                if (++spins > kSpinLimit) {
+                    atomicExch(&sy->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
-        atomicAdd(&offn, lo);
-        atomicAdd(&totn, lt_);
+        __threadfence();
+        ok = (*verr == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ int ord(int i, int r, int bp) { return i == 0 ? 0 : 1 + (i - 1 + r) % (bp - 1); }
+
+__global__ void __launch_bounds__(kThreads) k_jacobi_grid(const double2* __restrict__ Hin, double2* A0, double2* A1,
+                                                          double2* Wp, double* part, Sync* sy, int b, int bp,
+                                                          int sweeps) {
+    extern __shared__ double sm_rot[];
+    const int half = bp / 2;
+    double* rc = sm_rot;                  // half each: c, s, Re e^{i phi}, Im e^{i phi}
+    double* rs = rc + half;
+    double* rpr = rs + half;
+    double* rpi = rpr + half;
+    int* rp = reinterpret_cast<int*>(rpi + half);   // pair indices p < q
+    int* rq = rp + half;
+    __shared__ double red_off[kThreads], red_tot[kThreads];
+    __shared__ int stop;
+    const unsigned G = gridDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)G * blockDim.x;
+    const long long bb = (long long)bp * bp;
+    for (long long e = tid; e < bb; e += nthr) {
+        const int i = (int)(e / bp), j = (int)(e % bp);
+        A0[e] = (i < b && j < b) ? Hin[(long long)i * b + j] : make_double2(0.0, 0.0);
+        Wp[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    if (!grid_barrier(sy, G)) return;
+    double2* cur = A0;
+    double2* nxt = A1;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        double lo = 0.0, lt = 0.0;
+        for (long long e = tid; e < bb; e += nthr) {
+            const double2 v = __ldcg(cur + e);
+            const double m = v.x * v.x + v.y * v.y;
+            lt += m;
+            if (e / bp != e % bp) lo += m;
+        }
+        red_off[threadIdx.x] = lo;
+        red_tot[threadIdx.x] = lt;
         __syncthreads();
-        if (offn <= 1e-30 * totn) break;
-        for (int round = 0; round < bp - 1; ++round) {
-            // pair k: (order[k], order[bp-1-k])
-            for (int k = tid; k < bp / 2; k += nt) {
-                int p = order[k], q = order[bp - 1 - k];
+        for (int st = kThreads / 2; st > 0; st >>= 1) {
+            if ((int)threadIdx.x < st) {
+                red_off[threadIdx.x] += red_off[threadIdx.x + st];
+                red_tot[threadIdx.x] += red_tot[threadIdx.x + st];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = red_off[0];
+            part[2 * blockIdx.x + 1] = red_tot[0];
+        }
+        if (!grid_barrier(sy, G)) return;
+        if (threadIdx.x == 0) {
+            double off = 0.0, tot = 0.0;       // same order in every CTA: the same decision
+            for (unsigned g2 = 0; g2 < G; ++g2) {
+                off += __ldcg(part + 2 * g2);
+                tot += __ldcg(part + 2 * g2 + 1);
+            }
+            stop = (off <= 1e-30 * tot);
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int r = 0; r < bp - 1; ++r) {
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int p = ord(k, r, bp), q = ord(bp - 1 - k, r, bp);
                 if (p > q) { const int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0, pr = 1.0, pi = 0.0;
+                double c = 1.0, sn = 0.0, pr = 1.0, pi = 0.0;
                 if (q < b) {
-                    const double2 hpq = H[p * b + q];
+                    const double2 hpq = __ldcg(cur + (long long)p * bp + q);
                     const double a = sqrt(hpq.x * hpq.x + hpq.y * hpq.y);
                     if (a > 0.0) {
-                        const double hpp = H[p * b + p].x, hqq = H[q * b + q].x;
+                        const double hpp = __ldcg(cur + (long long)p * bp + p).x;
+                        const double hqq = __ldcg(cur + (long long)q * bp + q).x;
                         const double tau = (hqq - hpp) / (2.0 * a);
                         const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
-                        pr = hpq.x / a;     // e^{i phi}
+                        sn = t * c;
+                        pr = hpq.x / a;
                         pi = hpq.y / a;
                     }
                 }
-                cs[k] = c; sn[k] = s; ph_re[k] = pr; ph_im[k] = pi;
+                rc[k] = c; rs[k] = sn; rpr[k] = pr; rpi[k] = pi; rp[k] = p; rq[k] = q;
             }
             __syncthreads();
-            // rows: [H_pj; H_qj] <- G^H [H_pj; H_qj],  G^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]
-            for (int e = tid; e < (bp / 2) * b; e += nt) {
-                const int k = e / b, jcol = e % b;
-                int p = order[k], q = order[bp - 1 - k];
-                if (p > q) { const int t = p; p = q; q = t; }
-                if (q >= b) continue;
-                const double c = cs[k], s = sn[k];
-                const double2 ph = make_double2(ph_re[k], ph_im[k]);
-                const double2 hp = H[p * b + jcol], hq = H[q * b + jcol];
-                const double2 phq = cmul(ph, hq);
-                H[p * b + jcol] = make_double2(c * hp.x - s * phq.x, c * hp.y - s * phq.y);
-                H[q * b + jcol] = make_double2(s * hp.x + c * phq.x, s * hp.y + c * phq.y);
+            // 2x2 blocks (P, Q): out = G_P^H B G_Q
+            const long long nblk = (long long)half * half;
+            for (long long e = tid; e < nblk; e += nthr) {
+                const int P = (int)(e / half), Q = (int)(e % half);
+                const int p1 = rp[P], q1 = rq[P], p2 = rp[Q], q2 = rq[Q];
+                const double c1 = rc[P], s1 = rs[P], c2 = rc[Q], s2 = rs[Q];
+                const double2 f1 = make_double2(rpr[P], rpi[P]);
+                const double2 f2c = make_double2(rpr[Q], -rpi[Q]);
+                // written by other CTAs in the previous round: read through L2, not L1
+                const double2 b00 = __ldcg(cur + (long long)p1 * bp + p2), b01 = __ldcg(cur + (long long)p1 * bp + q2);
+                const double2 b10 = __ldcg(cur + (long long)q1 * bp + p2), b11 = __ldcg(cur + (long long)q1 * bp + q2);
+                // rows: R0 = c1 B0 - s1 f1 B1, R1 = s1 B0 + c1 f1 B1
+                const double2 fb10 = cmul(f1, b10), fb11 = cmul(f1, b11);
+                const double2 r00 = make_double2(c1 * b00.x - s1 * fb10.x, c1 * b00.y - s1 * fb10.y);
+                const double2 r01 = make_double2(c1 * b01.x - s1 * fb11.x, c1 * b01.y - s1 * fb11.y);
+                const double2 r10 = make_double2(s1 * b00.x + c1 * fb10.x, s1 * b00.y + c1 * fb10.y);
+                const double2 r11 = make_double2(s1 * b01.x + c1 * fb11.x, s1 * b01.y + c1 * fb11.y);
+                // columns: O_i0 = c2 R_i0 - s2 conj(f2) R_i1, O_i1 = s2 R_i0 + c2 conj(f2) R_i1
+                const double2 g01 = cmul(r01, f2c), g11 = cmul(r11, f2c);
+                nxt[(long long)p1 * bp + p2] = make_double2(c2 * r00.x - s2 * g01.x, c2 * r00.y - s2 * g01.y);
+                nxt[(long long)p1 * bp + q2] = make_double2(s2 * r00.x + c2 * g01.x, s2 * r00.y + c2 * g01.y);
+                nxt[(long long)q1 * bp + p2] = make_double2(c2 * r10.x - s2 * g11.x, c2 * r10.y - s2 * g11.y);
+                nxt[(long long)q1 * bp + q2] = make_double2(s2 * r10.x + c2 * g11.x, s2 * r10.y + c2 * g11.y);
             }
-            __syncthreads();
-            // columns: [H_ip, H_iq] <- [H_ip, H_iq] G, G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]; same for W
-            for (int e = tid; e < (bp / 2) * b * 2; e += nt) {
-                const int which = e / ((bp / 2) * b);
-                const int e2 = e % ((bp / 2) * b);
-                const int k = e2 / b, i = e2 % b;
-                int p = order[k], q = order[bp - 1 - k];
-                if (p > q) { const int t = p; p = q; q = t; }
-                if (q >= b) continue;
-                double2* M = which ? W : H;
-                const double c = cs[k], s = sn[k];
-                const double2 phc = make_double2(ph_re[k], -ph_im[k]);
-                const double2 mp = M[i * b + p], mq = M[i * b + q];
-                const double2 mqp = cmul(mq, phc);
-                M[i * b + p] = make_double2(c * mp.x - s * mqp.x, c * mp.y - s * mqp.y);
-                M[i * b + q] = make_double2(s * mp.x + c * mqp.x, s * mp.y + c * mqp.y);
+            // eigenvectors: W(:, P) <- W(:, P) G_P, in place (disjoint columns)
+            const long long nw = (long long)bp * half;
+            for (long long e = tid; e < nw; e += nthr) {
+                const int i = (int)(e / half), P = (int)(e % half);
+                const int p = rp[P], q = rq[P];
+                const double c = rc[P], sn = rs[P];
+                const double2 fc = make_double2(rpr[P], -rpi[P]);
+                const double2 wp = __ldcg(Wp + (long long)i * bp + p);
+                const double2 wq = cmul(__ldcg(Wp + (long long)i * bp + q), fc);
+                Wp[(long long)i * bp + p] = make_double2(c * wp.x - sn * wq.x, c * wp.y - sn * wq.y);
+                Wp[(long long)i * bp + q] = make_double2(sn * wp.x + c * wq.x, sn * wp.y + c * wq.y);
             }
-            __syncthreads();
-            // round-robin: keep order[0], rotate the rest
-            if (tid == 0) {
-                const int last = order[bp - 1];
-                for (int i = bp - 1; i > 1; --i) order[i] = order[i - 1];
-                order[1] = last;
-            }
-            __syncthreads();
+            if (!grid_barrier(sy, G)) return;
+            double2* t = cur;
+            cur = nxt;
+            nxt = t;
         }
     }
-    __syncthreads();
-    // sort by |lambda| (rank sort), eigenvectors move with their eigenvalue; H is scratch
-    for (int i = tid; i < b; i += nt) lam[i] = H[i * b + i].x;
-    __syncthreads();
-    for (int e = tid; e < b * b; e += nt) H[e] = W[e];
-    __syncthreads();
-    for (int i = tid; i < b; i += nt) {
-        const double li = descending ? -fabs(lam[i]) : fabs(lam[i]);
-        int rank = 0;
-        for (int j2 = 0; j2 < b; ++j2) {
-            const double lj = descending ? -fabs(lam[j2]) : fabs(lam[j2]);
-            if (lj < li || (lj == li && j2 < i)) ++rank;
-        }
-        order[i] = rank;
-    }
-    __syncthreads();
-    double* lcopy = cs;   // reuse (needs b doubles: cs..ph_im hold 2*bp)
-    for (int i = tid; i < b; i += nt) lcopy[order[i]] = lam[i];
-    for (int e = tid; e < b * b; e += nt) {
-        const int row = e / b, col = e % b;
-        W[row * b + order[col]] = H[row * b + col];
-    }
-    __syncthreads();
-    for (int i = tid; i < b; i += nt) lam[i] = lcopy[i];
+    // the diagonal of the last matrix goes to part[0 .. b) for the sorting kernel
+    for (long long i = tid; i < b; i += nthr) part[2 * G + i] = __ldcg(cur + i * bp + i).x;
 }
 
-// Cholesky factor of a Hermitian positive definite b x b matrix G = R^H R (R upper,
-// right-looking outer-product form, in place in G), then Rinv = R^{-1} by
-// back-substitution, one column per thread.  One CTA; status[0] = 1 if a pivot is
-// not positive.
-__global__ void __launch_bounds__(1024) k_cholesky_inv(double2* G, double2* Rinv, int b, int* status) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+// rank of every eigenvalue by |lambda| (ties by index), then lam and the columns
+// of W permuted to that order; a barrier failure is passed to the caller's flag.
+__global__ void k_jacobi_rank(const double* diag, int* rank, int b, int descending) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= b) return;
+    const double lc = descending ? -fabs(diag[col]) : fabs(diag[col]);
+    int r = 0;
     for (int j = 0; j < b; ++j) {
-        if (tid == 0) {
-            double d = G[j * b + j].x;
-            if (!(d > 0.0)) {
-                *status = 1;
-                d = 1e-300;
-            }
-            G[j * b + j] = make_double2(sqrt(d), 0.0);
-        }
-        __syncthreads();
-        const double inv = 1.0 / G[j * b + j].x;
-        for (int i = j + 1 + tid; i < b; i += nt) G[j * b + i] = make_double2(G[j * b + i].x * inv, G[j * b + i].y * inv);
-        __syncthreads();
-        const int m = b - j - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int p = j + 1 + e / m, q = j + 1 + e % m;
-            if (q < p) continue;
-            const double2 rp = G[j * b + p], rq = G[j * b + q];
-            // G[p][q] -= conj(R[j][p]) R[j][q]
-            G[p * b + q] = make_double2(G[p * b + q].x - (rp.x * rq.x + rp.y * rq.y),
-                                        G[p * b + q].y - (rp.x * rq.y - rp.y * rq.x));
-        }
-        __syncthreads();
+        const double lj = descending ? -fabs(diag[j]) : fabs(diag[j]);
+        r += (lj < lc || (lj == lc && j < col)) ? 1 : 0;
     }
-    // Rinv: solve R z = e_c for each column c (upper triangular back substitution)
-    for (int c = tid; c < b; c += nt) {
-        for (int i = b - 1; i >= 0; --i) {
-            double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            if (i > c) acc = make_double2(0.0, 0.0);
-            for (int k = i + 1; k <= c; ++k) {
-                const double2 r = G[i * b + k], z = Rinv[k * b + c];
-                acc.x -= r.x * z.x - r.y * z.y;
-                acc.y -= r.x * z.y + r.y * z.x;
-            }
-            const double d = G[i * b + i].x;
-            Rinv[i * b + c] = (i > c) ? make_double2(0.0, 0.0) : make_double2(acc.x / d, acc.y / d);
+    rank[col] = r;
+}
+
+__global__ void k_jacobi_permute(const double* diag, const int* rank, const double2* Wp, double2* W, double* lam,
+                                 int b, int bp, const Sync* sy, int* err) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < (long long)b * b; e += nthr) {
+        const int row = (int)(e / b), col = (int)(e % b);
+        W[(long long)row * b + rank[col]] = Wp[(long long)row * bp + col];
+        if (row == 0) lam[rank[col]] = diag[col];
+    }
+    if (tid == 0 && err && sy->err) *err = 1;
+}
+}  // namespace jac
+
+static int jacobi_grid_size() {
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0, per = 0, coop = 0;
+        MG_CUDA(cudaGetDevice(&dev));
+        MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        MG_REQUIRE(coop, MGMLMC_ECUDA, "jacobi: the device does not support cooperative launches");
+        const size_t sm = jacobi_smem_bytes(2048);
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jac::k_jacobi_grid, jac::kThreads, sm));
+        MG_REQUIRE(per >= 1, MGMLMC_ECUDA, "jacobi: kernel cannot be resident");
+        g = sms;   // one CTA per SM: every CTA resident, as the grid barrier requires
+    }
+    return g;
+}
+
+size_t jacobi_smem_bytes(int b) {
+    const int bp = b + (b & 1);
+    return (size_t)(bp / 2) * (4 * sizeof(double) + 2 * sizeof(int));
+}
+
+size_t jacobi_work_bytes(int b) {
+    const size_t bp = (size_t)(b + (b & 1));
+    return 3 * bp * bp * sizeof(double2) + (2 * (size_t)kNumSM * 4 + bp) * sizeof(double) + 256 + bp * sizeof(int);
+}
+
+// Cholesky factor of a Hermitian positive definite b x b matrix G = R^H R (R upper)
+// and Rinv = R^{-1}, one cooperative kernel over all SMs.
+//  Factorisation, right-looking, one grid barrier per column j: every thread reads
+//  d = G[j][j] (final after the previous column), row j of R is G[j][.] / sqrt(d),
+//  and the trailing upper triangle takes G[p][q] -= conj(R[j][p]) R[j][q] (p, q > j),
+//  with R[j][.] formed on the fly from G's row j, which this column leaves untouched.
+//  Inverse, one warp per column c of T = R^{-1} (back substitution from i = c down,
+//  T[i][c] = (delta_ic - sum_{k>i} R[i][k] T[k][c]) / R[i][i], the sum split over the
+//  lanes); T is kept transposed (Tt[c][k], coalesced along k) and written out at the end.
+//  status[0] = 1 if a pivot was not positive (it is then replaced by 1e-300).
+namespace chol {
+__global__ void __launch_bounds__(jac::kThreads) k_cholesky_grid(double2* G, double2* Rinv, double2* R, double2* Tt,
+                                                                 int b, int* status, jac::Sync* sy) {
+    const unsigned NB = gridDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)NB * blockDim.x;
+    for (int j = 0; j < b; ++j) {
+        double d = __ldcg(G + (long long)j * b + j).x;
+        if (!(d > 0.0)) {
+            if (tid == 0) *status = 1;
+            d = 1e-300;
         }
+        const double rd = sqrt(d), inv = 1.0 / rd;
+        for (long long i = tid; i < b; i += nthr) {
+            double2 v = make_double2(0.0, 0.0);
+            if (i == j) v = make_double2(rd, 0.0);
+            else if (i > j) {
+                const double2 g = __ldcg(G + (long long)j * b + i);
+                v = make_double2(g.x * inv, g.y * inv);
+            }
+            R[(long long)j * b + i] = v;
+        }
+        const long long m = b - j - 1;
+        for (long long e = tid; e < m * m; e += nthr) {
+            const int p = j + 1 + (int)(e / m), q = j + 1 + (int)(e % m);
+            if (q < p) continue;
+            const double2 gp = __ldcg(G + (long long)j * b + p), gq = __ldcg(G + (long long)j * b + q);
+            const double2 g = __ldcg(G + (long long)p * b + q);
+            // conj(R[j][p]) R[j][q] = conj(gp) gq / d
+            G[(long long)p * b + q] = make_double2(g.x - (gp.x * gq.x + gp.y * gq.y) / d,
+                                                   g.y - (gp.x * gq.y - gp.y * gq.x) / d);
+        }
+        if (!jac::grid_barrier(sy, NB)) return;
+    }
+    const int lane = threadIdx.x & 31;
+    const long long warp = tid >> 5, nwarps = nthr >> 5;
+    for (long long c = warp; c < b; c += nwarps) {
+        double2* t = Tt + c * b;
+        for (int i = (int)c; i >= 0; --i) {
+            double sr = 0.0, si = 0.0;
+            for (int k = i + 1 + lane; k <= c; k += 32) {
+                const double2 r = __ldcg(R + (long long)i * b + k), tk = t[k];
+                sr += r.x * tk.x - r.y * tk.y;
+                si += r.x * tk.y + r.y * tk.x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) {
+                const double rii = __ldcg(R + (long long)i * b + i).x;
+                t[i] = make_double2(((i == c ? 1.0 : 0.0) - sr) / rii, -si / rii);
+            }
+            __syncwarp();
+        }
+        for (int i = (int)c + 1 + lane; i < b; i += 32) t[i] = make_double2(0.0, 0.0);
+    }
+    if (!jac::grid_barrier(sy, NB)) return;
+    for (long long e = tid; e < (long long)b * b; e += nthr) {
+        const long long i = e / b, c = e % b;
+        Rinv[e] = __ldcg(Tt + c * b + i);
     }
 }
 
-void launch_cholesky_inv(double2* G, double2* Rinv, int b, int* status, cudaStream_t s) {
+__global__ void k_flag(const jac::Sync* sy, int* err) {
+    if (err && sy->err) *err = 1;
+}
+}  // namespace chol
+
+size_t cholesky_work_bytes(int b) { return 2 * (size_t)b * b * sizeof(double2) + 256; }
+
+void launch_cholesky_inv(double2* G, double2* Rinv, int b, void* work, int* status, int* err, cudaStream_t s) {
     MG_REQUIRE(b >= 1 && b <= 4096, MGMLMC_EINVAL, "cholesky: 1 <= b <= 4096");
-    k_cholesky_inv<<<1, 1024, 0, s>>>(G, Rinv, b, status);
+    const int NB = jacobi_grid_size();
+    double2* R = reinterpret_cast<double2*>(work);
+    double2* Tt = R + (size_t)b * b;
+    jac::Sync* sy = reinterpret_cast<jac::Sync*>(Tt + (size_t)b * b);
+    MG_CUDA(cudaMemsetAsync(sy, 0, sizeof(jac::Sync), s));
+    void* args[] = {(void*)&G, (void*)&Rinv, (void*)&R, (void*)&Tt, (void*)&b, (void*)&status, (void*)&sy};
+    MG_CUDA(cudaLaunchCooperativeKernel((const void*)chol::k_cholesky_grid, dim3(NB), dim3(jac::kThreads), args, 0,
+                                        s));
+    MG_LAUNCHED();
+    chol::k_flag<<<1, 1, 0, s>>>(sy, err);
     MG_LAUNCHED();
 }
 
-void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, cudaStream_t s, bool descending) {
-    MG_REQUIRE(b >= 1 && b <= 1024, MGMLMC_EINVAL, "jacobi: 1 <= b <= 1024");
+void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, void* work, int* err, cudaStream_t s,
+                       bool descending) {
+    MG_REQUIRE(b >= 1 && b <= 2048, MGMLMC_EINVAL, "jacobi: 1 <= b <= 2048");
     const int bp = b + (b & 1);
-    size_t sm = (size_t)((bp + 1) / 2 + 1) * sizeof(double) + 4 * (size_t)(bp / 2) * sizeof(double) + 64;
-    if (sm < (size_t)(bp + 1) * sizeof(int)) sm = (bp + 1) * sizeof(int);
-    k_jacobi<<<1, 1024, sm, s>>>(H, W, lam, b, sweeps, descending ? 1 : 0);
+    const int G = jacobi_grid_size();
+    MG_REQUIRE(G <= 4 * kNumSM, MGMLMC_ECUDA, "jacobi: more SMs than the work space assumes");
+    char* w = reinterpret_cast<char*>(work);
+    const size_t mat = (size_t)bp * bp * sizeof(double2);
+    double2* A0 = reinterpret_cast<double2*>(w);
+    double2* A1 = reinterpret_cast<double2*>(w + mat);
+    double2* Wp = reinterpret_cast<double2*>(w + 2 * mat);
+    double* part = reinterpret_cast<double*>(w + 3 * mat);
+    jac::Sync* sy = reinterpret_cast<jac::Sync*>(part + 2 * (size_t)kNumSM * 4 + bp);
+    MG_CUDA(cudaMemsetAsync(sy, 0, sizeof(jac::Sync), s));
+    const size_t sm = jacobi_smem_bytes(b);
+    void* args[] = {(void*)&H, (void*)&A0, (void*)&A1, (void*)&Wp, (void*)&part, (void*)&sy, (void*)&b, (void*)&bp,
+                    (void*)&sweeps};
+    MG_CUDA(cudaLaunchCooperativeKernel((const void*)jac::k_jacobi_grid, dim3(G), dim3(jac::kThreads), args, sm, s));
+    MG_LAUNCHED();
+    int* rank = reinterpret_cast<int*>(sy + 1);
+    jac::k_jacobi_rank<<<(b + 255) / 256, 256, 0, s>>>(part + 2 * G, rank, b, descending ? 1 : 0);
+    MG_LAUNCHED();
+    jac::k_jacobi_permute<<<2 * kNumSM, 256, 0, s>>>(part + 2 * G, rank, Wp, W, lam, b, bp, sy, err);
     MG_LAUNCHED();
 }
 

@@ -1032,7 +1032,7 @@ static bool use_site_kernel(int d, int N) { return (d == 8 || d == 16) && N >= 6
 static bool use_narrow_kernel(int d, int N) { return (d == 8 || d == 16) && N <= 16; }
 
 int block_stencil_groups(int nsites, int d, int N) {
-    if (use_narrow_kernel(d, N)) return nsites;
+    if (use_narrow_kernel(d, N)) return nsites < 32 * kNumSM ? nsites : 32 * kNumSM;   // grid-stride over sites
     if (use_site_kernel(d, N)) {
         // one site per CTA up to 16 CTAs per SM: staging and compute of different
         // sites overlap across CTAs

@@ -354,6 +354,172 @@ void launch_coarse_inverse_bf16(float2* Y, const float2* X, const __nv_bfloat16*
 
 namespace tc {
 // ------------------------------------------------------------------------------
+// Deflation projections on the tensor cores (mg_precision 16).  For the traced
+// operator's deflated part L diag(a) R^H (Sect. 2, Eq. splitting_defl_trace) a
+// block of real probe vectors X [n][N] needs A = R^H X and B = L^H X.  With X real,
+//     Re A = (Re R)^T X,  Im A = -(Im R)^T X  (and the same for B with L),
+// so the four are one real GEMM  Y = W^T X  with W^T = [Re R | -Im R | Re L | -Im L]^T
+// (M = 4k rows, padded to 128; K = n; N = the rhs), BF16 operands, FP32
+// accumulation in TMEM.  W^T is rounded and pre-tiled once per deflation (the
+// K-major layout of the GEMM above); X (+-1, exact in BF16) is packed per block.
+// The samples then subtract sum_m a_m conj(B_m) A_m in FP64, and the estimate adds
+// the deflated trace from the same rounded factors (k_defl_tau), which keeps it
+// unbiased.
+
+// W^T pre-tiled in 128-row tiles: row m < k: Re R[:, m]; k + m: -Im R; 2k + m: Re L;
+// 3k + m: -Im L; rows >= 4k zero.  Rounding: FP64 -> FP32 -> BF16, both to nearest.
+__global__ void k_embed_defl(__nv_bfloat16* __restrict__ W, const double2* __restrict__ R,
+                             const double2* __restrict__ L, int n, int k, int Mpad) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)n * Mpad) return;
+    const int i = (int)(e / Mpad), m = (int)(e % Mpad);
+    float v = 0.f;
+    if (m < 4 * k) {
+        const int q = m / k, c = m % k;
+        const double2 z = (q < 2 ? R : L)[(long long)i * k + c];
+        v = (q & 1) ? -(float)z.y : (float)z.x;
+    }
+    W[tiled_off(m, i, BM, n / BK) / 2] = __float2bfloat16(v);
+}
+
+// X^T pre-tiled in NT-row tiles (row j = rhs, K = n): the real part of X, zero for j >= N.
+__global__ void k_pack_x_real(__nv_bfloat16* __restrict__ Bt, const double2* __restrict__ X, int n, int N, int Ncols,
+                              int NT) {
+    __shared__ float t[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, j = j0 + threadIdx.x;
+        t[r][threadIdx.x] = (i < n && j < N) ? (float)X[(size_t)i * N + j].x : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        if (i < n && j < Ncols) Bt[tiled_off(j, i, NT, n / BK) / 2] = __float2bfloat16(t[threadIdx.x][r]);
+    }
+}
+
+__device__ __forceinline__ double2 bf16_round(double2 z) {
+    return make_double2((double)__bfloat162float(__float2bfloat16((float)z.x)),
+                        (double)__bfloat162float(__float2bfloat16((float)z.y)));
+}
+
+// t[m] = R~_m^H L~_m in FP64 over the BF16-rounded factors (one CTA per m, fixed tree).
+__global__ void k_defl_tau(double2* __restrict__ t, const double2* __restrict__ R, const double2* __restrict__ L,
+                           int n, int k) {
+    __shared__ double sr[256], si[256];
+    const int m = blockIdx.x;
+    double re = 0, im = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 r = bf16_round(R[(long long)i * k + m]), l = bf16_round(L[(long long)i * k + m]);
+        re += r.x * l.x + r.y * l.y;
+        im += r.x * l.y - r.y * l.x;
+    }
+    sr[threadIdx.x] = re;
+    si[threadIdx.x] = im;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            sr[threadIdx.x] += sr[threadIdx.x + st];
+            si[threadIdx.x] += si[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) t[m] = make_double2(sr[0], si[0]);
+}
+
+// s[j] -= sum_m a_m conj(B_mj) A_mj from the split partials Yp[z][Mpad][Ncols] (one
+// CTA per rhs, fixed order over splits and a fixed reduction tree over m).
+__global__ void k_defl_correction_tc(double2* __restrict__ smp, const float* __restrict__ Yp,
+                                     const double* __restrict__ a, int k, int Mpad, int Ncols, int splits) {
+    __shared__ double sr[256], si[256];
+    const int j = blockIdx.x;
+    const size_t slab = (size_t)Mpad * Ncols;
+    double re = 0, im = 0;
+    for (int m = threadIdx.x; m < k; m += blockDim.x) {
+        double ar = 0, ai = 0, br = 0, bi = 0;
+        for (int z = 0; z < splits; ++z) {
+            const float* Y = Yp + z * slab;
+            ar += Y[(size_t)m * Ncols + j];
+            ai += Y[(size_t)(k + m) * Ncols + j];
+            br += Y[(size_t)(2 * k + m) * Ncols + j];
+            bi += Y[(size_t)(3 * k + m) * Ncols + j];
+        }
+        const double w = a[m];
+        re += w * (br * ar + bi * ai);     // conj(B) A
+        im += w * (br * ai - bi * ar);
+    }
+    sr[threadIdx.x] = re;
+    si[threadIdx.x] = im;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            sr[threadIdx.x] += sr[threadIdx.x + st];
+            si[threadIdx.x] += si[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) smp[j] = make_double2(smp[j].x - sr[0], smp[j].y - si[0]);
+}
+}  // namespace tc
+
+bool tc_deflation_supported(long long n, int k) { return n >= 64 && n % 64 == 0 && n <= 65535LL * 32 && k >= 1; }
+int tc_deflation_rows(int k) { return (4 * k + tc::BM - 1) / tc::BM * tc::BM; }
+
+void launch_embed_deflation_bf16(__nv_bfloat16* W, const double2* R, const double2* L, long long n, int k,
+                                 cudaStream_t s) {
+    MG_REQUIRE(tc_deflation_supported(n, k), MGMLMC_EINVAL, "tensor-core deflation needs n % 64 == 0");
+    const int Mpad = tc_deflation_rows(k);
+    const long long tot = n * Mpad;
+    tc::k_embed_defl<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W, R, L, (int)n, k, Mpad);
+    MG_LAUNCHED();
+}
+
+void launch_deflation_tau_bf16(double2* t, const double2* R, const double2* L, long long n, int k, cudaStream_t s) {
+    tc::k_defl_tau<<<k, 256, 0, s>>>(t, R, L, (int)n, k);
+    MG_LAUNCHED();
+}
+
+static int pick_nt_real(int N) { return N >= 256 ? 256 : (N > 64 ? 128 : 64); }
+
+static int defl_splits(long long n, int Mpad, int Ncols, int NT) {
+    const int tiles = (Ncols / NT) * (Mpad / tc::BM);
+    const long long ktiles = n / tc::BK;
+    long long S = kNumSM / (tiles > 0 ? tiles : 1);
+    if (S < 1) S = 1;
+    if (S > 16) S = 16;
+    if (S > ktiles) S = ktiles;
+    const long long per = (ktiles + S - 1) / S;
+    return (int)((ktiles + per - 1) / per);
+}
+
+size_t deflation_bf16_scratch(long long n, int k, int N) {
+    const int NT = pick_nt_real(N);
+    const size_t Ncols = (size_t)((N + NT - 1) / NT) * NT;
+    const int Mpad = tc_deflation_rows(k);
+    const int S = defl_splits(n, Mpad, (int)Ncols, NT);
+    return Ncols * (size_t)n * sizeof(__nv_bfloat16) + (size_t)S * Mpad * Ncols * sizeof(float) + 256;
+}
+
+void launch_deflation_correction_bf16(double2* smp, const double2* X, const __nv_bfloat16* W, const double* a,
+                                      long long n, int k, int N, void* scratch, int* err, cudaStream_t s) {
+    MG_REQUIRE(tc_deflation_supported(n, k), MGMLMC_EINVAL, "tensor-core deflation needs n % 64 == 0");
+    const int NT = pick_nt_real(N);
+    const int Ncols = (N + NT - 1) / NT * NT;
+    const int Mpad = tc_deflation_rows(k);
+    const int S = defl_splits(n, Mpad, Ncols, NT);
+    __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(scratch);
+    float* Yp = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(scratch) + (size_t)Ncols * n * 2);
+    dim3 g((Ncols + 31) / 32, (unsigned)((n + 31) / 32));
+    tc::k_pack_x_real<<<g, dim3(32, 8), 0, s>>>(Bt, X, (int)n, N, Ncols, NT);
+    MG_LAUNCHED();
+    launch_tc(NT, Yp, W, Bt, Mpad, (int)n, Ncols, S, err, s);
+    tc::k_defl_correction_tc<<<N, 256, 0, s>>>(smp, Yp, a, k, Mpad, Ncols, S);
+    MG_LAUNCHED();
+}
+
+
+namespace tc {
+// ------------------------------------------------------------------------------
 // Coarse block stencil on the tensor cores, d = 16 (the first coarse level of the
 // workloads): y(s) = sum_dir A(s, dir) x(nbr(s, dir)), the operator that the
 // block-Jacobi smoother's minimal-residual steps apply.
@@ -431,10 +597,11 @@ __global__ void k_embed_stencil(__nv_bfloat16* __restrict__ E, const float2* __r
 
 // BF16 tiles of x: rt[(site * T + t) * 4096 + off / 2], zero rows for rhs >= N.
 // Thread = (site, component group of 4, rhs): four FP32 loads, one 16-byte store.
+// Grid: x = (site, component group), y = 128-rhs tile.
 __global__ void k_pack_tiles(__nv_bfloat16* __restrict__ rt, const float2* __restrict__ x, int nsites, int N) {
-    const int T = gridDim.x;
-    const int j = blockIdx.x * CH + threadIdx.x;
-    const int site = blockIdx.y >> 2, cg = blockIdx.y & 3;
+    const int T = gridDim.y, tt = blockIdx.y;
+    const int j = tt * CH + threadIdx.x;
+    const int site = blockIdx.x >> 2, cg = blockIdx.x & 3;
     float2 v[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -444,7 +611,7 @@ __global__ void k_pack_tiles(__nv_bfloat16* __restrict__ rt, const float2* __res
     w.y = pack_bf16(v[1].x, v[1].y);
     w.z = pack_bf16(v[2].x, v[2].y);
     w.w = pack_bf16(v[3].x, v[3].y);
-    uint8_t* tile = reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A;
+    uint8_t* tile = reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + tt) * TILE_A;
     *reinterpret_cast<uint4*>(tile + kmaj32_off(threadIdx.x, 8 * cg)) = w;
     (void)nsites;
 }
@@ -455,9 +622,9 @@ __global__ void k_pack_tiles(__nv_bfloat16* __restrict__ rt, const float2* __res
 __global__ void __launch_bounds__(CH) k_mr_update_tc(float2* __restrict__ yh, float2* __restrict__ r,
                                                     const float2* __restrict__ p, const double2* __restrict__ dots,
                                                     int N, bool first, __nv_bfloat16* __restrict__ rt) {
-    const int T = gridDim.x;
-    const int j = blockIdx.x * CH + threadIdx.x;
-    const int site = blockIdx.y;
+    const int T = gridDim.y, tt = blockIdx.y;     // grid: x = site, y = 128-rhs tile
+    const int j = tt * CH + threadIdx.x;
+    const int site = blockIdx.x;
     float ax = 0.f, ay = 0.f;
     if (j < N) {
         const double2 pr = dots[j];
@@ -467,7 +634,7 @@ __global__ void __launch_bounds__(CH) k_mr_update_tc(float2* __restrict__ yh, fl
             ay = (float)(pr.y / pp);
         }
     }
-    uint8_t* tile = rt ? reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + blockIdx.x) * TILE_A : nullptr;
+    uint8_t* tile = rt ? reinterpret_cast<uint8_t*>(rt) + ((size_t)site * T + tt) * TILE_A : nullptr;
     // all loads of the thread first (memory-level parallelism), then the arithmetic
     float2 rv[D], pv[D], ev[D];
     const size_t base = (size_t)site * D * N + j;
@@ -507,14 +674,14 @@ __global__ void __launch_bounds__(CH) k_mr_update_tc(float2* __restrict__ yh, fl
 __global__ void __launch_bounds__(CH) k_mr_update_bf16(float2* __restrict__ yh, __nv_bfloat16* __restrict__ rt,
                                                       const __nv_bfloat16* __restrict__ pt,
                                                       const double2* __restrict__ dots, int N, bool first) {
-    const int T = gridDim.x;
-    const int jl = threadIdx.x, j = blockIdx.x * CH + jl;
-    const int site = blockIdx.y;
+    const int T = gridDim.y, tt = blockIdx.y;     // grid: x = site, y = 128-rhs tile
+    const int jl = threadIdx.x, j = tt * CH + jl;
+    const int site = blockIdx.x;
     if (j >= N) return;                           // pad rows stay zero
     const double2 pr = dots[j];
     const double pp = dots[N + j].x;
     const float ax = pp > 0.0 ? (float)(pr.x / pp) : 0.f, ay = pp > 0.0 ? (float)(pr.y / pp) : 0.f;
-    const size_t toff = ((size_t)site * T + blockIdx.x) * TILE_A;
+    const size_t toff = ((size_t)site * T + tt) * TILE_A;
     uint8_t* rrow = reinterpret_cast<uint8_t*>(rt) + toff;
     const uint8_t* prow = reinterpret_cast<const uint8_t*>(pt) + toff;
     uint4 rw[4], pw[4];
@@ -774,15 +941,15 @@ static int tc_tiles(int N) { return (N + tc::tcs::CH - 1) / tc::tcs::CH; }
 size_t tc_tiles_bytes(int nsites, int N) { return (size_t)nsites * tc_tiles(N) * tc::tcs::TILE_A; }
 
 void launch_pack_tiles_bf16(__nv_bfloat16* rt, const float2* x, int nsites, int N, cudaStream_t s) {
-    MG_REQUIRE(nsites <= 16383, MGMLMC_EINVAL, "BF16 tiles: at most 16383 sites");
-    tc::tcs::k_pack_tiles<<<dim3(tc_tiles(N), 4 * nsites), tc::tcs::CH, 0, s>>>(rt, x, nsites, N);
+    MG_REQUIRE(nsites >= 1 && nsites <= (1 << 28) && tc_tiles(N) <= 65535, MGMLMC_EINVAL, "BF16 tiles: size");
+    tc::tcs::k_pack_tiles<<<dim3(4 * nsites, tc_tiles(N)), tc::tcs::CH, 0, s>>>(rt, x, nsites, N);
     MG_LAUNCHED();
 }
 
 void launch_mr_update_tc(float2* yh, float2* r, const float2* p, const double2* dots, int nsites, int N, bool first,
                          __nv_bfloat16* rt, cudaStream_t s) {
-    MG_REQUIRE(nsites <= 65535, MGMLMC_EINVAL, "BF16 tiles: at most 65535 sites");
-    tc::tcs::k_mr_update_tc<<<dim3(tc_tiles(N), nsites), tc::tcs::CH, 0, s>>>(yh, r, p, dots, N, first, rt);
+    MG_REQUIRE(nsites >= 1 && nsites <= (1 << 30) && tc_tiles(N) <= 65535, MGMLMC_EINVAL, "BF16 tiles: size");
+    tc::tcs::k_mr_update_tc<<<dim3(nsites, tc_tiles(N)), tc::tcs::CH, 0, s>>>(yh, r, p, dots, N, first, rt);
     MG_LAUNCHED();
 }
 
@@ -819,8 +986,8 @@ void launch_block_stencil_tc(float2* y, __nv_bfloat16* yt, const float2* b, cons
 
 void launch_mr_update_bf16(float2* yh, __nv_bfloat16* rt, const __nv_bfloat16* pt, const double2* dots, int nsites,
                            int N, bool first, cudaStream_t s) {
-    MG_REQUIRE(nsites <= 65535, MGMLMC_EINVAL, "BF16 tiles: at most 65535 sites");
-    tc::tcs::k_mr_update_bf16<<<dim3(tc_tiles(N), nsites), tc::tcs::CH, 0, s>>>(yh, rt, pt, dots, N, first);
+    MG_REQUIRE(nsites >= 1 && nsites <= (1 << 30) && tc_tiles(N) <= 65535, MGMLMC_EINVAL, "BF16 tiles: size");
+    tc::tcs::k_mr_update_bf16<<<dim3(nsites, tc_tiles(N)), tc::tcs::CH, 0, s>>>(yh, rt, pt, dots, N, first);
     MG_LAUNCHED();
 }
 

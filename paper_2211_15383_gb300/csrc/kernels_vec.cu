@@ -405,22 +405,27 @@ namespace mg {
 // out[c][r] = in[r][c] for a rows x cols complex matrix (32 x 32 tiles).
 __global__ void k_transpose(double2* __restrict__ out, const double2* __restrict__ in, long long rows, int cols) {
     __shared__ double2 t[32][33];
-    const long long r0 = (long long)blockIdx.y * 32;
     const int c0 = blockIdx.x * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const long long r = r0 + k;
-        const int cc = c0 + threadIdx.x;
-        if (r < rows && cc < cols) t[k][threadIdx.x] = in[r * cols + cc];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int cc = c0 + k;
-        const long long r = r0 + threadIdx.x;
-        if (r < rows && cc < cols) out[(long long)cc * rows + r] = t[threadIdx.x][k];
+    const long long nrb = (rows + 31) / 32;
+    for (long long rb = blockIdx.y; rb < nrb; rb += gridDim.y) {      // grid-stride over 32-row blocks
+        const long long r0 = rb * 32;
+        __syncthreads();
+        for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+            const long long r = r0 + k;
+            const int cc = c0 + threadIdx.x;
+            if (r < rows && cc < cols) t[k][threadIdx.x] = in[r * cols + cc];
+        }
+        __syncthreads();
+        for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+            const int cc = c0 + k;
+            const long long r = r0 + threadIdx.x;
+            if (r < rows && cc < cols) out[(long long)cc * rows + r] = t[threadIdx.x][k];
+        }
     }
 }
 void launch_transpose(double2* out, const double2* in, long long rows, int cols, cudaStream_t s) {
-    dim3 g((cols + 31) / 32, (unsigned)((rows + 31) / 32));
+    const long long nrb = (rows + 31) / 32;
+    dim3 g((cols + 31) / 32, (unsigned)(nrb < 65535 ? nrb : 65535));
     k_transpose<<<g, dim3(32, 8), 0, s>>>(out, in, rows, cols);
     MG_LAUNCHED();
 }

@@ -21,6 +21,7 @@
 
 #include "admission.h"
 #include "context.h"
+#include "footprint.h"
 
 namespace {
 
@@ -80,6 +81,10 @@ int geometry(const mgmlmc_request& r, Geometry& g, std::string& why) {
         lt /= at;
         d = 2 * nv;
     }
+    if (r.sum_levels < 0 || r.sum_levels > r.nlevels) {
+        why = "request: 0 <= sum_levels <= nlevels";
+        return MGMLMC_EINVAL;
+    }
     if (g.n[g.L - 1] > 16384) {
         why = "request: the coarsest level is inverted densely (at most 16384 unknowns)";
         return MGMLMC_ENOTIMPL;
@@ -87,60 +92,34 @@ int geometry(const mgmlmc_request& r, Geometry& g, std::string& why) {
     return MGMLMC_OK;
 }
 
-// Device bytes a request's context holds at most, summed over the allocations of
-// the setup, the deflation and the estimator (an upper estimate: scratch blocks that
-// are never live together are counted together).
+int term_levels_of(const mgmlmc_request& r) {
+    return (r.sum_levels > 0 && r.sum_levels < r.nlevels) ? r.sum_levels : r.nlevels;
+}
+
+// Device bytes a request's context holds at most (mg::footprint_bytes).
 size_t footprint_bytes(const mgmlmc_request& r, const Geometry& g) {
-    const double N = std::max(1, r.opt.max_block_rhs);
-    const double m = std::max(1, r.opt.fgmres_restart);
-    const bool f64 = r.opt.mg_precision == 64, bf16 = r.opt.mg_precision == 16;
-    const double sz = f64 ? 16 : 8;              // bytes of a complex entry of the V-cycle
-    const double G = 608, GA = 2432;             // bounds on reduction row groups
-    const int L = g.L;
-    const double n0 = (double)g.n[0], nL = (double)g.n[L - 1];
-    double nvmax = 1;
-    for (int l = 0; l + 1 < L; ++l) nvmax = std::max(nvmax, (double)r.nvec[l]);
-    double b = 0;
-    b += (double)g.sites[0] * 2 * 24;                                        // links
-    for (int l = 0; l < L; ++l) {
-        const double s = (double)g.sites[l], d = g.d[l], n = (double)g.n[l];
-        b += s * 5 * d * d * (l > 0 ? 24 : 16);                              // D_l (FP64, FP32)
-        if (l + 1 < L) {
-            const double nv = r.nvec[l];
-            b += n * nv * (40 + 16);                                         // P (FP64, FP32), test vectors, raw
-            b += s * 5 * d * 2 * nv * 16;                                    // Galerkin product scratch
-        }
-        if (l > 0 && l + 1 < L) {
-            b += s * d * d * (24 + 16) + s * 5 * d * d * 24;                 // M^{-1}, D M^{-1}, work
-            if (bf16) b += s * d * d * 80;                                   // BF16 operand tiles
-        }
-        if (l > 0) b += (2.0 * (double)g.n[l - 1] + n) * N * 16;            // FP64 Galerkin apply
-        if (l + 1 < L) {
-            b += n * N * sz * 3 + 2.0 * (double)g.n[l + 1] * N * sz;         // V-cycle blocks
-            if (bf16) b += 3.0 * s * std::ceil(N / 128) * 8192 + n * N * 8; // BF16 tiles and rhs
-        }
-        if (l > 0) b += n * N * 16;                                          // estimator block of level l
+    mg::Shape s;
+    s.L = g.L;
+    s.nterm_levels = term_levels_of(r);
+    for (int l = 0; l < g.L; ++l) {
+        s.sites[l] = g.sites[l];
+        s.n[l] = g.n[l];
+        s.d[l] = g.d[l];
+        s.nvec[l] = l + 1 < g.L ? r.nvec[l] : 0;
     }
-    b += 2.0 * n0 * nvmax * 16;                                              // setup blocks
-    b += nL * nL * 44 + nL * N * 136;                                        // dense coarsest inverse, BF16 solve
-    b += (2 * m + 1) * n0 * (N * sz + nvmax * 16);                           // FGMRES bases
-    b += G * (m + 1) * N * 16 + N * (m + 1) * (m + 4) * 16;                  // Gram-Schmidt partials, Hessenberg
-    b += n0 * N * 56;                                                        // refinement blocks
-    b += n0 * N * 32;                                                        // noise and solution blocks
-    b += G * N * 16 * 6 + GA * N * 8;                                        // reduction partials
-    if (r.k > 0) {
-        const double k = r.k, bb = std::min(nL, std::max(2 * k, k + 16));
-        b += 6 * nL * bb * 16 + 5 * bb * bb * 16 + 2 * G * bb * bb * 16;   // eigensolver blocks
-        b += 2 * nL * k * 16 + G * k * 16;                                   // triplets
-        b += 2 * k * N * 16 + G * k * N * 16;                                // deflation projections
-    }
-    return (size_t)(b * 1.15) + ((size_t)32 << 20);
+    s.k = r.k;
+    s.N = r.opt.max_block_rhs;
+    s.m = r.opt.fgmres_restart;
+    s.precision = r.opt.mg_precision;
+    s.kcycle = r.opt.kcycle_iters;
+    return mg::footprint_bytes(s);
 }
 
 std::string shape_key(const mgmlmc_request& r) {
     std::string s = std::to_string(r.Lx) + "x" + std::to_string(r.Lt) + "/" + std::to_string(r.nlevels);
     for (int l = 0; l + 1 < r.nlevels; ++l)
         s += ":" + std::to_string(r.agg_x[l]) + "," + std::to_string(r.agg_t[l]) + "," + std::to_string(r.nvec[l]);
+    s += "/t" + std::to_string(term_levels_of(r));
     s += "/k" + std::to_string(r.k) + "/p" + std::to_string(r.opt.mg_precision) + "/N" +
          std::to_string(r.opt.max_block_rhs) + "/m" + std::to_string(r.opt.fgmres_restart);
     return s;
@@ -249,6 +228,13 @@ int run_job(Job& j, cudaStream_t stream, PoolUser* pu, std::string& msg, size_t&
         for (size_t l = 0; l < j.start.size(); ++l) sv[l] = j.start[l].data();
         step(mgmlmc_set_hierarchy(ctx, r.nlevels, r.agg_x, r.agg_t, r.nvec, r.setup_iters, r.setup_tol, sv.data()),
              "set_hierarchy");
+    }
+    if (rc == MGMLMC_OK && term_levels_of(r) < r.nlevels) {
+        // the last levels serve only the solver: the sum ends at level sum_levels
+        int skip[MGMLMC_MAX_LEVELS];
+        int ns = 0;
+        for (int l = term_levels_of(r) + 1; l <= r.nlevels; ++l) skip[ns++] = l;
+        step(mgmlmc_set_terms(ctx, ns, skip), "set_terms");
     }
     if (rc == MGMLMC_OK && r.k > 0)
         step(mgmlmc_compute_deflation(ctx, r.k, r.defl_tol, r.defl_max_iters), "compute_deflation");
@@ -420,10 +406,10 @@ int mgmlmc_submit(mgmlmc_server* srv, const mgmlmc_request* req, uint64_t* id) {
     int positive = 0;
     for (int t = 0; t < MGMLMC_MAX_LEVELS; ++t) {
         if (!(r.costs[t] >= 0) || !std::isfinite(r.costs[t])) return fail(MGMLMC_EINVAL, "submit: costs >= 0");
-        positive += t < r.nlevels && r.costs[t] > 0;
+        positive += t < term_levels_of(r) && r.costs[t] > 0;
     }
-    if (positive != 0 && positive != r.nlevels)   // the allocation divides by every term's cost
-        return fail(MGMLMC_EINVAL, "submit: costs all zero (measured) or > 0 for each of the nlevels terms");
+    if (positive != 0 && positive != term_levels_of(r))   // the allocation divides by every term's cost
+        return fail(MGMLMC_EINVAL, "submit: costs all zero (measured) or > 0 for each term");
     std::shared_ptr<Job> job;
     try {
         job = std::make_shared<Job>();

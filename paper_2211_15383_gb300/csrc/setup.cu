@@ -69,17 +69,17 @@ void Ctx::release_all() {
     defl = Deflation();
 }
 
+static void free_one_deflation(Ctx& c, Deflation& d) {
+    c.dev_free(d.Lv);
+    c.dev_free(d.Rv);
+    c.dev_free(d.a);
+    c.dev_free(d.W16);
+    d = Deflation();
+}
+
 void Ctx::free_deflation() {
-    dev_free(defl.Lv);
-    dev_free(defl.Rv);
-    dev_free(defl.a);
-    defl = Deflation();
-    for (auto& d : ddefl) {
-        dev_free(d.Lv);
-        dev_free(d.Rv);
-        dev_free(d.a);
-        d = Deflation();
-    }
+    free_one_deflation(*this, defl);
+    for (auto& d : ddefl) free_one_deflation(*this, d);
 }
 
 const Deflation* term_deflation(const Ctx& c, int a, int b) {
@@ -185,6 +185,9 @@ static void dup_deflation(Ctx& d, const Ctx& s, const Deflation& from, Deflation
     to.Lv = dup(d, from.Lv, n * k);
     to.Rv = dup(d, from.Rv, n * k);
     to.a = dup(d, from.a, k);
+    to.W16 = from.W16 ? dup(d, from.W16, (size_t)tc_deflation_rows(from.k) * n) : nullptr;
+    to.tau16_re = from.tau16_re;
+    to.tau16_im = from.tau16_im;
 }
 
 // d (fresh, on its own stream) receives s's gauge field, mass, hierarchy, term list
@@ -302,8 +305,31 @@ __global__ void k_weighted_sum(double2* out, const double2* t, const double* a, 
 
 static void small_launch_check() { MG_LAUNCHED(); }
 
+void prepare_tc_deflation(Ctx& c, Deflation& D) {
+    c.dev_free(D.W16);
+    D.W16 = nullptr;
+    const long long n = c.lev[D.fine].n;
+    if (c.opt.mg_precision != 16 || D.k < 1 || !tc_deflation_supported(n, D.k)) return;
+    D.W16 = c.alloc_n<__nv_bfloat16>((size_t)tc_deflation_rows(D.k) * n);
+    launch_embed_deflation_bf16(D.W16, D.Rv, D.Lv, n, D.k, c.stream);
+    double2* t = c.scratch<double2>("tcd_t", D.k);
+    double2* tau = c.scratch<double2>("tcd_tau", 1);
+    launch_deflation_tau_bf16(t, D.Rv, D.Lv, n, D.k, c.stream);
+    k_weighted_sum<<<1, 1, 0, c.stream>>>(tau, t, D.a, D.k);
+    small_launch_check();
+    double2 h;
+    MG_CUDA(cudaMemcpyAsync(&h, tau, sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    D.tau16_re = h.x;
+    D.tau16_im = h.y;
+}
+
+
 void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);   // solver.cu
-constexpr int kBootstrapRounds = 2;
+// Rounds of the preconditioner bootstrap: two, plus one per level beyond three (the
+// deeper the hierarchy, the more its coarse levels built from random vectors weaken
+// the first cycles).
+static int bootstrap_rounds(int nlevels) { return 2 + std::max(0, nlevels - 3); }
 // Subspace iterations between Rayleigh-Ritz projections (and convergence checks).
 constexpr int kRayleighRitzEvery = 4;
 
@@ -445,7 +471,7 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
         // level's vectors by a few rounds of approximate inverse iteration (one FGMRES
         // cycle each).  This only shapes the preconditioner of the setup solves; the
         // final test vectors come from the exact iteration below.
-        for (int round = 0; round < kBootstrapRounds; ++round)
+        for (int round = 0; round < bootstrap_rounds(nlev); ++round)
             for (int l = 0; l < nlev - 1; ++l) {
                 Level& L = c.lev[l];
                 const int nv = L.nvec;
@@ -470,7 +496,10 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
             launch_transpose(B, raw[l], nv, (int)L.n, c.stream);
             for (int it = 0; it < setup_iters; ++it) {
                 int ok = 0;
-                solve(c, l, B, X, nv, setup_tol, &ok);
+                const long long its = solve(c, l, B, X, nv, setup_tol, &ok);
+                if (c.opt.verbose)
+                    fprintf(stderr, "[mgmlmc] setup level %d inverse iteration %d: %lld iterations%s\n", l + 1, it,
+                            its, ok ? "" : " (not converged)");
                 MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED,
                            "set_hierarchy: inverse-iteration solve on level " + std::to_string(l + 1) +
                                " did not converge");
@@ -489,47 +518,70 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
 }
 
 // ------------------------------------------------------------------ deflation
+// Block products of the eigensolvers.  On large levels with a loose tolerance they
+// run with FP32 arithmetic on the FP64 vectors (fast = true): FP64 runs at 1/64 of
+// the FP32 rate on this GPU, and n b^2 products at n = 262144, b = 1024 would take
+// seconds each.  The Ritz residuals are still formed in FP64; FP32 rounding of the
+// Ritz vectors limits them to about 1e-6 ||Q|| / |lambda| (hence the tolerance bound).
+static bool fast_block_products(long long n, int b, double tol) {
+    return (double)n * b * b * 8.0 > 2e11 && tol >= 1e-4;
+}
+static void block_hn(Ctx& c, bool fast, double2* G, const double2* A, const double2* B, long long n, int ka, int kb,
+                     const char* part_name) {
+    if (fast) {
+        const int groups = gemm_hn_fp32_groups(n, ka, kb);
+        double2* part = c.scratch<double2>(part_name, (size_t)groups * ka * kb);
+        launch_gemm_hn_fp32(G, A, B, n, ka, kb, part, groups, c.stream);
+        return;
+    }
+    const int groups = gemm_hn_groups(n, ka, kb);
+    double2* part = c.scratch<double2>(part_name, (size_t)groups * ka * kb);
+    launch_gemm_hn<double2>(G, A, B, n, ka, kb, part, groups, c.stream);
+}
+static void block_nn(Ctx& c, bool fast, double2* Y, const double2* X, const double2* W, long long n, int b, int kb) {
+    if (fast) launch_gemm_nn_fp32(Y, X, W, (int)n, b, kb, c.stream);
+    else launch_gemm_nn<double2>(Y, X, W, (int)n, b, kb, false, c.stream);
+}
+
 // Loewdin orthonormalisation X <- X G^{-1/2} (G = X^H X via the Jacobi eigensolver),
 // twice: robust for nearly dependent columns, used as the fallback.
-static void orthonormalize_loewdin(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
+static void orthonormalize_loewdin(Ctx& c, double2*& X, double2*& Y, long long n, int b, bool fast) {
     double2* G = c.scratch<double2>("df_G", (size_t)b * b);
     double2* W = c.scratch<double2>("df_W", (size_t)b * b);
     double* lam = c.scratch<double>("df_lamG", b);
-    const int groups = gemm_hn_groups(n, b, b);
-    double2* part = c.scratch<double2>("df_part", (size_t)groups * b * b);
     for (int pass = 0; pass < 2; ++pass) {
-        launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
+        block_hn(c, fast, G, X, X, n, b, b, "df_part");
         k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(G, b);
         small_launch_check();
         {
             ProfScope ps(c, "setup.jacobi", 0, 0);
-            launch_jacobi_eig(G, W, lam, b, 40, c.stream);
+            launch_jacobi_eig(G, W, lam, b, 40, c.scratch_bytes("jacobi_work", jacobi_work_bytes(b)),
+                              device_error_flag(c), c.stream);
         }
         k_scale_cols_rsqrt<<<(b * b + 127) / 128, 128, 0, c.stream>>>(W, lam, b);
         small_launch_check();
-        launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
+        block_nn(c, fast, Y, X, W, n, b, b);
         std::swap(X, Y);
     }
 }
 
 // CholQR2: X <- X R^{-1} with G = X^H X = R^H R, twice; falls back to the
 // Loewdin form if a Gram matrix is not numerically positive definite.
-static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b) {
+static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b, bool fast) {
     double2* G = c.scratch<double2>("df_G", (size_t)b * b);
     double2* Ri = c.scratch<double2>("df_Ri", (size_t)b * b);
     int* st = c.scratch<int>("df_st", 4);
-    const int groups = gemm_hn_groups(n, b, b);
-    double2* part = c.scratch<double2>("df_part", (size_t)groups * b * b);
     double2* keep = c.scratch<double2>("df_Xkeep", (size_t)n * b);
     MG_CUDA(cudaMemcpyAsync(keep, X, sizeof(double2) * n * b, cudaMemcpyDeviceToDevice, c.stream));
     MG_CUDA(cudaMemsetAsync(st, 0, sizeof(int), c.stream));
     for (int pass = 0; pass < 2; ++pass) {
-        launch_gemm_hn<double2>(G, X, X, n, b, b, part, groups, c.stream);
+        block_hn(c, fast, G, X, X, n, b, b, "df_part");
         {
             ProfScope ps(c, "setup.cholqr", 0, 0);
-            launch_cholesky_inv(G, Ri, b, st, c.stream);
+            launch_cholesky_inv(G, Ri, b, c.scratch_bytes("chol_work", cholesky_work_bytes(b)), st,
+                                device_error_flag(c), c.stream);
         }
-        launch_gemm_nn<double2>(Y, X, Ri, (int)n, b, b, false, c.stream);
+        block_nn(c, fast, Y, X, Ri, n, b, b);
         std::swap(X, Y);
     }
     int hs = 0;
@@ -537,71 +589,124 @@ static void orthonormalize(Ctx& c, double2*& X, double2*& Y, long long n, int b)
     c.sync();
     if (hs) {
         MG_CUDA(cudaMemcpyAsync(X, keep, sizeof(double2) * n * b, cudaMemcpyDeviceToDevice, c.stream));
-        orthonormalize_loewdin(c, X, Y, n, b);
+        orthonormalize_loewdin(c, X, Y, n, b, fast);
     }
+}
+
+// Block of the subspace iteration on level l (per-level names: a coarser level's
+// iteration runs while the finer level's block is held).
+struct Subspace {
+    double2 *X, *Y, *T, *T2, *H, *W;
+    double *lam, *res;
+};
+static Subspace subspace_buffers(Ctx& c, int l, int b) {
+    const size_t n = (size_t)c.lev[l].n;
+    const std::string sfx = "_" + std::to_string(l);
+    Subspace S;
+    S.X = c.scratch<double2>("df_X" + sfx, n * b);
+    S.Y = c.scratch<double2>("df_Y" + sfx, n * b);
+    S.T = c.scratch<double2>("df_T" + sfx, n * b);
+    S.T2 = c.scratch<double2>("df_T2" + sfx, n * b);
+    S.H = c.scratch<double2>("df_H" + sfx, (size_t)b * b);
+    S.W = c.scratch<double2>("df_WR" + sfx, (size_t)b * b);
+    S.lam = c.scratch<double>("df_lam" + sfx, b);
+    S.res = c.scratch<double>("df_res" + sfx, b);
+    return S;
+}
+
+// Subspace iteration on Q_l^{-1} = D_l^{-1} Gamma5^l from the orthonormal block S.X
+// (FP64-accurate solves to solve_tol), Rayleigh-Ritz with Q_l after the first
+// iteration, every kRayleighRitzEvery and after the last; stops once every one of
+// the k wanted Ritz pairs has ||Q x - lambda x|| <= tol |lambda|.  S.X holds the
+// Ritz vectors (by increasing |lambda|) and h_lam their values after the last
+// Rayleigh-Ritz step.
+static bool subspace_iteration(Ctx& c, int l, int k, int b, double tol, int max_iters, double solve_tol, Subspace& S,
+                               std::vector<double>& h_lam) {
+    const Level& L = c.lev[l];
+    const long long n = L.n;
+    const bool fast = fast_block_products(n, b, tol);
+    std::vector<double> h_res(b);
+    h_lam.assign(b, 0.0);
+    bool conv = false;
+    for (int it = 0; it < max_iters && !conv; ++it) {
+        // X <- Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves), then orthonormalise
+        launch_gamma5<double2>(S.T, S.X, L.nsites, L.d, b, c.stream);
+        int ok = 0;
+        solve(c, l, S.T, S.Y, b, solve_tol, &ok);
+        MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "deflation eigensolver: a solve did not converge");
+        std::swap(S.X, S.Y);
+        orthonormalize(c, S.X, S.Y, n, b, fast);
+        if (it > 0 && (it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) continue;
+        // Rayleigh-Ritz with Q = Gamma5 D
+        apply_D<double2>(c, l, S.T, S.X, nullptr, b, 0, nullptr);
+        launch_gamma5<double2>(S.T, S.T, L.nsites, L.d, b, c.stream);
+        block_hn(c, fast, S.H, S.X, S.T, n, b, b, "df_partR");
+        k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(S.H, b);
+        small_launch_check();
+        {
+            ProfScope ps(c, "setup.jacobi", 0, 0);
+            launch_jacobi_eig(S.H, S.W, S.lam, b, 40, c.scratch_bytes("jacobi_work", jacobi_work_bytes(b)),
+                              device_error_flag(c), c.stream);
+        }
+        block_nn(c, fast, S.Y, S.X, S.W, n, b, b);
+        block_nn(c, fast, S.T2, S.T, S.W, n, b, b);
+        std::swap(S.X, S.Y);
+        k_resid_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(S.T, S.T2, S.X, S.lam, n, b);
+        small_launch_check();
+        column_norms(c, S.res, S.T, n, b);
+        MG_CUDA(cudaMemcpyAsync(h_lam.data(), S.lam, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+        MG_CUDA(cudaMemcpyAsync(h_res.data(), S.res, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        check_device_error(c);
+        double worst = 0;
+        for (int i = 0; i < k; ++i) worst = std::max(worst, h_res[i] / std::fabs(h_lam[i]));
+        if (c.opt.verbose)
+            fprintf(stderr, "[mgmlmc] deflation level %d it %d worst rel residual %.3e\n", l + 1, it, worst);
+        conv = worst <= tol;
+    }
+    return conv;
+}
+
+// Iterations of the eigensolver on a coarser level that only shapes the start block.
+constexpr int kCoarseStartIters = 8;
+
+// Orthonormal start block of the subspace iteration on level l.  The coarser level's
+// Q_{l+1} = P^H Q_l P is Q_l's Galerkin (Rayleigh-Ritz) projection on range(P), which
+// holds the near-kernel the test vectors captured; so, where a coarser level has room
+// for the block, its approximate smallest-|lambda| Ritz vectors (a few iterations, the
+// same construction one level down) are prolongated; else seeded Z2 noise.
+static void subspace_start(Ctx& c, int l, int k, int b, double solve_tol, Subspace& S) {
+    const Level& L = c.lev[l];
+    if (l + 1 < c.L && c.lev[l + 1].n >= 2LL * b) {
+        Subspace Sc = subspace_buffers(c, l + 1, b);
+        subspace_start(c, l + 1, k, b, solve_tol, Sc);
+        std::vector<double> hl;
+        subspace_iteration(c, l + 1, k, b, 1e-2, kCoarseStartIters, std::max(solve_tol, 1e-8), Sc, hl);
+        apply_prolong<double2>(c, l, S.X, Sc.X, b, false);
+    } else {
+        launch_noise<double2>(S.X, L.n, b, 0x2211153830ull, 77 + (uint64_t)l, 0, c.stream);
+    }
+    orthonormalize(c, S.X, S.Y, L.n, b, fast_block_products(L.n, b, 1.0));
 }
 
 void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool inexact, double eig_solve_tol) {
     if (eig_solve_tol <= 0) eig_solve_tol = c.opt.solve_tol;
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "compute_deflation: no hierarchy");
     MG_REQUIRE(l >= 0 && l < c.L, MGMLMC_EINVAL, "compute_deflation: bad level");
-    c.dev_free(c.defl.Lv);
-    c.dev_free(c.defl.Rv);
-    c.dev_free(c.defl.a);
-    c.defl = Deflation();
+    free_one_deflation(c, c.defl);
     if (k == 0) return;
     const Level& L = c.lev[l];
     const long long n = L.n;
-    MG_REQUIRE(k >= 1 && k <= n && k <= 512, MGMLMC_EINVAL, "compute_deflation: 0 <= k <= min(n_L, 512)");
+    MG_REQUIRE(k >= 1 && k <= n && k <= 1024, MGMLMC_EINVAL, "compute_deflation: 0 <= k <= min(n_L, 1024)");
     MG_REQUIRE(tol > 0 && max_iters >= 1, MGMLMC_EINVAL, "compute_deflation: tol > 0 and max_iters >= 1");
     const int b = (int)std::min<long long>(n, std::max(2 * k, k + 16));
-    double2* X = c.scratch<double2>("df_X", (size_t)n * b);
-    double2* Y = c.scratch<double2>("df_Y", (size_t)n * b);
-    double2* T = c.scratch<double2>("df_T", (size_t)n * b);
-    double2* T2 = c.scratch<double2>("df_T2", (size_t)n * b);
-    double2* H = c.scratch<double2>("df_H", (size_t)b * b);
-    double2* W = c.scratch<double2>("df_WR", (size_t)b * b);
-    double* lam = c.scratch<double>("df_lam", b);
-    double* res = c.scratch<double>("df_res", b);
-    const int groups = gemm_hn_groups(n, b, b);
-    double2* part = c.scratch<double2>("df_partR", (size_t)groups * b * b);
-    launch_noise<double2>(X, n, b, 0x2211153830ull, 77, 0, c.stream);
-    orthonormalize(c, X, Y, n, b);
-    std::vector<double> h_lam(b), h_res(b);
-    bool conv = false;
-    for (int it = 0; it < max_iters && !conv; ++it) {
-        // X <- Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves), then orthonormalise
-        launch_gamma5<double2>(T, X, L.nsites, L.d, b, c.stream);
-        int ok = 0;
-        solve(c, l, T, Y, b, eig_solve_tol, &ok);
-        MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "compute_deflation: coarsest solve did not converge");
-        std::swap(X, Y);
-        orthonormalize(c, X, Y, n, b);
-        if ((it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) continue;
-        // Rayleigh-Ritz with Q = Gamma5 D
-        apply_D<double2>(c, l, T, X, nullptr, b, 0, nullptr);
-        launch_gamma5<double2>(T, T, L.nsites, L.d, b, c.stream);
-        launch_gemm_hn<double2>(H, X, T, n, b, b, part, groups, c.stream);
-        k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(H, b);
-        small_launch_check();
-        {
-            ProfScope ps(c, "setup.jacobi", 0, 0);
-            launch_jacobi_eig(H, W, lam, b, 40, c.stream);
-        }
-        launch_gemm_nn<double2>(Y, X, W, (int)n, b, b, false, c.stream);
-        launch_gemm_nn<double2>(T2, T, W, (int)n, b, b, false, c.stream);
-        std::swap(X, Y);
-        k_resid_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(T, T2, X, lam, n, b);
-        small_launch_check();
-        column_norms(c, res, T, n, b);
-        MG_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
-        MG_CUDA(cudaMemcpyAsync(h_res.data(), res, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
-        c.sync();
-        double worst = 0;
-        for (int i = 0; i < k; ++i) worst = std::max(worst, h_res[i] / std::fabs(h_lam[i]));
-        if (c.opt.verbose) fprintf(stderr, "[mgmlmc] deflation it %d worst rel residual %.3e\n", it, worst);
-        conv = worst <= tol;
-    }
+    Subspace S = subspace_buffers(c, l, b);
+    subspace_start(c, l, k, b, eig_solve_tol, S);
+    std::vector<double> h_lam;
+    const bool conv = subspace_iteration(c, l, k, b, tol, max_iters, eig_solve_tol, S, h_lam);
+    double2* X = S.X;
+    double2* T = S.T;
+    double* lam = S.lam;
     if (inexact) {
         // orthogonal projector on U = Gamma5 X (Sect. 2's Pi = U U^H) with the deflated
         // part recomputed from the approximate vectors by k extra solves
@@ -643,6 +748,7 @@ void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool ine
     c.defl.tau_re = htau.x;
     c.defl.tau_im = htau.y;
     c.defl.lambda.assign(h_lam.begin(), h_lam.begin() + k);
+    prepare_tc_deflation(c, c.defl);
     if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "compute_deflation: eigensolver did not reach tol (results kept)");
 }
 
@@ -686,10 +792,7 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "difference deflation: no hierarchy");
     MG_REQUIRE(a >= 0 && b > a && b < c.L, MGMLMC_EINVAL, "difference deflation: bad term");
     Deflation& D = c.ddefl[a];
-    c.dev_free(D.Lv);
-    c.dev_free(D.Rv);
-    c.dev_free(D.a);
-    D = Deflation();
+    free_one_deflation(c, D);
     if (k == 0) return;
     const Level& La = c.lev[a];
     const long long n = La.n;
@@ -704,35 +807,36 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
     double2* W = c.scratch<double2>("dd_W", (size_t)nb * nb);
     double* lam = c.scratch<double>("dd_lam", nb);
     double* res = c.scratch<double>("dd_res", nb);
-    const int groups = gemm_hn_groups(n, nb, nb);
-    double2* part = c.scratch<double2>("dd_part", (size_t)groups * nb * nb);
+    const bool fast = fast_block_products(n, nb, tol);
     launch_noise<double2>(X, n, nb, 0x2211153831ull, 78 + a, 0, c.stream);
-    orthonormalize(c, X, Y, n, nb);
+    orthonormalize(c, X, Y, n, nb, fast);
     std::vector<double> h_lam(nb), h_res(nb);
     bool conv = false;
     for (int it = 0; it < max_iters && !conv; ++it) {
         apply_J(c, a, b, X, Y, nb, eig_solve_tol);
         if ((it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) {
             std::swap(X, Y);               // X <- J X, orthonormalised
-            orthonormalize(c, X, Y, n, nb);
+            orthonormalize(c, X, Y, n, nb, fast);
             continue;
         }
         // Rayleigh-Ritz on span(X): H = X^H J X, largest |lambda| first
-        launch_gemm_hn<double2>(H, X, Y, n, nb, nb, part, groups, c.stream);
+        block_hn(c, fast, H, X, Y, n, nb, nb, "dd_part");
         k_hermitize<<<(nb * nb + 127) / 128, 128, 0, c.stream>>>(H, nb);
         small_launch_check();
         {
             ProfScope ps(c, "setup.jacobi", 0, 0);
-            launch_jacobi_eig(H, W, lam, nb, 40, c.stream, true);
+            launch_jacobi_eig(H, W, lam, nb, 40, c.scratch_bytes("jacobi_work", jacobi_work_bytes(nb)),
+                              device_error_flag(c), c.stream, true);
         }
-        launch_gemm_nn<double2>(Xr, X, W, (int)n, nb, nb, false, c.stream);
-        launch_gemm_nn<double2>(Yr, Y, W, (int)n, nb, nb, false, c.stream);
+        block_nn(c, fast, Xr, X, W, n, nb, nb);
+        block_nn(c, fast, Yr, Y, W, n, nb, nb);
         k_resid_cols<<<(unsigned)((n * nb + 255) / 256), 256, 0, c.stream>>>(Y, Yr, Xr, lam, n, nb);
         small_launch_check();
         column_norms(c, res, Y, n, nb);
         MG_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.stream));
         MG_CUDA(cudaMemcpyAsync(h_res.data(), res, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.stream));
         c.sync();
+        check_device_error(c);
         double worst = 0;
         for (int i = 0; i < k; ++i) worst = std::max(worst, h_res[i] / std::fabs(h_lam[i]));
         if (c.opt.verbose) fprintf(stderr, "[mgmlmc] difference deflation level %d it %d worst rel residual %.3e\n",
@@ -744,7 +848,7 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
         }
         // next iterate: J applied to the Ritz vectors, orthonormalised
         std::swap(X, Yr);
-        orthonormalize(c, X, Y, n, nb);
+        orthonormalize(c, X, Y, n, nb, fast);
     }
     if (!conv) {
         // the last Ritz vectors are the best available
@@ -794,6 +898,7 @@ void compute_difference_deflation(Ctx& c, int a, int b, int k, double tol, int m
     D.tau_re = htau.x;
     D.tau_im = htau.y;
     D.lambda.assign(h_lam.begin(), h_lam.begin() + k);
+    prepare_tc_deflation(c, D);
     if (!conv) throw Error(MGMLMC_ENOTCONVERGED, "difference deflation: eigensolver did not reach tol (results kept)");
 }
 
@@ -842,10 +947,7 @@ void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k) {
     MG_CUDA(cudaMemcpyAsync(Rv, R, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, c.stream));
     double2* Lv = c.alloc_n<double2>((size_t)n * k);
     apply_traced(c, a, b, Rv, Lv, k);
-    c.dev_free(D.Lv);
-    c.dev_free(D.Rv);
-    c.dev_free(D.a);
-    D = Deflation();
+    free_one_deflation(c, D);
     D.k = k;
     D.fine = a;
     D.coarse = b;
@@ -868,6 +970,7 @@ void set_deflation_vectors(Ctx& c, int a, int b, const double2* R, int k) {
     D.tau_im = htau.y;
     D.inexact = true;
     D.lambda.assign(k, 0.0);
+    prepare_tc_deflation(c, D);
 }
 
 }  // namespace mg

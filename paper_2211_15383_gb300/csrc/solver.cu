@@ -94,7 +94,7 @@ void apply_D(Ctx& c, int l, C* y, const C* x, const C* b, int N, int mode, doubl
     }
 }
 
-static int* device_error_flag(Ctx& c) {
+int* device_error_flag(Ctx& c) {
     if (!c.dev_err) {
         c.dev_err = c.scratch<int>("dev_err", 1);
         MG_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
@@ -361,6 +361,75 @@ static void mr_smooth(Ctx& c, int l, C* e, C* r, int N, int nu, bool e_zero, boo
     }
 }
 
+__global__ void k_sqrt_inplace(double* v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = sqrt(v[i]);
+}
+__global__ void k_add2(double2* a, const double2* b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
+}
+
+static void sqrt_inplace(Ctx& c, double* v, int n) {
+    k_sqrt_inplace<<<(n + 127) / 128, 128, 0, c.stream>>>(v, n);
+    MG_LAUNCHED();
+}
+
+template <typename C>
+static void norms(Ctx& c, double* out, const C* x, long long n, int N) {
+    double* part = c.scratch<double>("part_nrm", (size_t)reduce_groups(n, N) * N);
+    launch_norm2<C>(out, x, n, N, part, c.stream);
+    sqrt_inplace(c, out, N);
+}
+
+// K-cycle coarse-grid correction: e ~ D_l^{-1} r by k steps of flexible GMRES from
+// e = 0, preconditioned by the multigrid cycle of level l.  A fixed number of steps
+// with no convergence test, so nothing is read back to the host; the Arnoldi
+// bookkeeping (Givens rotations, least-squares solve) runs per rhs on the device.
+template <typename C>
+static void kcycle(Ctx& c, int l, C* e, const C* r, int N, int k) {
+    const Level& L = c.lev[l];
+    const long long n = L.n;
+    const size_t nN = (size_t)n * N;
+    const size_t sz = sizeof(C);
+    C* V = c.scratch<C>(nm("kc_V", l, sz), (size_t)(k + 1) * nN);
+    C* Z = c.scratch<C>(nm("kc_Z", l, sz), (size_t)k * nN);
+    double* beta = c.scratch<double>(nm("kc_beta", l, sz), N);
+    double* hnorm = c.scratch<double>(nm("kc_hn", l, sz), N);
+    double* resid = c.scratch<double>(nm("kc_res", l, sz), N);
+    double2* h = c.scratch<double2>(nm("kc_h", l, sz), (size_t)(k + 1) * N);
+    double2* y = c.scratch<double2>(nm("kc_y", l, sz), (size_t)(k + 1) * N);
+    double2* H = c.scratch<double2>(nm("kc_H", l, sz), (size_t)N * (k + 1) * k);
+    double* cs = c.scratch<double>(nm("kc_cs", l, sz), (size_t)N * k);
+    double2* sn = c.scratch<double2>(nm("kc_sn", l, sz), (size_t)N * k);
+    double2* g = c.scratch<double2>(nm("kc_g", l, sz), (size_t)N * (k + 1));
+    // own partials: the caller's FGMRES holds the pointer of its "part_md" across this call
+    double2* part = c.scratch<double2>(nm("kc_part", l, sz), (size_t)reduce_groups(n, N) * (k + 1) * N);
+    double* npart = c.scratch<double>(nm("kc_npart", l, sz), (size_t)axpy_groups(n, N) * N);
+    norms<C>(c, beta, r, n, N);
+    launch_scale_rhs<C, C>(V, r, beta, true, n, N, c.stream);
+    launch_init_g(g, beta, k, N, c.stream);
+    for (int j = 0; j < k; ++j) {
+        C* Vj = V + (size_t)j * nN;
+        C* Vn = V + (size_t)(j + 1) * nN;
+        C* Zj = Z + (size_t)j * nN;
+        mg_cycle<C>(c, l, Zj, Vj, N);
+        apply_D<C>(c, l, Vn, Zj, nullptr, N, 0, nullptr);
+        {
+            ProfScope ps(c, "orth." + std::string(prec_tag(sz)), (j + 2) * (double)nN * sz + (double)nN * sz,
+                         2.0 * 8.0 * (j + 1) * (double)nN);
+            launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
+            launch_multiaxpy_norm2<C>(Vn, h, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
+        }
+        sqrt_inplace(c, hnorm, N);
+        if (j + 1 < k) launch_scale_rhs<C, C>(Vn, Vn, hnorm, true, n, N, c.stream);
+        launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, k, N, c.stream);
+    }
+    launch_back_substitute(y, H, g, k - 1, k, N, c.stream);
+    launch_zero<C>(e, (long long)nN, c.stream);
+    launch_multiaxpy<C>(e, y, k, Z, 1.0, n, N, c.stream);
+}
+
 template <typename C>
 void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
     if (l == c.L - 1) {
@@ -381,7 +450,10 @@ void mg_cycle(Ctx& c, int l, C* e, const C* r, int N) {
     } else {
         apply_restrict<C>(c, l, rc, r, N);
     }
-    mg_cycle<C>(c, l + 1, ec, rc, N);
+    if (c.opt.kcycle_iters > 0 && l + 2 < c.L)
+        kcycle<C>(c, l + 1, ec, rc, N, c.opt.kcycle_iters);
+    else
+        mg_cycle<C>(c, l + 1, ec, rc, N);
     apply_prolong<C>(c, l, e, ec, N, !e_zero);
     if (c.opt.nu_post > 0 && !residual_smooth_tc<C>(c, l, e, r, N)) {
         apply_D<C>(c, l, res, e, r, N, 1, nullptr);
@@ -393,23 +465,6 @@ static double read_scalar(Ctx& c, const double* dev) {
     MG_CUDA(cudaMemcpyAsync(c.hbuf, dev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     c.sync();
     return c.hbuf[0];
-}
-
-__global__ void k_sqrt_inplace(double* v, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = sqrt(v[i]);
-}
-__global__ void k_add2(double2* a, const double2* b, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
-}
-
-template <typename C>
-static void norms(Ctx& c, double* out, const C* x, long long n, int N) {
-    double* part = c.scratch<double>("part_nrm", (size_t)reduce_groups(n, N) * N);
-    launch_norm2<C>(out, x, n, N, part, c.stream);
-    k_sqrt_inplace<<<(N + 127) / 128, 128, 0, c.stream>>>(out, N);
-    MG_LAUNCHED();
 }
 
 template <typename C>
@@ -520,7 +575,35 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
     return it;
 }
 
+static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok);
+
+// Blocks wider than opt.max_block_rhs (the eigensolvers' subspaces) are solved in
+// column chunks of at most that width, so the Krylov work space stays bounded.
 long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok) {
+    const int blk = c.opt.max_block_rhs;
+    if (N <= blk) return solve_block(c, l, b, x, N, tol, ok);
+    const long long n = c.lev[l].n;
+    double2* bb = c.scratch<double2>("sv_chunk_b", (size_t)n * blk);
+    double2* xb = c.scratch<double2>("sv_chunk_x", (size_t)n * blk);
+    const size_t w = sizeof(double2);
+    long long it = 0;
+    int all = 1;
+    for (int j0 = 0; j0 < N; j0 += blk) {
+        const int nb = std::min(blk, N - j0);
+        MG_CUDA(cudaMemcpy2DAsync(bb, nb * w, b + j0, (size_t)N * w, nb * w, (size_t)n, cudaMemcpyDeviceToDevice,
+                                  c.stream));
+        int okb = 0;
+        it += solve_block(c, l, bb, xb, nb, tol, &okb);
+        all &= okb;
+        MG_CUDA(cudaMemcpy2DAsync(x + j0, (size_t)N * w, xb, nb * w, nb * w, (size_t)n, cudaMemcpyDeviceToDevice,
+                                  c.stream));
+    }
+    *ok = all;
+    c.last_iters = it;
+    return it;
+}
+
+static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok) {
     const long long maxit = c.opt.max_iters;
     if (c.opt.mg_precision == 64) {
         const long long it = fgmres<double2>(c, l, b, x, N, tol, maxit, true, ok, 1 << 30);
@@ -547,7 +630,8 @@ long long solve(Ctx& c, int l, const double2* b, double2* x, int N, double tol, 
     MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * nN, cudaMemcpyDeviceToDevice, c.stream));
     long long it = 0;
     *ok = 0;
-    for (int cycle = 0; cycle < 40; ++cycle) {
+    // cycles until the FP64 residual meets tol or the iteration budget is spent
+    for (int cycle = 0;; ++cycle) {
         norms<double2>(c, rnorm, r, n, N);
         launch_max_ratio(maxr, rnorm, bnorm, N, c.stream);
         const double ratio = read_scalar(c, maxr);

@@ -43,3 +43,30 @@ def rel_sample_error(got, ref):
 
 def rand_complex(rng, shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def bf16_deflation_bound(defl, X, factors_rounded=False):
+    """Per-sample bound on how far the tensor-core deflation correction (factors
+    rounded to BF16, FP32 accumulation over n terms) can be from the correction
+    sum_m a_m conj(L_m^H x) (R_m^H x) that the oracle forms with defl's factors.
+
+    Rounding a part of a factor moves it by at most u = 2^-8 (+ 2^-24 for the FP32
+    step) of itself, so |dA_m| <= u ||R_m||_1 for +-1 entries; the FP32 sum of n
+    terms adds at most 2 n 2^-24 ||R_m||_1.  With factors_rounded the oracle already
+    uses the rounded factors and only the accumulation remains."""
+    n = X.shape[1]
+    acc = 2.0 * n * 2.0 ** -24
+    u = acc if factors_rounded else 2.0 ** -8 + 2.0 ** -24 + acc
+    Xt = np.ascontiguousarray(X.T).astype(np.complex128)
+    A = np.abs(defl.R.conj().T @ Xt)
+    B = np.abs(defl.L.conj().T @ Xt)
+    eA = 1.01 * u * np.abs(defl.R).sum(axis=0)[:, None]
+    eB = 1.01 * u * np.abs(defl.L).sum(axis=0)[:, None]
+    return np.sum(defl.a[:, None] * (eA * B + eB * A + eA * eB), axis=0)
+
+
+def within_bound(got, ref, bound, tol=1e-9):
+    """|s_gpu - s_ref| <= tol * max(|s_ref|, RMS) + bound, per sample."""
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    return bool(np.all(np.abs(got - ref) <= tol * np.maximum(np.abs(ref), rms) + bound))
+

@@ -9,7 +9,8 @@ from oracle import deflation as odefl
 from oracle import estimator as oest
 from oracle import hierarchy as ohier
 
-from gpu_common import make_ctx, rel_sample_error, require_gpu, small_problem
+from gpu_common import bf16_deflation_bound, make_ctx, rel_sample_error, require_gpu, small_problem, within_bound
+from oracle import noise as onoise
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-9
@@ -50,6 +51,12 @@ def test_c1_samples_match_oracle(pkg, c1, prec):
             got, st = ctx.estimate_level(t, 0, w.nrhs, w.noise_seed)
             ref = oest.noise_samples(H, term, w.noise_seed, 0, w.nrhs, solvers,
                                      defl if term[1] is None else None)
+            if prec == 16 and term[1] is None:
+                # deflation projections on the tensor cores: BF16 factors, FP32 sums
+                X = onoise.z2_noise(w.noise_seed, term[0], 0, w.nrhs, H.D[term[0] - 1].shape[0])
+                assert within_bound(got, ref, bf16_deflation_bound(defl, X)), (prec, term)
+                assert rel_sample_error(got, ref) < 1e-2
+                continue
             assert rel_sample_error(got, ref) < TOL64, (prec, term)
             assert st["nsamples"] == w.nrhs
             assert abs(st["mean_re"] - ref.mean().real) < 1e-9 * max(1, abs(ref.mean()))
@@ -161,6 +168,50 @@ def test_deflation_by_given_vectors(pkg, c1):
         assert rel_sample_error(got, ref) < TOL64
 
 
+def test_tensor_core_deflation_matches_rounded_factors(pkg, c1):
+    # mg_precision 16 forms the deflation projections on the tensor cores from the
+    # factors rounded to BF16.  With given vectors that are BF16 numbers already
+    # (R = V exact) and L = A V rounded on both sides by the same rule, the samples
+    # equal the oracle's with the rounded factors up to FP32 accumulation, and the
+    # deflated part the estimate adds is the trace over those rounded factors.
+    from oracle import rounding
+    w, theta, sv, H, defl = c1
+    solvers = oest.DirectSolvers(H)
+    term = (2, None)
+    n = H.D[1].shape[0]
+    V, _ = np.linalg.qr(inputs.gaussian_complex(19, 4, (n, 12)))
+    V = rounding.bf16(V)
+    dref = odefl.bf16_factors(odefl.vector_deflation(H, term, V, solvers))
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16) as ctx:
+        ctx.set_term_deflation_vectors(1, V.T)
+        tau_used = ctx.term_deflated_part(1)
+        assert abs(tau_used - dref.trace_term()) < 1e-12 * abs(dref.trace_term())
+        got, _ = ctx.estimate_level(1, 0, 96, 21)
+        ref = oest.noise_samples(H, term, 21, 0, 96, solvers, dref)
+        X = onoise.z2_noise(21, 2, 0, 96, n)
+        assert within_bound(got, ref, bf16_deflation_bound(dref, X, factors_rounded=True))
+        # and the bound is tight enough to see a wrong factor: without the deflation
+        # the samples are far outside it
+        plain = oest.noise_samples(H, term, 21, 0, 96, solvers, None)
+        assert not within_bound(got, plain, bf16_deflation_bound(dref, X, factors_rounded=True))
+
+
+def test_tensor_core_deflation_keeps_estimate_unbiased(pkg, c1):
+    # exact deflation at mg_precision 16: BF16 projections in the samples, the trace
+    # over the same rounded factors in the estimate -> consistent with the exact trace
+    w, theta, sv, H, defl = c1
+    exact = np.trace(np.linalg.inv(H.D[0].toarray()))
+    with make_ctx(pkg, theta, w.m0, w.agg, w.nvec, sv, w.setup_iters, mg_precision=16) as ctx:
+        ctx.compute_deflation(w.k, 1e-10, 500)
+        tau_used = ctx.term_deflated_part(1)
+        tau64 = ctx.get_deflation(w.k, 2)[4]
+        assert tau_used != tau64 and abs(tau_used - tau64) < 1e-2 * abs(tau64)
+        res = ctx.estimate_trace(2e-2, 200000, 77, [1.0, 0.1])
+        assert res["converged"] == 1
+        assert abs(res["deflated_part"] - tau_used.real) < 1e-12 * abs(tau_used)
+        assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_inexact_deflation_keeps_estimate_unbiased(pkg, c1, prec):
     # loosely converged vectors (eigensolver 1e-1, inner solves 1e-3, as in the paper's
@@ -211,6 +262,23 @@ def test_three_levels_with_wide_coarse_blocks(pkg, prec):
             assert rel_sample_error(got, ref) < TOL64, (prec, term)
 
 
+@pytest.mark.parametrize("prec", [64, 16])
+def test_kcycle_coarse_correction(pkg, prec):
+    # 4 levels with a K-cycle (two FGMRES steps per coarse-grid correction on the
+    # levels above the coarsest): only the preconditioner changes, so every sample
+    # still meets the FP64 bar against the oracle's direct solves
+    # 16^2 -> 8^2 x 4 -> 4^2 x 8 -> 4 x 2 sites x 8 dof: no aggregation is complete
+    agg, nvec, m0 = ((2, 2), (2, 2), (2, 1)), (2, 4, 4), 0.02
+    theta, sv = small_problem(16, 16, 3.0, m0, agg, nvec, seed=41)
+    H = ohier.build_hierarchy(theta, m0, agg, nvec, sv, 2)
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, m0, agg, nvec, sv, 2, mg_precision=prec, kcycle_iters=2) as ctx:
+        for t, term in enumerate(oest.term_list(4)):
+            got, _ = ctx.estimate_level(t, 0, 40, 9)
+            ref = oest.noise_samples(H, term, 9, 0, 40, solvers)
+            assert rel_sample_error(got, ref) < TOL64, (prec, term)
+
+
 def test_concurrent_terms_on_separate_streams(pkg, c1):
     # the two terms of the 16x16 workload at once, each on its own context and CUDA
     # stream (one entry with device noise, one with caller probes): the second context
@@ -238,7 +306,9 @@ def test_concurrent_terms_on_separate_streams(pkg, c1):
         ref0 = oest.noise_samples(H, (1, 2), w.noise_seed, 16, 48, solvers)
         ref1 = oest.term_samples(H, (2, None), probes.astype(float), solvers, defl)
         assert rel_sample_error(outs[0], ref0) < TOL64
-        assert rel_sample_error(outs[1], ref1) < TOL64
+        # mg_precision 16: the deflation projections use BF16 factors on the tensor cores
+        assert within_bound(outs[1], ref1, bf16_deflation_bound(defl, probes.astype(float)))
+        assert cpy.term_deflated_part(1) == src.term_deflated_part(1)
         with pytest.raises(pkg.MgmlmcError):
             pkg.estimate_concurrent([ctxs[0], ctxs[0]], [0, 1], 0, 8, 1)   # one context twice
     finally:

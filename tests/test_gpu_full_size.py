@@ -12,7 +12,8 @@ from oracle import deflation as odefl
 from oracle import estimator as oest
 from oracle import hierarchy as ohier
 
-from gpu_common import make_ctx, rel_sample_error, require_gpu
+from gpu_common import bf16_deflation_bound, make_ctx, rel_sample_error, require_gpu, within_bound
+from oracle import noise as onoise
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -51,8 +52,13 @@ def test_full_size_sampled_parity(pkg, c2, prec):
         for t, term in enumerate(oest.term_list(3)):
             got, st = ctx.estimate_level(t, 0, w.nrhs, w.noise_seed)
             ref = oest.noise_samples(H, term, w.noise_seed, 0, nchk, solvers, defl if term[1] is None else None)
-            err = rel_sample_error(got[:nchk], ref)
-            assert err < 1e-9, (prec, term, err)
+            if prec == 16 and term[1] is None:
+                # tensor-core deflation projections: BF16 factors, FP32 sums
+                X = onoise.z2_noise(w.noise_seed, term[0], 0, nchk, H.D[term[0] - 1].shape[0])
+                assert within_bound(got[:nchk], ref, bf16_deflation_bound(defl, X)), (prec, term)
+            else:
+                err = rel_sample_error(got[:nchk], ref)
+                assert err < 1e-9, (prec, term, err)
             # every sample of the block is finite and the block statistics are consistent
             assert np.all(np.isfinite(got)) and st["nsamples"] == w.nrhs
             assert abs(st["mean_re"] - got.mean().real) < 1e-9 * max(1.0, abs(got.mean()))

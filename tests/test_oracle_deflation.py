@@ -120,3 +120,20 @@ def test_vector_deflation_unbiased_and_exact_limit():
     ex = deflation.difference_deflation(H, term, 3)
     dv = deflation.vector_deflation(H, term, ex.R, solvers)
     assert np.abs(estimator.deflated_operator(A, dv) - estimator.deflated_operator(A, ex)).max() < 1e-10 * np.abs(A).max()
+
+
+def test_sparse_triplets_match_dense_eigensolver():
+    # shift-invert Lanczos (eigsh at sigma = 0) gives the same k smallest |lambda| and
+    # the same deflated part as the dense Hermitian eigensolver
+    th = inputs.metropolis_u1(8, 8, 2.0, 20, 31)
+    D = wilson.wilson_dirac(th, 0.05)
+    g5 = np.tile([1.0, -1.0], D.shape[0] // 2)
+    for k in (4, 12):
+        dd = deflation.coarsest_deflation(D, g5, k)
+        ds = deflation.coarsest_deflation(D, g5, k, sparse=True)
+        assert np.allclose(np.sort(1 / dd.a), np.sort(1 / ds.a), rtol=1e-10, atol=0)
+        assert abs(dd.trace_term() - ds.trace_term()) < 1e-10 * abs(dd.trace_term())
+        Pd = dd.L @ dd.L.conj().T
+        Ps = ds.L @ ds.L.conj().T
+        assert np.abs(Pd - Ps).max() < 1e-9
+

@@ -33,7 +33,7 @@ def _structs():
     return {"mgmlmc_options": _lib.Options, "mgmlmc_level_stats": _lib.LevelStats,
             "mgmlmc_trace_result": _lib.TraceResult, "mgmlmc_server_options": _lib.ServerOptions,
             "mgmlmc_request": _lib.Request, "mgmlmc_request_result": _lib.RequestResult,
-            "mgmlmc_server_stats": _lib.ServerStats}
+            "mgmlmc_server_stats": _lib.ServerStats, "mgmlmc_tune_result": _lib.TuneResult}
 
 
 def test_struct_layout_matches_header(tmp_path):
@@ -112,6 +112,30 @@ def test_request_footprint_checks_and_grows(pkg):
     with pytest.raises(pkg.MgmlmcError) as e:
         pkg.request_footprint(_request(pkg, 64, [(4, 4)], [8], mg_precision=8))   # options as mgmlmc_create
     assert e.value.code == -1 and "mg_precision" in str(e.value)
+
+
+def test_footprint_of_deep_solver_hierarchies(pkg):
+    # the 1024^2 workload: a 3-term sum over 6 levels (three solver-only levels),
+    # 512 triplets of level 3; the model must admit one block of 128 rhs with
+    # restart 16 on a 288 GB GPU and refuse 1024 rhs with restart 24, which is how
+    # the autotuner's candidates are bounded
+    agg, nvec = [(4, 4), (2, 2), (2, 2), (2, 2), (2, 2)], [8] * 5
+    small = pkg.request_footprint(_request(pkg, 1024, agg, nvec, k=512, mg_precision=16, sum_levels=3,
+                                           max_block_rhs=128, fgmres_restart=16))
+    big = pkg.request_footprint(_request(pkg, 1024, agg, nvec, k=512, mg_precision=16, sum_levels=3,
+                                         max_block_rhs=1024, fgmres_restart=24))
+    assert small < 250e9 < big
+    # the deflated level is level 3 (262144 unknowns): more triplets cost more there
+    more = pkg.request_footprint(_request(pkg, 1024, agg, nvec, k=1024, mg_precision=16, sum_levels=3,
+                                          max_block_rhs=128, fgmres_restart=16))
+    assert more - small > 2 * 262144 * 512 * 16
+    # a K-cycle keeps extra Krylov bases on the coarse levels
+    kc = pkg.request_footprint(_request(pkg, 1024, agg, nvec, k=512, mg_precision=16, sum_levels=3,
+                                        max_block_rhs=128, fgmres_restart=16, kcycle_iters=2))
+    assert kc > small
+    with pytest.raises(pkg.MgmlmcError) as e:
+        pkg.request_footprint(_request(pkg, 64, [(4, 4), (2, 2)], [8, 8], sum_levels=4))   # > nlevels
+    assert e.value.code == -1
 
 
 def test_server_calls_without_a_device(pkg):
