@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="schwinger-1024x1024")
     ap.add_argument("--no-tune", action="store_true", help="keep the workload's block width (no autotuner)")
+    ap.add_argument("--k", type=int, default=-1,
+                    help="deflated triplets (default: the workload's; 0: no deflation, for small profiler cases)")
     ap.add_argument("--fp64-block", type=int, default=32, help="right-hand sides per block of the FP64 comparison")
     ap.add_argument("--fp64-deflation", action="store_true",
                     help="deflate the FP64 comparison too (its eigensolver runs in FP64)")
@@ -246,8 +248,11 @@ def roofline(report, peaks, fp64_peak, fp32_peak, cls=None):
             ach = bytes_l / per_launch_s / 1e9
             out = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    impl_l = st.get("impl_bytes", st["bytes"]) / st["count"]
     out.update({"kernel": cls, "launches": st["count"], "avg_launch_us": per_launch_s * 1e6,
                 "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
+                "implementation_bytes_per_launch": impl_l,
+                "implementation_GB_per_s": impl_l / per_launch_s / 1e9,
                 "traffic": ncu_traffic(cls), "share_of_profiled_time":
                     st["ms"] / sum(v["ms"] for v in report.values())})
     return out
@@ -273,8 +278,10 @@ def gauge_of(w):
     return _GAUGE[w.name]
 
 
-def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False):
-    """Context with the workload's hierarchy (and deflation); optionally autotuned."""
+def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False, test_vectors=None):
+    """Context with the workload's hierarchy (and deflation); optionally autotuned.
+    test_vectors: another context's test vectors, taken as they are (the same P and D_l
+    without running this precision's setup)."""
     t0 = time.time()
     opts = {"mg_precision": prec, "max_block_rhs": nrhs or w.nrhs, "kcycle_iters": w.kcycle}
     if restart:
@@ -283,7 +290,10 @@ def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False):
     ctx.set_gauge(gauge_of(w))
     ctx.set_mass(w.m0)
     t1 = time.time()
-    ctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
+    if test_vectors is None:
+        ctx.set_hierarchy(w.agg, w.nvec, w.start_vectors(), setup_iters=w.setup_iters, setup_tol=1e-12)
+    else:
+        ctx.set_hierarchy(w.agg, w.nvec, test_vectors, setup_iters=0)
     if w.skip:
         ctx.set_terms(list(w.skip))
     t2 = time.time()
@@ -302,7 +312,7 @@ def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False):
     tuned = None
     if tune:
         t4 = time.time()
-        tuned = ctx.autotune()
+        tuned = ctx.autotune(max_trials=6)
         setup["autotune_s"] = time.time() - t4
     return ctx, setup, tuned
 
@@ -371,9 +381,9 @@ def gpu_arm(args, rank, ws, local):
     import paper_2211_15383_gb300 as pkg
 
     w = inputs.workload(args.workload)
-    if args.block_rhs:
+    if args.block_rhs or args.k >= 0:
         import dataclasses
-        w = dataclasses.replace(w, nrhs=args.block_rhs)
+        w = dataclasses.replace(w, nrhs=args.block_rhs or w.nrhs, k=w.k if args.k < 0 else args.k)
     peaks = measured_peaks()
     fp64_peak = pkg.fma_peak(64)
     fp32_peak = pkg.fma_peak(32)
@@ -514,11 +524,14 @@ def gpu_arm(args, rank, ws, local):
     if not args.no_mixed:
         head_samples = [ctx.estimate_level(t, 0, min(N, 32), seed)[0] for t in range(nterms)]
         mixed_cost = per_term_rate(ctx, nterms, N, 10 ** 6, seed, torch)
+        tv = [ctx.get_test_vectors(l + 1, w.nvec[l]) for l in range(len(w.agg))]
         ctx.close()
         torch.cuda.empty_cache()
         n64 = min(N, args.fp64_block)
-        t0 = time.time()
-        octx, osetup, _ = make_ctx(pkg, w, 64, nrhs=n64, restart=16, k=w.k if args.fp64_deflation else 0)
+        # the FP64 contexts take the mixed context's test vectors: the same hierarchy (P,
+        # D_l), so their samples are the headline's, and no FP64 setup iteration runs
+        octx, osetup, _ = make_ctx(pkg, w, 64, nrhs=n64, restart=16, k=w.k if args.fp64_deflation else 0,
+                                   test_vectors=tv)
         oth_samples = [octx.estimate_level(t, 0, min(N, 32), seed)[0] for t in range(nterms)]
         errs = []
         for t in range(nterms):
@@ -543,7 +556,7 @@ def gpu_arm(args, rank, ws, local):
         torch.cuda.empty_cache()
         single_cost = None
         if args.single_rhs_samples > 0:
-            sctx, ssetup, _ = make_ctx(pkg, w, 64, nrhs=1, restart=16, k=0)
+            sctx, ssetup, _ = make_ctx(pkg, w, 64, nrhs=1, restart=16, k=0, test_vectors=tv)
             ns = args.single_rhs_samples
             for t in range(nterms):
                 sctx.estimate_level(t, 10 ** 6, 1, seed, samples=False)
@@ -563,13 +576,12 @@ def gpu_arm(args, rank, ws, local):
             out["time_to_trace"]["mixed_device_seconds_from_costs"] = mixed_est
             out["time_to_trace"]["fp64_batched"] = {
                 "seconds_excl_setup": sum(n * c for n, c in zip(Nt, f64_cost)),
-                "setup_hierarchy_s": osetup["hierarchy_s"],
                 "what": "projected: the mixed run's sample counts (identical samples) x the measured FP64 "
-                        "per-sample device cost of each term"}
+                        "per-sample device cost of each term; the FP64 context reuses the mixed setup's test "
+                        "vectors, so no FP64 setup time is measured"}
             if single_cost:
                 out["time_to_trace"]["fp64_single_rhs"] = {
                     "seconds_excl_setup": sum(n * c for n, c in zip(Nt, single_cost)),
-                    "setup_hierarchy_s": ssetup["hierarchy_s"],
                     "what": "projected as above from the single-rhs per-sample cost"}
     else:
         ctx.close()
@@ -598,14 +610,14 @@ def serving_run(pkg, args):
     then arriving as a Poisson stream at args.serving_load x that rate.  Each request is
     a whole problem (gauge field, hierarchy, deflation, MLMC loop to args.serving_tol);
     its time to trace runs from submission to result.  64^2 and 128^2 use 3 levels;
-    256^2 and 512^2 a 3-term sum with solver-only levels below it (coarsest 4096
-    unknowns).  Fixed per-term costs (level sizes) make every request's result
+    256^2 and 512^2 a 3-term sum with one solver-only level below it (4096 unknowns,
+    stored inverse).  Fixed per-term costs (level sizes) make every request's result
     independent of the load."""
     n = args.serving_requests
     rng = np.random.default_rng(20221115)
     sizes = (64, 128, 256, 512)
     shapes = {64: ((4, 4), (2, 2)), 128: ((4, 4), (2, 2)), 256: ((4, 4), (2, 2), (2, 2)),
-              512: ((4, 4), (2, 2), (2, 2), (2, 2))}
+              512: ((4, 4), (2, 2), (4, 4))}
     t0 = time.time()
     fields, starts = {}, {}
     for L in sizes:
@@ -682,8 +694,9 @@ def serving_run(pkg, args):
                             "device_peak_gb": max(peaks) / 1e9 if peaks else None}
     return {"requests_per_phase": n, "slots": args.serving_slots, "rel_tol": args.serving_tol,
             "mix": "lattices 64^2, 128^2, 256^2, 512^2, beta 3 (m0 -0.09, -0.04) and 5 (m0 -0.03, 0.02); "
-                   "3-term sums (4x4 then 2x2 aggregates, 8 test vectors; 256^2 and 512^2 with 1 and 2 "
-                   "solver-only levels below), k = 32 (64^2) / 64, mg_precision %d" % args.precision,
+                   "3-term sums (4x4 then 2x2 aggregates, 8 test vectors; 256^2 and 512^2 with one "
+                   "solver-only level below, 2x2 resp. 4x4 aggregates of level 3), k = 32 (64^2) / 64, "
+                   "mg_precision %d" % args.precision,
             "saturated": summary(res1, span1),
             "poisson": dict(summary(res2, span2), load=args.serving_load, arrival_rate_per_s=lam),
             "by_lattice": by_L,

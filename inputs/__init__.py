@@ -280,9 +280,9 @@ class Workload:
         return out
 
 
-# Near-critical mass of the 1024^2 workload (sigma_min(D) ~ 1e-3 on the 128^2 field of
-# the same recipe, python -m oracle.tune_mass schwinger-1024x1024 1e-3 --lattice 128).
-M0_1024 = -0.088359
+# Near-critical mass of the 1024^2 workload: sigma_min(D) ~ 1e-3 on the 256^2 field of
+# the same recipe (python -m oracle.tune_mass schwinger-1024x1024 1e-3 --lattice 256).
+M0_1024 = -0.081836
 
 # Mass of the 128^2 workload: chosen with the oracle so that sigma_min(D) ~ 1e-3
 # (value written by oracle/tune_mass.py into tests/golden/mass_128.json).
@@ -299,13 +299,15 @@ WORKLOADS = {
     "schwinger-256x256": Workload("schwinger-256x256", 256, 256, 5.0, -0.05,
                                   ((4, 4), (2, 2), (2, 2)), (8, 8, 8), 128, 512,
                                   gauge_seed=3001, noise_seed=6001, setup_seed=9001, skip=(4,)),
-    # 3-term sum (n = 2097152 / 1048576 / 262144 on levels 1..3) with three solver-only
-    # levels (65536, 16384, 4096 unknowns); m0 tuned with the oracle on a 128^2 field of
-    # the same recipe (tests/golden/mass_1024_at128.json)
+    # 3-term sum (n = 2097152 / 1048576 / 262144 on levels 1..3) with one solver-only
+    # level (4x4 aggregates of level 3: 32^2 sites x 16 = 16384 unknowns, stored
+    # inverse), so that the level-3 solves are two-grid solves with an exact coarse
+    # correction; m0 tuned with the oracle on a 256^2 field of the same recipe
+    # (tests/golden/mass_1024_at256.json)
     "schwinger-1024x1024": Workload("schwinger-1024x1024", 1024, 1024, 5.0, M0_1024,
-                                    ((4, 4), (2, 2), (2, 2), (2, 2), (2, 2)), (8, 8, 8, 8, 8), 512, 256,
-                                    gauge_seed=4001, noise_seed=8001, setup_seed=12001, skip=(4, 5, 6),
-                                    kcycle=2, defl_tol=1e-3, defl_iters=24),
+                                    ((4, 4), (2, 2), (4, 4)), (8, 8, 8), 512, 128,
+                                    gauge_seed=4001, noise_seed=8001, setup_seed=12001, skip=(4,),
+                                    defl_tol=1e-3, defl_iters=16),
 }
 
 

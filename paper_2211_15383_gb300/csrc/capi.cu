@@ -776,8 +776,10 @@ int mgmlmc_profile_report(mgmlmc_ctx* h, char* buf, size_t cap, size_t* needed) 
     bool first = true;
     char tmp[256];
     for (const auto& kv : c.prof.stats) {
-        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"count\": %lld, \"ms\": %.6f, \"bytes\": %.6e, \"flops\": %.6e}",
-                 first ? "" : ", ", kv.first.c_str(), kv.second.count, kv.second.ms, kv.second.bytes, kv.second.flops);
+        snprintf(tmp, sizeof(tmp),
+                 "%s\"%s\": {\"count\": %lld, \"ms\": %.6f, \"bytes\": %.6e, \"flops\": %.6e, \"impl_bytes\": %.6e}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.count, kv.second.ms, kv.second.bytes, kv.second.flops,
+                 kv.second.impl_bytes);
         js += tmp;
         first = false;
     }

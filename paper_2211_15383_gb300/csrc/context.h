@@ -74,6 +74,7 @@ struct TermStats {
 struct ProfStat {
     long long count = 0;
     double ms = 0, bytes = 0, flops = 0;
+    double impl_bytes = 0;           // bytes the implementation moves (>= the algorithmic bytes)
 };
 struct Profiler {
     bool on = false;
@@ -81,7 +82,7 @@ struct Profiler {
     struct Pending {
         std::string key;
         cudaEvent_t a, b;
-        double bytes, flops;
+        double bytes, flops, impl_bytes;
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
@@ -100,7 +101,8 @@ struct ProfScope {
     Ctx* c;
     bool active;
     Profiler::Pending p;
-    ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops);
+    // impl_bytes < 0: the implementation moves the algorithmic bytes
+    ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops, double impl_bytes = -1);
     ~ProfScope();
 };
 
@@ -150,6 +152,8 @@ struct Ctx {
         return reinterpret_cast<T*>(scratch_bytes(name, count * sizeof(T)));
     }
     void release_all();
+    // Frees the named work space whose names start with one of the prefixes.
+    void free_scratch(const std::vector<std::string>& prefixes);
     void free_hierarchy();
     void free_deflation();
     void sync();

@@ -53,6 +53,20 @@ void* Ctx::scratch_bytes(const std::string& name, size_t bytes) {
     return b.p;
 }
 
+void Ctx::free_scratch(const std::vector<std::string>& prefixes) {
+    sync();
+    for (auto it = ws.begin(); it != ws.end();) {
+        bool hit = false;
+        for (const auto& p : prefixes) hit |= it->first.compare(0, p.size(), p) == 0;
+        if (hit) {
+            dev_free(it->second.p);
+            it = ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 void Ctx::release_all() {
     if (stream) cudaStreamSynchronize(stream);
     for (auto& kv : owned) {
@@ -133,6 +147,7 @@ void Profiler::resolve() {
         s.ms += ms;
         s.bytes += p.bytes;
         s.flops += p.flops;
+        s.impl_bytes += p.impl_bytes;
         pool.push_back(p.a);
         pool.push_back(p.b);
     }
@@ -149,10 +164,10 @@ Profiler::~Profiler() {
     }
     for (auto e : pool) cudaEventDestroy(e);
 }
-ProfScope::ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops)
+ProfScope::ProfScope(Ctx& ctx, const std::string& key, double bytes, double flops, double impl_bytes)
     : c(&ctx), active(ctx.prof.on) {
     if (!active) return;
-    p = Profiler::Pending{key, c->prof.take(), c->prof.take(), bytes, flops};
+    p = Profiler::Pending{key, c->prof.take(), c->prof.take(), bytes, flops, impl_bytes < 0 ? bytes : impl_bytes};
     MG_CUDA(cudaEventRecord(p.a, c->stream));
 }
 ProfScope::~ProfScope() {
@@ -330,6 +345,8 @@ void column_norms(Ctx& c, double* out, const double2* x, long long n, int N);   
 // deeper the hierarchy, the more its coarse levels built from random vectors weaken
 // the first cycles).
 static int bootstrap_rounds(int nlevels) { return 2 + std::max(0, nlevels - 3); }
+constexpr int kSetupRestart = 64;
+constexpr int kRefreshRounds = 2;
 // Subspace iterations between Rayleigh-Ritz projections (and convergence checks).
 constexpr int kRayleighRitzEvery = 4;
 
@@ -457,6 +474,16 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
     launch_materialize_wilson(c.lev[0].A64, c.U64, c.m0, c.Lx, c.Lt, c.stream);
     rebuild_from(c, 0);
     if (setup_iters > 0) {
+        // The setup solves run nvec right-hand sides only, so their Krylov bases are
+        // small: they use a restart length of at least kSetupRestart, which keeps the
+        // low modes a hierarchy built from rough vectors still misses (a short restart
+        // stagnates on them near the critical mass).
+        struct RestartScope {
+            Ctx& c;
+            int keep;
+            ~RestartScope() { c.opt.fgmres_restart = keep; }
+        } restart_scope{c, c.opt.fgmres_restart};
+        c.opt.fgmres_restart = std::max(c.opt.fgmres_restart, kSetupRestart);
         // Keep the start vectors: the test vectors are defined by exact inverse
         // iteration from them.
         std::vector<double2*> raw(nlev - 1);
@@ -467,27 +494,35 @@ void build_hierarchy(Ctx& c, int nlev, const int* ax, const int* at, const int* 
                                     c.stream));
         }
         // Preconditioner bootstrap: a hierarchy built from random vectors is too weak
-        // for the near-critical solves of the inverse iteration, so first improve every
-        // level's vectors by a few rounds of approximate inverse iteration (one FGMRES
-        // cycle each).  This only shapes the preconditioner of the setup solves; the
-        // final test vectors come from the exact iteration below.
-        for (int round = 0; round < bootstrap_rounds(nlev); ++round)
-            for (int l = 0; l < nlev - 1; ++l) {
-                Level& L = c.lev[l];
-                const int nv = L.nvec;
-                double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
-                double2* X = c.scratch<double2>("setup_X", (size_t)L.n * nv);
-                double* nrm = c.scratch<double>("setup_nrm", nv);
-                launch_transpose(B, L.tv, nv, (int)L.n, c.stream);
-                approx_inverse(c, l, B, X, nv);
-                column_norms(c, nrm, X, L.n, nv);
-                launch_scale_rhs<double2, double2>(X, X, nrm, true, L.n, nv, c.stream);
-                launch_transpose(L.tv, X, L.n, nv, c.stream);
-                rebuild_from(c, l);
-            }
+        // for the near-critical solves of the inverse iteration, so first improve the
+        // vectors of levels from..L-1 by rounds of approximate inverse iteration (one
+        // FGMRES cycle each) on their current operators.  This only shapes the
+        // preconditioner of the setup solves; the final test vectors come from the
+        // exact iteration below.
+        auto bootstrap = [&](int from, int rounds) {
+            for (int round = 0; round < rounds; ++round)
+                for (int l = from; l < nlev - 1; ++l) {
+                    Level& L = c.lev[l];
+                    const int nv = L.nvec;
+                    double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
+                    double2* X = c.scratch<double2>("setup_X", (size_t)L.n * nv);
+                    double* nrm = c.scratch<double>("setup_nrm", nv);
+                    launch_transpose(B, L.tv, nv, (int)L.n, c.stream);
+                    approx_inverse(c, l, B, X, nv);
+                    column_norms(c, nrm, X, L.n, nv);
+                    launch_scale_rhs<double2, double2>(X, X, nrm, true, L.n, nv, c.stream);
+                    launch_transpose(L.tv, X, L.n, nv, c.stream);
+                    rebuild_from(c, l);
+                }
+        };
+        bootstrap(0, bootstrap_rounds(nlev));
         // Inverse iteration v <- D_l^{-1} v / ||.|| from the start vectors, level by
         // level top-down, each solve to setup_tol.
         for (int l = 0; l < nlev - 1; ++l) {
+            // the exact vectors of the levels above changed D_l and everything below it:
+            // adapt level l's preconditioner (its vectors and the levels under it) to
+            // those operators first
+            if (l > 0) bootstrap(l, kRefreshRounds);
             Level& L = c.lev[l];
             const int nv = L.nvec;
             double2* B = c.scratch<double2>("setup_B", (size_t)L.n * nv);
@@ -700,6 +735,16 @@ void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool ine
     MG_REQUIRE(k >= 1 && k <= n && k <= 1024, MGMLMC_EINVAL, "compute_deflation: 0 <= k <= min(n_L, 1024)");
     MG_REQUIRE(tol > 0 && max_iters >= 1, MGMLMC_EINVAL, "compute_deflation: tol > 0 and max_iters >= 1");
     const int b = (int)std::min<long long>(n, std::max(2 * k, k + 16));
+    // the eigensolver's blocks are not needed once the triplets are stored
+    struct FreeBlocks {
+        Ctx& c;
+        ~FreeBlocks() {
+            try {
+                c.free_scratch({"df_", "jacobi_work", "chol_work", "sv_chunk_"});
+            } catch (...) {
+            }
+        }
+    } free_blocks{c};
     Subspace S = subspace_buffers(c, l, b);
     subspace_start(c, l, k, b, eig_solve_tol, S);
     std::vector<double> h_lam;

@@ -416,8 +416,8 @@ static void kcycle(Ctx& c, int l, C* e, const C* r, int N, int k) {
         mg_cycle<C>(c, l, Zj, Vj, N);
         apply_D<C>(c, l, Vn, Zj, nullptr, N, 0, nullptr);
         {
-            ProfScope ps(c, "orth." + std::string(prec_tag(sz)), (j + 2) * (double)nN * sz + (double)nN * sz,
-                         2.0 * 8.0 * (j + 1) * (double)nN);
+            ProfScope ps(c, "orth." + std::string(prec_tag(sz)), (j + 1) * (double)nN * sz,
+                         2.0 * 8.0 * (j + 1) * (double)nN, (2 * j + 5) * (double)nN * sz);
             launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
             launch_multiaxpy_norm2<C>(Vn, h, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
         }
@@ -534,9 +534,12 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
             // classical Gram-Schmidt: twice in FP64; once in the FP32 inner solve of the
             // refinement loop, whose FP64 residual absorbs the loss of orthogonality
             {
+                // algorithmic bytes: the j+1 basis vectors read once per Gram-Schmidt pass;
+                // the implementation reads them twice (dot products, then the update) and
+                // reads w twice and writes it once per pass: (2j + 5) vectors
                 const int passes = (sz == sizeof(double2)) ? 2 : 1;
-                ProfScope ps(c, "orth." + std::string(prec_tag(sz)), passes * (2 * j + 5) * (double)nN * sz,
-                             passes * 2.0 * 8.0 * (j + 1) * (double)nN);
+                ProfScope ps(c, "orth." + std::string(prec_tag(sz)), passes * (j + 1) * (double)nN * sz,
+                             passes * 2.0 * 8.0 * (j + 1) * (double)nN, passes * (2 * j + 5) * (double)nN * sz);
                 // the last axpy also returns |Vn|^2 (its partials), saving a pass over Vn
                 double* npart = c.scratch<double>("part_nrm_ax", (size_t)axpy_groups(n, N) * N);
                 launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);

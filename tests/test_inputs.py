@@ -20,7 +20,7 @@ def test_parallel_metropolis_equals_serial():
 
 def test_workload_masses_come_from_the_oracle_tuning():
     # the masses of the tuned workloads are the ones python -m oracle.tune_mass wrote
-    for name, fname in [("schwinger-128x128", "mass_128.json"), ("schwinger-1024x1024", "mass_1024_at128.json")]:
+    for name, fname in [("schwinger-128x128", "mass_128.json"), ("schwinger-1024x1024", "mass_1024_at256.json")]:
         g = json.load(open(os.path.join(GOLDEN, fname)))
         assert g["workload"] == name
         assert inputs.workload(name).m0 == g["m0"]
@@ -29,9 +29,9 @@ def test_workload_masses_come_from_the_oracle_tuning():
 
 def test_workload_term_levels():
     w = inputs.workload("schwinger-1024x1024")
-    assert w.nlevels == 6 and w.term_levels == (1, 2, 3) and w.nterms == 3
+    assert w.nlevels == 4 and w.term_levels == (1, 2, 3) and w.nterms == 3
     dims = w.level_dims()
-    assert [lx * lt * d for lx, lt, d in dims] == [2097152, 1048576, 262144, 65536, 16384, 4096]
+    assert [lx * lt * d for lx, lt, d in dims] == [2097152, 1048576, 262144, 16384]
     w3 = inputs.workload("schwinger-256x256")
     assert w3.term_levels == (1, 2, 3) and [lx * lt * d for lx, lt, d in w3.level_dims()] == [131072, 65536, 16384,
                                                                                               4096]
