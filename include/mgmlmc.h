@@ -130,6 +130,13 @@ int mgmlmc_create(mgmlmc_ctx** out, const mgmlmc_options* opt, void* cuda_stream
 int mgmlmc_create_copy(mgmlmc_ctx** out, mgmlmc_ctx* src, void* cuda_stream, mgmlmc_alloc_fn alloc,
                        mgmlmc_free_fn free_fn, void* alloc_user);
 
+/* Replace the solver options of a context: block width, restart length, iteration
+ * cap, smoothing steps, coarse-grid correction, solve tolerance, verbosity (the
+ * setting mgmlmc_autotune makes, or a caller's).  mg_precision must stay what the
+ * context was created with (MGMLMC_EINVAL otherwise): it decides which operator
+ * copies the hierarchy holds.  Later calls use the new options. */
+int mgmlmc_set_options(mgmlmc_ctx* ctx, const mgmlmc_options* opt);
+
 /* Release every device allocation of the context, then the context. */
 void mgmlmc_destroy(mgmlmc_ctx* ctx);
 
@@ -353,6 +360,13 @@ int mgmlmc_fma_peak(int precision, double* flops_per_s);
  * gave up. */
 int mgmlmc_coarse_inverse_noalloc(mgmlmc_ctx* ctx, int nrhs, const float* x, float* y, void* stream);
 
+/* One timed setting of mgmlmc_autotune. */
+#define MGMLMC_TUNE_LOG 16
+typedef struct {
+    int block_rhs, fgmres_restart, nu_post, kcycle_iters;
+    double samples_per_s;
+} mgmlmc_tune_trial;
+
 /* Result of mgmlmc_autotune. */
 typedef struct {
     int block_rhs;        /* chosen opt.max_block_rhs                                  */
@@ -363,6 +377,7 @@ typedef struct {
     size_t footprint;     /* modelled device bytes of the chosen setting               */
     size_t budget;        /* the budget the candidates were held to                    */
     int trials;           /* settings timed                                            */
+    mgmlmc_tune_trial log[MGMLMC_TUNE_LOG];   /* the first trials, in order             */
 } mgmlmc_tune_result;
 
 /* Autotuner (no counterpart in the paper): chooses the block width, the FGMRES
@@ -371,8 +386,9 @@ typedef struct {
  * mgmlmc_request_footprint for the context's own shape) exceeds hbm_budget bytes
  * (0: 90 % of the free device memory plus what the context holds) are skipped; at
  * most max_trials others are timed on one block of samples of every term (a fixed
- * Z2 noise block; the context's statistics are not touched), widest blocks first,
- * then restart length, smoother steps and, with four levels or more, the K-cycle.
+ * Z2 noise block; the context's statistics are not touched): the three widest blocks
+ * that fit with a restart of at most 16, then restart length (8, 16, 24), smoother
+ * steps (2, 6) and, with four levels or more, the other coarse-grid correction.
  * The fastest becomes the context's setting; its work space is released.  Needs a
  * hierarchy (and the deflation, if any, already computed).  MGMLMC_ENOMEM if no
  * block width fits the budget. */
@@ -453,6 +469,10 @@ typedef struct {
     size_t peak_bytes;    /* device bytes the request's context held at most         */
     int retries;          /* re-admissions after a refused device allocation         */
     char error[160];      /* text of the failure ("" if none)                        */
+    int deflation_converged; /* 1: the deflation eigensolver reached defl_tol; 0: it
+                             stopped at defl_max_iters and the request went on with the
+                             factors it had (the estimate adds their own deflated
+                             trace, so it stays unbiased), or k = 0                    */
 } mgmlmc_request_result;
 
 typedef struct {

@@ -69,16 +69,27 @@ class Request(C.Structure):
 class RequestResult(C.Structure):
     _fields_ = [("status", C.c_int), ("result", TraceResult), ("queued_s", C.c_double), ("setup_s", C.c_double),
                 ("estimate_s", C.c_double), ("total_s", C.c_double), ("reserved_bytes", C.c_size_t),
-                ("peak_bytes", C.c_size_t), ("retries", C.c_int), ("error", C.c_char * 160)]
+                ("peak_bytes", C.c_size_t), ("retries", C.c_int), ("error", C.c_char * 160),
+                ("deflation_converged", C.c_int)]
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("block_rhs", C.c_int), ("fgmres_restart", C.c_int), ("nu_post", C.c_int),
+                ("kcycle_iters", C.c_int), ("samples_per_s", C.c_double)]
+
+
+TUNE_LOG = 16
 
 
 class TuneResult(C.Structure):
     _fields_ = [("block_rhs", C.c_int), ("fgmres_restart", C.c_int), ("nu_post", C.c_int),
                 ("kcycle_iters", C.c_int), ("samples_per_s", C.c_double), ("footprint", C.c_size_t),
-                ("budget", C.c_size_t), ("trials", C.c_int)]
+                ("budget", C.c_size_t), ("trials", C.c_int), ("log", TuneTrial * TUNE_LOG)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "log"}
+        d["log"] = [{k: getattr(t, k) for k, _ in TuneTrial._fields_} for t in self.log[:min(self.trials, TUNE_LOG)]]
+        return d
 
 
 class ServerStats(C.Structure):
@@ -110,6 +121,7 @@ SIGNATURES = [
     ("mgmlmc_compute_term_deflation", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int]),
     ("mgmlmc_get_term_deflation", C.c_int, [_P, C.c_int, _I, _D, _D, _D, _D]),
     ("mgmlmc_term_deflated_part", C.c_int, [_P, C.c_int, _D]),
+    ("mgmlmc_set_options", C.c_int, [_P, C.POINTER(Options)]),
     ("mgmlmc_autotune", C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(TuneResult)]),
     ("mgmlmc_compute_term_deflation_inexact", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int]),
     ("mgmlmc_set_term_deflation_vectors", C.c_int, [_P, C.c_int, C.c_int, _D]),
@@ -389,6 +401,14 @@ class Context:
         return lam, L, R, complex(tau[0], tau[1])
 
     # ---------------------------------------------------------------- estimation
+    def set_options(self, **kw):
+        o = Options()
+        C.memmove(C.byref(o), C.byref(self.options), C.sizeof(Options))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self._check(self.lib.mgmlmc_set_options(self.h, C.byref(o)))
+        self.options = o
+
     def autotune(self, hbm_budget: int = 0, max_trials: int = 10) -> dict:
         r = TuneResult()
         self._check(self.lib.mgmlmc_autotune(self.h, int(hbm_budget), int(max_trials), C.byref(r)))

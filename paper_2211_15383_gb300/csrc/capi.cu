@@ -287,6 +287,16 @@ void mgmlmc_destroy(mgmlmc_ctx* h) {
 
 const char* mgmlmc_last_error(const mgmlmc_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
 
+int mgmlmc_set_options(mgmlmc_ctx* h, const mgmlmc_options* opt) {
+    API_BEGIN(h)
+    MG_REQUIRE(opt, MGMLMC_EINVAL, "set_options: opt is NULL");
+    check_options(*opt);
+    MG_REQUIRE(opt->mg_precision == c.opt.mg_precision, MGMLMC_EINVAL,
+               "set_options: mg_precision is fixed for the life of a context");
+    c.opt = *opt;
+    API_END
+}
+
 int mgmlmc_set_gauge(mgmlmc_ctx* h, int Lx, int Lt, const double* theta) {
     API_BEGIN(h)
     MG_REQUIRE(theta, MGMLMC_EINVAL, "set_gauge: theta is NULL");
@@ -857,6 +867,7 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
     API_BEGIN(h)
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "autotune: no hierarchy");
     MG_REQUIRE(out && max_trials >= 1, MGMLMC_EINVAL, "autotune: bad argument");
+    std::memset(out, 0, sizeof(*out));
     size_t free_b = 0, total_b = 0;
     MG_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const size_t budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)(free_b + c.live_bytes));
@@ -911,8 +922,16 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
         MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        ++trials;
         const double rate = (double)c.nterms * q.N / (ms * 1e-3);
+        if (trials < MGMLMC_TUNE_LOG) {
+            mgmlmc_tune_trial& tr = out->log[trials];
+            tr.block_rhs = q.N;
+            tr.fgmres_restart = q.m;
+            tr.nu_post = q.nu;
+            tr.kcycle_iters = q.kc;
+            tr.samples_per_s = rate;
+        }
+        ++trials;
         if (rate > best_rate) {
             best_rate = rate;
             best = q;
@@ -920,15 +939,17 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
         return rate;
     };
     try {
-        // 1. block width: the widest that fit, at the current restart length
+        // 1. block width: the three widest that fit with a restart of at most 16 (the
+        //    restart is chosen next, for the width found here)
+        const int m1 = std::min(start.fgmres_restart, 16);
         std::vector<int> widths;
         for (int N : {1024, 512, 256, 128, 64, 32}) {
-            Cand q{N, start.fgmres_restart, start.nu_post, start.kcycle_iters};
+            Cand q{N, m1, start.nu_post, start.kcycle_iters};
             if (fits(q, nullptr)) widths.push_back(N);
         }
         MG_REQUIRE(!widths.empty(), MGMLMC_ENOMEM, "autotune: no block width fits the budget");
         for (size_t i = 0; i < widths.size() && i < 3 && trials < max_trials; ++i)
-            time_one(Cand{widths[i], start.fgmres_restart, start.nu_post, start.kcycle_iters});
+            time_one(Cand{widths[i], m1, start.nu_post, start.kcycle_iters});
         // 2. restart length, 3. smoother steps, 4. coarse-grid correction
         for (int m : {8, 16, 24}) {
             Cand q{best.N, m, best.nu, best.kc};

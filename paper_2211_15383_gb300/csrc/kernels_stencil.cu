@@ -9,9 +9,15 @@
 // with s_0 = sigma_1, s_1 = sigma_2, antiperiodic in time.  Each hop needs a
 // single complex multiply: (1 -+ s_mu) projects the 2-spinor onto one
 // component (e.g. (1 - sigma_1) psi = (a, -a) with a = psi_0 - psi_1).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace mg {
+
+// Threads of the one-rhs-per-thread CTAs: 128, or fewer for narrower blocks so that
+// no lane idles (N = 64: two warps).
+static int cta_threads(int N) { return std::min(128, (N + 31) / 32 * 32); }
 
 template <typename C, int MODE>
 __global__ void __launch_bounds__(256) k_wilson(C* __restrict__ y, const C* __restrict__ x, const C* __restrict__ b,
@@ -166,13 +172,13 @@ __global__ void __launch_bounds__(128) k_block_stencil_d(C* __restrict__ y, cons
                                                          int lt, int N, double2* __restrict__ part) {
     using R = re_t<C>;
     __shared__ C At[5 * D * D];
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int V = lx * lt;
     C dyx = czero<C>();
     R dyy = 0;
     for (int site = blockIdx.y; site < V; site += gridDim.y) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 5 * D * D; e += 128) {
+        for (int e = threadIdx.x; e < 5 * D * D; e += blockDim.x) {
             const int dir = e / (D * D), r = e % (D * D), c = r / D, bb = r % D;
             At[(dir * D + bb) * D + c] = A[(long long)site * 5 * D * D + e];
         }
@@ -223,13 +229,14 @@ __global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y
                                                           const float2* __restrict__ b, const float2* __restrict__ A,
                                                           int lx, int lt, int N, double2* __restrict__ part) {
     __shared__ float2 At[5 * D * D];
-    const int j = 2 * (blockIdx.x * 128 + threadIdx.x);
+    // blockDim.x threads (32..128) x 2 rhs each: blocks of 64 rhs use one-warp CTAs
+    const int j = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int V = lx * lt;
     float2 dyx0 = make_float2(0.f, 0.f), dyx1 = make_float2(0.f, 0.f);
     float dyy0 = 0.f, dyy1 = 0.f;
     for (int site = blockIdx.y; site < V; site += gridDim.y) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 5 * D * D; e += 128) {
+        for (int e = threadIdx.x; e < 5 * D * D; e += blockDim.x) {
             const int dir = e / (D * D), r = e % (D * D), c = r / D, bb = r % D;
             At[(dir * D + bb) * D + c] = A[(long long)site * 5 * D * D + e];
         }
@@ -345,10 +352,10 @@ __global__ void __launch_bounds__(128) k_block_diag_apply(C* __restrict__ y, con
                                                           const C* __restrict__ Minv, int nsites, int d, int N,
                                                           bool accumulate) {
     __shared__ C Ms[32 * 32];
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     for (int site = blockIdx.y; site < nsites; site += gridDim.y) {
         __syncthreads();
-        for (int e = threadIdx.x; e < d * d; e += 128) Ms[e] = Minv[(long long)site * d * d + e];
+        for (int e = threadIdx.x; e < d * d; e += blockDim.x) Ms[e] = Minv[(long long)site * d * d + e];
         __syncthreads();
         if (j >= N) continue;
         C xv[32];
@@ -368,10 +375,10 @@ __global__ void __launch_bounds__(128) k_block_diag_apply_d(C* __restrict__ y, c
                                                             const C* __restrict__ Minv, int nsites, int N,
                                                             bool accumulate) {
     __shared__ C Ms[D * D];
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     for (int site = blockIdx.y; site < nsites; site += gridDim.y) {
         __syncthreads();
-        for (int e = threadIdx.x; e < D * D; e += 128) Ms[e] = Minv[(long long)site * D * D + e];
+        for (int e = threadIdx.x; e < D * D; e += blockDim.x) Ms[e] = Minv[(long long)site * D * D + e];
         __syncthreads();
         if (j >= N) continue;
         C xv[D], acc[D];
@@ -393,13 +400,14 @@ template <typename C>
 void launch_block_diag_apply(C* y, const C* x, const C* Minv, int nsites, int d, int N, bool accumulate,
                              cudaStream_t s) {
     MG_REQUIRE(d <= 32, MGMLMC_EINVAL, "block-diagonal apply: d <= 32");
-    const int tiles = (N + 127) / 128;
+    const int th = cta_threads(N);
+    const int tiles = (N + th - 1) / th;
     int G = 16 * kNumSM / tiles;
     if (G > nsites) G = nsites;
     if (G < 1) G = 1;
-    if (d == 16) k_block_diag_apply_d<C, 16><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, N, accumulate);
-    else if (d == 8) k_block_diag_apply_d<C, 8><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, N, accumulate);
-    else k_block_diag_apply<C><<<dim3(tiles, G), 128, 0, s>>>(y, x, Minv, nsites, d, N, accumulate);
+    if (d == 16) k_block_diag_apply_d<C, 16><<<dim3(tiles, G), th, 0, s>>>(y, x, Minv, nsites, N, accumulate);
+    else if (d == 8) k_block_diag_apply_d<C, 8><<<dim3(tiles, G), th, 0, s>>>(y, x, Minv, nsites, N, accumulate);
+    else k_block_diag_apply<C><<<dim3(tiles, G), th, 0, s>>>(y, x, Minv, nsites, d, N, accumulate);
     MG_LAUNCHED();
 }
 
@@ -458,13 +466,13 @@ __global__ void __launch_bounds__(128) k_restrict_nv(C* __restrict__ xc, const C
                                                      int N) {
     extern __shared__ __align__(16) unsigned char smem_rp[];
     C* Ps = reinterpret_cast<C*>(smem_rp);
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int cx = lx / ax, ct = lt / at, hd = d / 2, na = ax * at;
     const int nP = na * d * NV;
     for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
         const int X = S % cx, T = S / cx;
         __syncthreads();
-        for (int e = threadIdx.x; e < nP; e += 128) {
+        for (int e = threadIdx.x; e < nP; e += blockDim.x) {
             const int q = e / (d * NV), r = e % (d * NV);
             const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
             Ps[e] = P[(long long)site * d * NV + r];
@@ -501,13 +509,13 @@ __global__ void __launch_bounds__(128) k_prolong_nv(C* __restrict__ x, const C* 
                                                     int N, bool accumulate) {
     extern __shared__ __align__(16) unsigned char smem_rp[];
     C* Ps = reinterpret_cast<C*>(smem_rp);
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int cx = lx / ax, ct = lt / at, hd = d / 2, na = ax * at;
     const int nP = na * d * NV;
     for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
         const int X = S % cx, T = S / cx;
         __syncthreads();
-        for (int e = threadIdx.x; e < nP; e += 128) {
+        for (int e = threadIdx.x; e < nP; e += blockDim.x) {
             const int q = e / (d * NV), r = e % (d * NV);
             const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
             Ps[e] = P[(long long)site * d * NV + r];
@@ -546,13 +554,13 @@ __global__ void __launch_bounds__(128) k_restrict_nvd(C* __restrict__ xc, const 
     extern __shared__ __align__(16) unsigned char smem_rp[];
     C* Ps = reinterpret_cast<C*>(smem_rp);
     constexpr int HD = D / 2;
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int cx = lx / ax, ct = lt / at, na = ax * at;
     const int nP = na * D * NV;
     for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
         const int X = S % cx, T = S / cx;
         __syncthreads();
-        for (int e = threadIdx.x; e < nP; e += 128) {
+        for (int e = threadIdx.x; e < nP; e += blockDim.x) {
             const int q = e / (D * NV), r = e % (D * NV);
             const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
             Ps[e] = P[(long long)site * D * NV + r];
@@ -594,13 +602,13 @@ __global__ void __launch_bounds__(128) k_prolong_nvd(C* __restrict__ x, const C*
     extern __shared__ __align__(16) unsigned char smem_rp[];
     C* Ps = reinterpret_cast<C*>(smem_rp);
     constexpr int HD = D / 2;
-    const int j = blockIdx.x * 128 + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int cx = lx / ax, ct = lt / at, na = ax * at;
     const int nP = na * D * NV;
     for (int S = blockIdx.y; S < cx * ct; S += gridDim.y) {
         const int X = S % cx, T = S / cx;
         __syncthreads();
-        for (int e = threadIdx.x; e < nP; e += 128) {
+        for (int e = threadIdx.x; e < nP; e += blockDim.x) {
             const int q = e / (D * NV), r = e % (D * NV);
             const int site = (X * ax + q % ax) + lx * (T * at + q / ax);
             Ps[e] = P[(long long)site * D * NV + r];
@@ -813,10 +821,12 @@ __device__ __forceinline__ uint32_t f2_bf(float2 v) {
 
 // Four rhs per thread: 16-byte accesses (four bf16x2 words), ten loads of a site in
 // flight per thread.  N % 4 == 0.
+// RPT right-hand sides per thread (4: 16-byte accesses, a warp spans 128 rhs; 2: 8-byte
+// accesses, 64 rhs, so that a block of 64 keeps every lane busy).
+template <int RPT>
 __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, const uint32_t* __restrict__ x,
                                                      const float2* __restrict__ U, float mass, int lx, int lt, int N,
                                                      double2* __restrict__ part) {
-    constexpr int RPT = 4;
     const int j = RPT * (blockIdx.x * kRhsTile + threadIdx.x);
     const int V = lx * lt;
     float2 dyx[RPT];
@@ -827,11 +837,17 @@ __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, c
         dyy[r] = 0.f;
     }
     auto ld4 = [&](long long idx, float2* v) {
-        const uint4 w = *reinterpret_cast<const uint4*>(x + idx);
-        v[0] = bf2_lo(w.x);
-        v[1] = bf2_lo(w.y);
-        v[2] = bf2_lo(w.z);
-        v[3] = bf2_lo(w.w);
+        if constexpr (RPT == 4) {
+            const uint4 w = *reinterpret_cast<const uint4*>(x + idx);
+            v[0] = bf2_lo(w.x);
+            v[1] = bf2_lo(w.y);
+            v[2] = bf2_lo(w.z);
+            v[3] = bf2_lo(w.w);
+        } else {
+            const uint2 w = *reinterpret_cast<const uint2*>(x + idx);
+            v[0] = bf2_lo(w.x);
+            v[1] = bf2_lo(w.y);
+        }
     };
     if (j < N) {
         const long long N2 = 2LL * N;
@@ -886,8 +902,13 @@ __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, c
                 w0[r] = f2_bf(o0);
                 w1[r] = f2_bf(o1);
             }
-            *reinterpret_cast<uint4*>(y + site * N2 + j) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-            *reinterpret_cast<uint4*>(y + site * N2 + N + j) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            if constexpr (RPT == 4) {
+                *reinterpret_cast<uint4*>(y + site * N2 + j) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4*>(y + site * N2 + N + j) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            } else {
+                *reinterpret_cast<uint2*>(y + site * N2 + j) = make_uint2(w0[0], w0[1]);
+                *reinterpret_cast<uint2*>(y + site * N2 + N + j) = make_uint2(w1[0], w1[1]);
+            }
         }
     }
     __shared__ double2 sh[2][kRowLanes][RPT * kRhsTile + 1];
@@ -897,14 +918,17 @@ __global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, c
         sh[1][threadIdx.y][RPT * threadIdx.x + r] = make_double2((double)dyy[r], 0.0);
     }
     __syncthreads();
-    // 128 rhs x 2 quantities = 256 sums: thread (x, y) adds the 8 row lanes of
-    // quantity y / 4, rhs 4 x + y % 4
-    const int q = threadIdx.y >> 2, jj = RPT * threadIdx.x + (threadIdx.y & 3);
-    const int jo = RPT * blockIdx.x * kRhsTile + jj;
-    if (jo < N) {
-        double2 acc = sh[q][0][jj];
-        for (int r = 1; r < kRowLanes; ++r) acc = cadd(acc, sh[q][r][jj]);
-        part[((long long)q * N + jo) * gridDim.y + blockIdx.y] = acc;
+    // RPT * 32 rhs x 2 quantities: thread t < 2 * RPT * 32 adds the 8 row lanes of
+    // quantity t / (RPT * 32), rhs t % (RPT * 32) of this block
+    const int t = threadIdx.y * kRhsTile + threadIdx.x;
+    if (t < 2 * RPT * kRhsTile) {
+        const int q = t / (RPT * kRhsTile), jj = t % (RPT * kRhsTile);
+        const int jo = RPT * blockIdx.x * kRhsTile + jj;
+        if (jo < N) {
+            double2 acc = sh[q][0][jj];
+            for (int r = 1; r < kRowLanes; ++r) acc = cadd(acc, sh[q][r][jj]);
+            part[((long long)q * N + jo) * gridDim.y + blockIdx.y] = acc;
+        }
     }
 }
 
@@ -941,8 +965,13 @@ __global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restri
 void launch_wilson_bf16(uint32_t* y, const uint32_t* x, const float2* U, double m0, int lx, int lt, int N,
                         double2* part, int groups, cudaStream_t s) {
     MG_REQUIRE(N % 4 == 0, MGMLMC_EINVAL, "BF16 Wilson operator: N a multiple of 4");
-    dim3 g((N / 4 + kRhsTile - 1) / kRhsTile, groups);
-    k_wilson_bf16<<<g, blk(), 0, s>>>(y, x, U, (float)(m0 + 2.0), lx, lt, N, part);
+    if (N % 128 == 0) {
+        dim3 g(N / 128, groups);
+        k_wilson_bf16<4><<<g, blk(), 0, s>>>(y, x, U, (float)(m0 + 2.0), lx, lt, N, part);
+    } else {
+        dim3 g((N / 2 + kRhsTile - 1) / kRhsTile, groups);
+        k_wilson_bf16<2><<<g, blk(), 0, s>>>(y, x, U, (float)(m0 + 2.0), lx, lt, N, part);
+    }
     MG_LAUNCHED();
 }
 
@@ -998,11 +1027,12 @@ template <int D>
 static bool bsd_f2(float2* y, const float2* x, const float2* b, const float2* A, int lx, int lt, int N, int mode,
                    double2* part, int groups, cudaStream_t s) {
     if (N % 2 != 0) return false;
-    dim3 g((N / 2 + 127) / 128, groups);
+    const int threads = std::min(128, (N / 2 + 31) / 32 * 32);
+    dim3 g((N / 2 + threads - 1) / threads, groups);
     switch (mode) {
-        case 0: k_block_stencil_f2<D, 0><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
-        case 1: k_block_stencil_f2<D, 1><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
-        default: k_block_stencil_f2<D, 2><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 0: k_block_stencil_f2<D, 0><<<g, threads, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 1: k_block_stencil_f2<D, 1><<<g, threads, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        default: k_block_stencil_f2<D, 2><<<g, threads, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
     }
     MG_LAUNCHED();
     return true;
@@ -1017,11 +1047,12 @@ template <typename C, int D>
 static void bsd_dispatch(C* y, const C* x, const C* b, const C* A, int lx, int lt, int N, int mode, double2* part,
                          int groups, cudaStream_t s) {
     if (bsd_f2<D>(y, x, b, A, lx, lt, N, mode, part, groups, s)) return;
-    dim3 g((N + 127) / 128, groups);
+    const int th = cta_threads(N);
+    dim3 g((N + th - 1) / th, groups);
     switch (mode) {
-        case 0: k_block_stencil_d<C, D, 0><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
-        case 1: k_block_stencil_d<C, D, 1><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
-        default: k_block_stencil_d<C, D, 2><<<g, 128, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 0: k_block_stencil_d<C, D, 0><<<g, th, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        case 1: k_block_stencil_d<C, D, 1><<<g, th, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        default: k_block_stencil_d<C, D, 2><<<g, th, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
     }
     MG_LAUNCHED();
 }
@@ -1076,27 +1107,28 @@ template <typename C, int NV>
 static void rp_launch(bool restrict_op, C* xc_or_x, const C* in, const C* P, int lx, int lt, int d, int ax, int at,
                       int N, bool accumulate, cudaStream_t s) {
     const int ncs = (lx / ax) * (lt / at);
-    const int tiles = (N + 127) / 128;
+    const int th = cta_threads(N);
+    const int tiles = (N + th - 1) / th;
     int G = 16 * kNumSM / tiles;
     if (G > ncs) G = ncs;
     if (G < 1) G = 1;
     const size_t sm = (size_t)ax * at * d * NV * sizeof(C);
     if (d == 2) {
-        if (restrict_op) k_restrict_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
-        else k_prolong_nvd<C, NV, 2, 4><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
+        if (restrict_op) k_restrict_nvd<C, NV, 2, 4><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
+        else k_prolong_nvd<C, NV, 2, 4><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
         MG_LAUNCHED();
         return;
     }
     if (d == 16) {
-        if (restrict_op) k_restrict_nvd<C, NV, 16, 1><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
-        else k_prolong_nvd<C, NV, 16, 1><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
+        if (restrict_op) k_restrict_nvd<C, NV, 16, 1><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N);
+        else k_prolong_nvd<C, NV, 16, 1><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, ax, at, N, accumulate);
         MG_LAUNCHED();
         return;
     }
     if (restrict_op)
-        k_restrict_nv<C, NV><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N);
+        k_restrict_nv<C, NV><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N);
     else
-        k_prolong_nv<C, NV><<<dim3(tiles, G), 128, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N, accumulate);
+        k_prolong_nv<C, NV><<<dim3(tiles, G), th, sm, s>>>(xc_or_x, in, P, lx, lt, d, ax, at, N, accumulate);
     MG_LAUNCHED();
 }
 

@@ -33,7 +33,8 @@ def _structs():
     return {"mgmlmc_options": _lib.Options, "mgmlmc_level_stats": _lib.LevelStats,
             "mgmlmc_trace_result": _lib.TraceResult, "mgmlmc_server_options": _lib.ServerOptions,
             "mgmlmc_request": _lib.Request, "mgmlmc_request_result": _lib.RequestResult,
-            "mgmlmc_server_stats": _lib.ServerStats, "mgmlmc_tune_result": _lib.TuneResult}
+            "mgmlmc_server_stats": _lib.ServerStats, "mgmlmc_tune_result": _lib.TuneResult,
+            "mgmlmc_tune_trial": _lib.TuneTrial}
 
 
 def test_struct_layout_matches_header(tmp_path):
