@@ -460,8 +460,8 @@ __device__ __forceinline__ bool grid_barrier(Sync* sy, unsigned nblocks) {
 __device__ __forceinline__ int ord(int i, int r, int bp) { return i == 0 ? 0 : 1 + (i - 1 + r) % (bp - 1); }
 
 __global__ void __launch_bounds__(kThreads) k_jacobi_grid(const double2* __restrict__ Hin, double2* A0, double2* A1,
-                                                          double2* Wp, double* part, Sync* sy, int b, int bp,
-                                                          int sweeps) {
+                                                          double2* Wp, double* part, double* rot, Sync* sy, int b,
+                                                          int bp, int sweeps) {
     extern __shared__ double sm_rot[];
     const int half = bp / 2;
     double* rc = sm_rot;                  // half each: c, s, Re e^{i phi}, Im e^{i phi}
@@ -518,8 +518,11 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(const double2* __restr
         __syncthreads();
         if (stop) break;
         for (int r = 0; r < bp - 1; ++r) {
-            for (int k = threadIdx.x; k < half; k += blockDim.x) {
-                int p = ord(k, r, bp), q = ord(bp - 1 - k, r, bp);
+            // each rotation of the round once, grid-wide (FP64 square roots and divisions
+            // run at 1/64 of the FP32 rate: computing all of them in every CTA cost more
+            // than the block updates), published in rot[4][half] ...
+            for (long long k = tid; k < half; k += nthr) {
+                int p = ord((int)k, r, bp), q = ord(bp - 1 - (int)k, r, bp);
                 if (p > q) { const int t = p; p = q; q = t; }
                 double c = 1.0, sn = 0.0, pr = 1.0, pi = 0.0;
                 if (q < b) {
@@ -536,7 +539,22 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(const double2* __restr
                         pi = hpq.y / a;
                     }
                 }
-                rc[k] = c; rs[k] = sn; rpr[k] = pr; rpi[k] = pi; rp[k] = p; rq[k] = q;
+                rot[k] = c;
+                rot[half + k] = sn;
+                rot[2 * half + k] = pr;
+                rot[3 * half + k] = pi;
+            }
+            if (!grid_barrier(sy, G)) return;
+            // ... and staged by every CTA into shared memory with the pair indices
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int p = ord(k, r, bp), q = ord(bp - 1 - k, r, bp);
+                if (p > q) { const int t = p; p = q; q = t; }
+                rc[k] = __ldcg(rot + k);
+                rs[k] = __ldcg(rot + half + k);
+                rpr[k] = __ldcg(rot + 2 * half + k);
+                rpi[k] = __ldcg(rot + 3 * half + k);
+                rp[k] = p;
+                rq[k] = q;
             }
             __syncthreads();
             // 2x2 blocks (P, Q): out = G_P^H B G_Q
@@ -635,7 +653,8 @@ size_t jacobi_smem_bytes(int b) {
 
 size_t jacobi_work_bytes(int b) {
     const size_t bp = (size_t)(b + (b & 1));
-    return 3 * bp * bp * sizeof(double2) + (2 * (size_t)kNumSM * 4 + bp) * sizeof(double) + 256 + bp * sizeof(int);
+    return 3 * bp * bp * sizeof(double2) + (2 * (size_t)kNumSM * 4 + bp) * sizeof(double) + 256 + bp * sizeof(int) +
+           2 * bp * sizeof(double) + 256;
 }
 
 // Cholesky factor of a Hermitian positive definite b x b matrix G = R^H R (R upper)
@@ -748,10 +767,13 @@ void launch_jacobi_eig(double2* H, double2* W, double* lam, int b, int sweeps, v
     double2* Wp = reinterpret_cast<double2*>(w + 2 * mat);
     double* part = reinterpret_cast<double*>(w + 3 * mat);
     jac::Sync* sy = reinterpret_cast<jac::Sync*>(part + 2 * (size_t)kNumSM * 4 + bp);
+    // after Sync: the rank array (bp ints), then the rotations (4 x bp/2 doubles)
+    double* rot = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(reinterpret_cast<int*>(sy + 1) + bp) + 255) / 256 * 256);
     MG_CUDA(cudaMemsetAsync(sy, 0, sizeof(jac::Sync), s));
     const size_t sm = jacobi_smem_bytes(b);
-    void* args[] = {(void*)&H, (void*)&A0, (void*)&A1, (void*)&Wp, (void*)&part, (void*)&sy, (void*)&b, (void*)&bp,
-                    (void*)&sweeps};
+    void* args[] = {(void*)&H, (void*)&A0, (void*)&A1, (void*)&Wp, (void*)&part, (void*)&rot, (void*)&sy, (void*)&b,
+                    (void*)&bp, (void*)&sweeps};
     MG_CUDA(cudaLaunchCooperativeKernel((const void*)jac::k_jacobi_grid, dim3(G), dim3(jac::kThreads), args, sm, s));
     MG_LAUNCHED();
     int* rank = reinterpret_cast<int*>(sy + 1);
