@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--block-rhs", type=int, default=0,
                     help="override the workload's right-hand sides per block (smaller ncu captures)")
+    ap.add_argument("--restart", type=int, default=0,
+                    help="FGMRES restart length without the autotuner (0: the library default)")
     ap.add_argument("--nvtx", action="store_true",
                     help="mark the timed regions with NVTX ranges timed_f64 / timed_mixed / timed_e2e")
     ap.add_argument("--single-rhs-samples", type=int, default=1,
@@ -390,7 +392,8 @@ def gpu_arm(args, rank, ws, local):
     t_gauge = time.time()
     gauge_of(w)
     gauge_gen_s = time.time() - t_gauge
-    ctx, setup, tuned = make_ctx(pkg, w, args.precision, tune=not args.block_rhs and not args.no_tune)
+    ctx, setup, tuned = make_ctx(pkg, w, args.precision, restart=args.restart or None,
+                                 tune=not args.block_rhs and not args.no_tune and not args.restart)
     setup["gauge_generation_s"] = gauge_gen_s
     N = tuned["block_rhs"] if tuned else w.nrhs
     nterms, levels = ctx.num_terms()

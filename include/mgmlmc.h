@@ -189,6 +189,9 @@ int mgmlmc_num_terms(const mgmlmc_ctx* ctx, int* nterms, int* term_level /* [MGM
  * sign(Lambda), Sigma = |Lambda|, V = X), found by subspace iteration on
  * Q_L^{-1} with Rayleigh-Ritz until every residual ||Q x - lambda x|| <=
  * tol |lambda| (Sect. 4.3 uses tol = 1e-9), at most max_iters iterations.
+ * Each iteration's solves run to max(solve_tol, min(1e-6, 1e-3 tol)): any
+ * vectors leave the estimator unbiased, since tau below comes from the stored
+ * factors.
  * k = 0 removes deflation.  Also computes tau = tr(V Sigma^{-1} U^H) (Eq.
  * small_trace_term) in FP64 from the stored factors. */
 int mgmlmc_compute_deflation(mgmlmc_ctx* ctx, int k, double tol, int max_iters);

@@ -198,7 +198,8 @@ void build_hierarchy(Ctx& c, int nlevels, const int* ax, const int* at, const in
 // Exact deflation of the last term (fine level a): k smallest triplets of D_a.
 // With inexact, the vectors come from the eigensolver as they are and the
 // deflated part is recomputed from them (see store_deflation).
-// eig_solve_tol: tolerance of the eigensolver's solves (0: the context's solve_tol).
+// eig_solve_tol: tolerance of the eigensolver's solves (0: 1e-3 tol, within
+// [solve_tol, 1e-6]).
 void compute_deflation(Ctx& c, int a, int k, double tol, int max_iters, bool inexact = false,
                        double eig_solve_tol = 0);
 // Exact deflation of the difference term with fine level a and coarse level b

@@ -35,6 +35,9 @@ void launch_convert(Cout* y, const Cin* x, long long count, cudaStream_t s);
 // y[i][j] = scale[j] * x[i][j] (scale real, per rhs); scale may be inverted (1/scale, 0 if scale == 0)
 template <typename Cy, typename Cx_>
 void launch_scale_rhs(Cy* y, const Cx_* x, const double* scale, bool invert, long long n, int N, cudaStream_t s);
+// w[:, j] *= s[j] where s[j] != 0 (other columns untouched).
+template <typename C>
+void launch_scale_cols_if(C* w, const double* s, long long n, int N, cudaStream_t st);
 // y[i][j] += sign * alpha[j] * x[i][j]  (alpha complex per rhs, optionally times real beta[j])
 template <typename Cy, typename Cx_>
 void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sign, const Cx_* x,
@@ -59,14 +62,18 @@ void launch_norm2(double* out, const C* x, long long n, int N, double* part, cud
 template <typename C>
 void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, int N, double2* part,
                      cudaStream_t s);
-// w[i][j] += sign * sum_k coef[k][j] * V_k[i][j]
+// w[i][j] = (accumulate ? w[i][j] : 0) + sign * sum_k c[k][j] V_k[i][j], with
+// c[k][j] = coef[k][j], or coef[k][j] / eta[k][j]^eta_pow (eta_pow 1 or 2; 0 where eta is 0)
+// when eta is given: the coefficients of unnormalised basis vectors V_k = eta_k v_k.
 template <typename C>
 void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
-                      cudaStream_t s);
-// As launch_multiaxpy, and norm2[j] = |w_j|^2 of the updated w (part: axpy_groups(n, N) * N scratch).
+                      cudaStream_t s, const double* eta = nullptr, int eta_pow = 0, bool accumulate = true);
+// As launch_multiaxpy (accumulating), and norm2[j] = |w_j / norm_div[j]|^2 of the updated
+// w (norm_div NULL or 0: 1; part: axpy_groups(n, N) * N scratch).
 template <typename C>
 void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
-                            double* norm2, double* part, cudaStream_t s);
+                            double* norm2, double* part, cudaStream_t s, const double* eta = nullptr,
+                            int eta_pow = 0, const double* norm_div = nullptr);
 // Sum of partials: out[j] = sum_g part[g][j] (count = values per group).
 void launch_finalize(double2* out, const double2* part, int groups, int count, cudaStream_t s);
 void launch_finalize(double* out, const double* part, int groups, int count, cudaStream_t s);

@@ -73,6 +73,23 @@ __global__ void k_scale_rhs(Cy* __restrict__ y, const Cx_* __restrict__ x, const
     }
 }
 
+// w[:, j] *= s[j] for the rhs with s[j] != 0; the others are left untouched (and their
+// threads return after one load).
+template <typename C>
+__global__ void k_scale_cols_if(C* __restrict__ w, const double* __restrict__ s, long long n, int N) {
+    using R = re_t<C>;
+    const int j = blockIdx.x * kRhsTile + threadIdx.x;
+    if (j >= N) return;
+    const double sc = s[j];
+    if (sc == 0.0) return;
+    const R f = (R)sc;
+    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
+         i += (long long)gridDim.y * kRowLanes) {
+        const C v = w[i * N + j];
+        w[i * N + j] = mk(v.x * f, v.y * f);
+    }
+}
+
 template <typename Cy, typename Cx_>
 __global__ void k_axpy_rhs(Cy* __restrict__ y, const double2* __restrict__ alpha, const double* __restrict__ beta,
                            double sign, const Cx_* __restrict__ x, long long n, int N) {
@@ -189,7 +206,9 @@ __global__ void k_multidot(double2* __restrict__ part, const C* __restrict__ V, 
 
 template <typename C>
 __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef, int m, const C* __restrict__ V,
-                            double sign, long long n, int N, double* __restrict__ norm_part) {
+                            double sign, long long n, int N, double* __restrict__ norm_part,
+                            const double* __restrict__ eta, int eta_pow, int accumulate,
+                            const double* __restrict__ norm_div) {
     using R = re_t<C>;
     __shared__ C cf[64][kRhsTile];
     __shared__ double sh[kRowLanes][kRhsTile + 1];
@@ -197,17 +216,33 @@ __global__ void k_multiaxpy(C* __restrict__ w, const double2* __restrict__ coef,
     const long long stride = n * (long long)N;
     for (int k = threadIdx.y; k < m; k += kRowLanes) {
         double2 c = (j < N) ? coef[(long long)k * N + j] : make_double2(0, 0);
-        cf[k][threadIdx.x] = mk((R)(c.x * sign), (R)(c.y * sign));
+        double f = sign;
+        if (eta && j < N) {
+            // coefficient of an unnormalised vector V_k = eta_k v_k: divided by eta_k^pow
+            // (a zero vector contributes nothing)
+            const double e = eta[(long long)k * N + j];
+            const double d = eta_pow == 2 ? e * e : e;
+            f = (d != 0.0) ? sign / d : 0.0;
+        }
+        cf[k][threadIdx.x] = mk((R)(c.x * f), (R)(c.y * f));
     }
     __syncthreads();
+    // the norm is summed over w / norm_div[j] (FP32 squares of a small vector would
+    // leave the normal range)
+    R ns = (R)1;
+    if (norm_div && j < N) {
+        const double dv = norm_div[j];
+        ns = (R)((dv != 0.0) ? 1.0 / dv : 1.0);
+    }
     R nrm = 0;
     if (j < N)
         for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n;
              i += (long long)gridDim.y * kRowLanes) {
-            C acc = w[i * N + j];
+            C acc = accumulate ? w[i * N + j] : mk((R)0, (R)0);
             for (int k = 0; k < m; ++k) cfma(acc, cf[k][threadIdx.x], V[k * stride + i * N + j]);
             w[i * N + j] = acc;
-            nrm = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm));
+            const R ax = acc.x * ns, ay = acc.y * ns;
+            nrm = fma(ax, ax, fma(ay, ay, nrm));
         }
     if (norm_part) {
         // |w|^2 partials of the updated vector, as k_norm2 writes them
@@ -285,6 +320,11 @@ void launch_scale_rhs(Cy* y, const Cx_* x, const double* scale, bool invert, lon
     k_scale_rhs<Cy, Cx_><<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, s>>>(y, x, scale, invert, n, N);
     MG_LAUNCHED();
 }
+template <typename C>
+void launch_scale_cols_if(C* w, const double* s, long long n, int N, cudaStream_t st) {
+    k_scale_cols_if<C><<<dim3(rhs_tiles(N), row_groups(n, N)), blk(), 0, st>>>(w, s, n, N);
+    MG_LAUNCHED();
+}
 template <typename Cy, typename Cx_>
 void launch_axpy_rhs(Cy* y, const double2* alpha, const double* beta, double sign, const Cx_* x, long long n, int N,
                      cudaStream_t s) {
@@ -356,17 +396,23 @@ void launch_multidot(double2* out, const C* V, int m, const C* w, long long n, i
     launch_finalize(out, part, G, m * N, s);
 }
 template <typename C>
-void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N, cudaStream_t s) {
+void launch_multiaxpy(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N, cudaStream_t s,
+                      const double* eta, int eta_pow, bool accumulate) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
-    k_multiaxpy<C><<<dim3(rhs_tiles(N), axpy_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr);
+    MG_REQUIRE(!eta || eta_pow == 1 || eta_pow == 2, MGMLMC_EINVAL, "multiaxpy: eta_pow is 1 or 2");
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), axpy_groups(n, N)), blk(), 0, s>>>(w, coef, m, V, sign, n, N, nullptr, eta,
+                                                                          eta_pow, accumulate ? 1 : 0, nullptr);
     MG_LAUNCHED();
 }
 template <typename C>
 void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double sign, long long n, int N,
-                            double* norm2, double* part, cudaStream_t s) {
+                            double* norm2, double* part, cudaStream_t s, const double* eta, int eta_pow,
+                            const double* norm_div) {
     MG_REQUIRE(m >= 1 && m <= 64, MGMLMC_EINVAL, "multiaxpy: 1 <= m <= 64");
+    MG_REQUIRE(!eta || eta_pow == 1 || eta_pow == 2, MGMLMC_EINVAL, "multiaxpy: eta_pow is 1 or 2");
     const int G = axpy_groups(n, N);
-    k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part);
+    k_multiaxpy<C><<<dim3(rhs_tiles(N), G), blk(), 0, s>>>(w, coef, m, V, sign, n, N, part, eta, eta_pow, 1,
+                                                            norm_div);
     MG_LAUNCHED();
     launch_finalize(norm2, part, G, N, s);
 }
@@ -375,13 +421,15 @@ void launch_multiaxpy_norm2(C* w, const double2* coef, int m, const C* V, double
     template void launch_noise<C>(C*, long long, int, uint64_t, uint64_t, int64_t, cudaStream_t);    \
     template void launch_probes<C>(C*, const int8_t*, long long, int, cudaStream_t);                 \
     template void launch_zero<C>(C*, long long, cudaStream_t);                                       \
+    template void launch_scale_cols_if<C>(C*, const double*, long long, int, cudaStream_t);          \
     template void launch_norm2<C>(double*, const C*, long long, int, double*, cudaStream_t);         \
     template void launch_multidot<C>(double2*, const C*, int, const C*, long long, int, double2*,    \
                                      cudaStream_t);                                                  \
     template void launch_multiaxpy<C>(C*, const double2*, int, const C*, double, long long, int,     \
-                                      cudaStream_t);                                                 \
+                                      cudaStream_t, const double*, int, bool);                       \
     template void launch_multiaxpy_norm2<C>(C*, const double2*, int, const C*, double, long long, int, \
-                                            double*, double*, cudaStream_t);
+                                            double*, double*, cudaStream_t, const double*, int,        \
+                                            const double*);
 INST_C(double2)
 INST_C(float2)
 #define INST_CC(A, B)                                                                               \

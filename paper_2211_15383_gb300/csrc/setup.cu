@@ -297,6 +297,10 @@ __global__ void k_resid_cols(double2* R, const double2* QX, const double2* X, co
     const int col = (int)(e % b);
     R[e] = make_double2(QX[e].x - lam[col] * X[e].x, QX[e].y - lam[col] * X[e].y);
 }
+__global__ void k_reciprocal(double* v, int b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < b) v[i] = (v[i] != 0.0) ? 1.0 / v[i] : 1e300;
+}
 __global__ void k_sign_cols(double2* Y, const double* lam, long long n, int b) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= n * b) return;
@@ -650,11 +654,18 @@ static Subspace subspace_buffers(Ctx& c, int l, int b) {
 }
 
 // Subspace iteration on Q_l^{-1} = D_l^{-1} Gamma5^l from the orthonormal block S.X
-// (FP64-accurate solves to solve_tol), Rayleigh-Ritz with Q_l after the first
-// iteration, every kRayleighRitzEvery and after the last; stops once every one of
-// the k wanted Ritz pairs has ||Q x - lambda x|| <= tol |lambda|.  S.X holds the
-// Ritz vectors (by increasing |lambda|) and h_lam their values after the last
-// Rayleigh-Ritz step.
+// (FP64-accurate solves to solve_tol), with Rayleigh-Ritz after the first iteration,
+// every kRayleighRitzEvery and after the last; stops once every one of the k wanted
+// Ritz pairs has ||Q x - lambda x|| <= tol |lambda|.  S.X holds the Ritz vectors (by
+// increasing |lambda|) and h_lam their values after the last Rayleigh-Ritz step.
+//
+// The Rayleigh-Ritz step projects the iterated operator Q^{-1}, not Q: H = X^H Q^{-1} X
+// = X^H Y with the block Y = Q^{-1} X the solves just formed.  The wanted pairs (the
+// smallest |lambda| of Q) are the extremal ones of Q^{-1}, and extremal Ritz values are
+// never spurious.  Q itself is indefinite: on a block that still mixes eigenvectors of
+// +lambda and -lambda (a slow gap after the block's last eigenvalue) its Ritz values can
+// fall anywhere in the spectral gap around 0, below the wanted ones, and hold the
+// iteration there.
 static bool subspace_iteration(Ctx& c, int l, int k, int b, double tol, int max_iters, double solve_tol, Subspace& S,
                                std::vector<double>& h_lam) {
     const Level& L = c.lev[l];
@@ -664,31 +675,35 @@ static bool subspace_iteration(Ctx& c, int l, int k, int b, double tol, int max_
     h_lam.assign(b, 0.0);
     bool conv = false;
     for (int it = 0; it < max_iters && !conv; ++it) {
-        // X <- Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves), then orthonormalise
+        // Y = Q^{-1} X = D^{-1} Gamma5 X (FP64-accurate solves)
         launch_gamma5<double2>(S.T, S.X, L.nsites, L.d, b, c.stream);
         int ok = 0;
         solve(c, l, S.T, S.Y, b, solve_tol, &ok);
         MG_REQUIRE(ok, MGMLMC_ENOTCONVERGED, "deflation eigensolver: a solve did not converge");
-        std::swap(S.X, S.Y);
-        orthonormalize(c, S.X, S.Y, n, b, fast);
-        if (it > 0 && (it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) continue;
-        // Rayleigh-Ritz with Q = Gamma5 D
-        apply_D<double2>(c, l, S.T, S.X, nullptr, b, 0, nullptr);
-        launch_gamma5<double2>(S.T, S.T, L.nsites, L.d, b, c.stream);
-        block_hn(c, fast, S.H, S.X, S.T, n, b, b, "df_partR");
+        if (it > 0 && (it + 1) % kRayleighRitzEvery != 0 && it + 1 < max_iters) {
+            std::swap(S.X, S.Y);
+            orthonormalize(c, S.X, S.Y, n, b, fast);
+            continue;
+        }
+        // Rayleigh-Ritz with Q^{-1} on span(X): Ritz values mu = 1/lambda by decreasing |mu|
+        block_hn(c, fast, S.H, S.X, S.Y, n, b, b, "df_partR");
         k_hermitize<<<(b * b + 127) / 128, 128, 0, c.stream>>>(S.H, b);
         small_launch_check();
         {
             ProfScope ps(c, "setup.jacobi", 0, 0);
             launch_jacobi_eig(S.H, S.W, S.lam, b, 40, c.scratch_bytes("jacobi_work", jacobi_work_bytes(b)),
-                              device_error_flag(c), c.stream);
+                              device_error_flag(c), c.stream, true);
         }
-        block_nn(c, fast, S.Y, S.X, S.W, n, b, b);
-        block_nn(c, fast, S.T2, S.T, S.W, n, b, b);
-        std::swap(S.X, S.Y);
-        k_resid_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(S.T, S.T2, S.X, S.lam, n, b);
+        k_reciprocal<<<(b + 127) / 128, 128, 0, c.stream>>>(S.lam, b);
         small_launch_check();
-        column_norms(c, S.res, S.T, n, b);
+        block_nn(c, fast, S.T, S.X, S.W, n, b, b);    // Ritz vectors x = X w
+        block_nn(c, fast, S.T2, S.Y, S.W, n, b, b);   // Q^{-1} x: the next block
+        // residuals with Q itself: Y = Q x - lambda x
+        apply_D<double2>(c, l, S.X, S.T, nullptr, b, 0, nullptr);
+        launch_gamma5<double2>(S.X, S.X, L.nsites, L.d, b, c.stream);
+        k_resid_cols<<<(unsigned)((n * b + 255) / 256), 256, 0, c.stream>>>(S.Y, S.X, S.T, S.lam, n, b);
+        small_launch_check();
+        column_norms(c, S.res, S.Y, n, b);
         MG_CUDA(cudaMemcpyAsync(h_lam.data(), S.lam, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
         MG_CUDA(cudaMemcpyAsync(h_res.data(), S.res, sizeof(double) * b, cudaMemcpyDeviceToHost, c.stream));
         c.sync();
@@ -698,6 +713,12 @@ static bool subspace_iteration(Ctx& c, int l, int k, int b, double tol, int max_
         if (c.opt.verbose)
             fprintf(stderr, "[mgmlmc] deflation level %d it %d worst rel residual %.3e\n", l + 1, it, worst);
         conv = worst <= tol;
+        if (conv || it + 1 >= max_iters) {
+            std::swap(S.X, S.T);   // the Ritz vectors and their values
+        } else {
+            std::swap(S.X, S.T2);
+            orthonormalize(c, S.X, S.Y, n, b, fast);
+        }
     }
     return conv;
 }
@@ -725,7 +746,11 @@ static void subspace_start(Ctx& c, int l, int k, int b, double solve_tol, Subspa
 }
 
 void compute_deflation(Ctx& c, int l, int k, double tol, int max_iters, bool inexact, double eig_solve_tol) {
-    if (eig_solve_tol <= 0) eig_solve_tol = c.opt.solve_tol;
+    // The iteration's solves need a few digits beyond its Ritz tolerance, not the
+    // estimator's: any vectors leave the estimator unbiased (the deflated trace is taken
+    // from the stored factors), their accuracy only sets how much variance is removed,
+    // and convergence is judged on residuals of Q itself.
+    if (eig_solve_tol <= 0) eig_solve_tol = std::max(c.opt.solve_tol, std::min(1e-6, 1e-3 * tol));
     MG_REQUIRE(c.have_hier, MGMLMC_ESTATE, "compute_deflation: no hierarchy");
     MG_REQUIRE(l >= 0 && l < c.L, MGMLMC_EINVAL, "compute_deflation: bad level");
     free_one_deflation(c, c.defl);

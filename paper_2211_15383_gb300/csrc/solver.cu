@@ -370,6 +370,43 @@ __global__ void k_add2(double2* a, const double2* b, int n) {
     if (i < n) a[i] = make_double2(a[i].x + b[i].x, a[i].y + b[i].y);
 }
 
+// Unnormalised basis vectors are kept while eta = |w| lies in [2^-32, 2^32]: their FP32
+// entries, dot products and squared sums then stay far inside the normal range.
+constexpr double kEtaLow = 0x1p-32, kEtaHigh = 0x1p32;
+__device__ __forceinline__ void keep_eta(double* eta, double* rsc, double en) {
+    const bool out = en > 0.0 && (en < kEtaLow || en > kEtaHigh);
+    *rsc = out ? 1.0 / en : 0.0;   // the vector is rescaled to unit norm where rsc != 0
+    *eta = out ? 1.0 : en;
+}
+
+// Arnoldi column j of FGMRES with an unnormalised basis w_i = eta_i v_i (per rhs r):
+// on entry h[i] = <w_i, u> summed over the Gram-Schmidt passes and hn2 = |u' / eta_j|^2
+// for the orthogonalised u' (u = D M(w_j)); on exit h[i] = H_ij = h[i] / (eta_i eta_j),
+// hn2 = H_{j+1,j} = |u'| / eta_j, and w_{j+1} = u' has eta_{j+1} = |u'| (or is marked in
+// rsc for rescaling, eta_{j+1} = 1).  A zero eta_j (a zero vector, as a zero rhs or an
+// exhausted Krylov space gives) leaves a zero column.
+__global__ void k_lazy_column(double2* __restrict__ h, double* __restrict__ hn2, double* __restrict__ eta,
+                              double* __restrict__ rsc, int j, int N) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double ej = eta[(long long)j * N + r];
+    const double hs = sqrt(hn2[r]);
+    for (int i = 0; i <= j; ++i) {
+        const double d = eta[(long long)i * N + r] * ej;
+        const double f = (d != 0.0) ? 1.0 / d : 0.0;
+        const double2 v = h[(long long)i * N + r];
+        h[(long long)i * N + r] = make_double2(v.x * f, v.y * f);
+    }
+    hn2[r] = (ej != 0.0) ? hs : 0.0;
+    keep_eta(eta + (long long)(j + 1) * N + r, rsc + r, hs * ej);
+}
+
+// The same range check for the first basis vector of a cycle (eta_0 = |r|).
+__global__ void k_eta_range(double* __restrict__ eta, double* __restrict__ rsc, int N) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < N) keep_eta(eta + r, rsc + r, eta[r]);
+}
+
 static void sqrt_inplace(Ctx& c, double* v, int n) {
     k_sqrt_inplace<<<(n + 127) / 128, 128, 0, c.stream>>>(v, n);
     MG_LAUNCHED();
@@ -426,8 +463,7 @@ static void kcycle(Ctx& c, int l, C* e, const C* r, int N, int k) {
         launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, k, N, c.stream);
     }
     launch_back_substitute(y, H, g, k - 1, k, N, c.stream);
-    launch_zero<C>(e, (long long)nN, c.stream);
-    launch_multiaxpy<C>(e, y, k, Z, 1.0, n, N, c.stream);
+    launch_multiaxpy<C>(e, y, k, Z, 1.0, n, N, c.stream, nullptr, 0, false);   // e = Z y
 }
 
 template <typename C>
@@ -491,18 +527,33 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
     double2* g = c.scratch<double2>(nm("fg_g", 0, sz), (size_t)N * (m + 1));
     double2* part = c.scratch<double2>("part_md", (size_t)reduce_groups(n, N) * (m + 1) * N);
 
+    // The Arnoldi basis is kept unnormalised, w_i = eta_i v_i with eta_i = |w_i| per rhs
+    // (eta: (m + 1) x N): the Gram-Schmidt coefficients are divided by eta_i^2, the
+    // Hessenberg column by eta_i eta_j, and the correction takes y_j / eta_j of z_j =
+    // M(w_j).  This is FGMRES on the normalised basis exactly (the preconditioner of
+    // each step is whatever maps v_j to z_j / eta_j: no property of M is assumed) and
+    // saves the pass that would scale each new vector.  A vector whose eta leaves
+    // [2^-32, 2^32] (an iteration run on past convergence shrinks it by the FP32
+    // rounding level each step) is rescaled to unit norm, only for that rhs.
+    double* eta = c.scratch<double>(nm("fg_eta", 0, sz), (size_t)(m + 1) * N);
+    double* rsc = c.scratch<double>(nm("fg_rsc", 0, sz), N);
+    MG_REQUIRE(b != V || (x_zero && max_cycles == 1), MGMLMC_EINVAL,
+               "fgmres: a right-hand side in the basis needs x = 0 and one cycle");
     norms<C>(c, bnorm, b, n, N);
-    if (x_zero) launch_zero<C>(x, (long long)nN, c.stream);
+    // x = 0 is not written: the first correction overwrites x (or x is zeroed on exit)
+    bool x_unset = x_zero;
     long long it = 0;
     int cycles = 0;
     *ok = 0;
     for (;;) {
-        if (x_zero && it == 0)
-            MG_CUDA(cudaMemcpyAsync(V, b, sz * nN, cudaMemcpyDeviceToDevice, c.stream));
-        else
+        if (x_unset) {
+            if (b != V) MG_CUDA(cudaMemcpyAsync(V, b, sz * nN, cudaMemcpyDeviceToDevice, c.stream));
+            MG_CUDA(cudaMemcpyAsync(eta, bnorm, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream));
+        } else {
             apply_D<C>(c, l, V, x, b, N, 1, nullptr);
-        norms<C>(c, beta, V, n, N);
-        launch_max_ratio(maxr, beta, bnorm, N, c.stream);
+            norms<C>(c, eta, V, n, N);
+        }
+        launch_max_ratio(maxr, eta, bnorm, N, c.stream);
         const double ratio = read_scalar(c, maxr);
         if (ratio != ratio) throw Error(MGMLMC_ENAN, "FGMRES: NaN residual");
         if (c.opt.verbose)
@@ -513,8 +564,10 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
             break;
         }
         if (it >= maxit) break;
-        launch_scale_rhs<C, C>(V, V, beta, true, n, N, c.stream);
-        launch_init_g(g, beta, m, N, c.stream);
+        launch_init_g(g, eta, m, N, c.stream);
+        k_eta_range<<<(N + 127) / 128, 128, 0, c.stream>>>(eta, rsc, N);
+        MG_LAUNCHED();
+        launch_scale_cols_if<C>(V, rsc, n, N, c.stream);
         int j_end = -1;
         // Inner cycles of the refinement loop converge in a repeatable number of steps
         // per level and tolerance: the host reads the residual estimate (a round trip
@@ -544,18 +597,20 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
                 double* npart = c.scratch<double>("part_nrm_ax", (size_t)axpy_groups(n, N) * N);
                 launch_multidot<C>(h, V, j + 1, Vn, n, N, part, c.stream);
                 if (passes == 2) {
-                    launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream);
+                    launch_multiaxpy<C>(Vn, h, j + 1, V, -1.0, n, N, c.stream, eta, 2);
                     launch_multidot<C>(h2, V, j + 1, Vn, n, N, part, c.stream);
-                    launch_multiaxpy_norm2<C>(Vn, h2, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
+                    launch_multiaxpy_norm2<C>(Vn, h2, j + 1, V, -1.0, n, N, hnorm, npart, c.stream, eta, 2,
+                                              eta + (size_t)j * N);
                     k_add2<<<((j + 1) * N + 127) / 128, 128, 0, c.stream>>>(h, h2, (j + 1) * N);
                     MG_LAUNCHED();
                 } else {
-                    launch_multiaxpy_norm2<C>(Vn, h, j + 1, V, -1.0, n, N, hnorm, npart, c.stream);
+                    launch_multiaxpy_norm2<C>(Vn, h, j + 1, V, -1.0, n, N, hnorm, npart, c.stream, eta, 2,
+                                              eta + (size_t)j * N);
                 }
             }
-            k_sqrt_inplace<<<(N + 127) / 128, 128, 0, c.stream>>>(hnorm, N);
+            k_lazy_column<<<(N + 127) / 128, 128, 0, c.stream>>>(h, hnorm, eta, rsc, j, N);
             MG_LAUNCHED();
-            launch_scale_rhs<C, C>(Vn, Vn, hnorm, true, n, N, c.stream);
+            launch_scale_cols_if<C>(Vn, rsc, n, N, c.stream);
             launch_arnoldi_column(H, cs, sn, g, resid, h, hnorm, j, m, N, c.stream);
             ++it;
             j_end = j;
@@ -567,15 +622,23 @@ long long fgmres(Ctx& c, int l, const C* b, C* x, int N, double tol, long long m
         }
         if (hint) *hint = j_end + 1;
         launch_back_substitute(y, H, g, j_end, m, N, c.stream);
-        launch_multiaxpy<C>(x, y, j_end + 1, Z, 1.0, n, N, c.stream);
-        x_zero = false;
+        launch_multiaxpy<C>(x, y, j_end + 1, Z, 1.0, n, N, c.stream, eta, 1, !x_unset);
+        x_unset = false;
         if (++cycles >= max_cycles) {
             // the caller checks the residual itself (inner solve of the refinement loop)
             *ok = 1;
             break;
         }
     }
+    if (x_unset) launch_zero<C>(x, (long long)nN, c.stream);
     return it;
+}
+
+// The Krylov basis block of fgmres<C> for N right-hand sides on level l: a caller that
+// builds its rhs there (x = 0, one cycle) saves the copy into the basis.
+template <typename C>
+static C* fgmres_basis(Ctx& c, int l, int N) {
+    return c.scratch<C>(nm("fg_V", 0, sizeof(C)), (size_t)(c.opt.fgmres_restart + 1) * c.lev[l].n * N);
 }
 
 static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N, double tol, int* ok);
@@ -618,7 +681,8 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
     const long long n = L.n;
     const size_t nN = (size_t)n * N;
     double2* r = c.scratch<double2>("ir_r", nN);
-    float2* r32 = c.scratch<float2>("ir_r32", nN);
+    // the FP32 rhs of each inner cycle is built in the inner FGMRES's first basis vector
+    float2* r32 = fgmres_basis<float2>(c, l, N);
     float2* e32 = c.scratch<float2>("ir_e32", nN);
     double* bnorm = c.scratch<double>("ir_bn", N);
     double* rnorm = c.scratch<double>("ir_rn", N);

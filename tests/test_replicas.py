@@ -37,7 +37,7 @@ def _rank_main(rank, ws, port, out):
 def test_two_gloo_replicas():
     import torch.multiprocessing as mp
     ws = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank_main, args=(ws, _free_port(), out), nprocs=ws, join=True, start_method="spawn")
     times = [out[r][0] for r in range(ws)]
