@@ -690,8 +690,17 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
     // inner tolerance: the reduction still needed this cycle (with margin), but no
     // tighter than FP32 arithmetic can deliver
     const double inner_floor = 2e-7;
-    // below this multiple of tol the next residual may be updated with an FP32 product
-    constexpr double kRecursiveResidual = 500.0;
+    // The next residual comes from an FP32 product, r <- r - |r| D e: its error against
+    // the FP64 residual b - D x is below kFp32Drift |r| (FP32 rounding of D e, amplified
+    // where D e cancels).  drift bounds the error accumulated since the last FP64
+    // residual (relative to |b|, max over the rhs); the FP64 residual is recomputed once
+    // drift exceeds 1 % of the residual, and for the convergence decision unless drift is
+    // below tol / 20.  Cycles that reduce the residual a little (hard coarse solves)
+    // then share one FP64 residual, which on a coarse level costs as much as tens of FP32
+    // products (d = 16: 1/64 of the FP32 FMA rate); a cycle that reduces it a lot is
+    // followed by an FP64 residual as before.
+    constexpr double kFp32Drift = 1e-3;
+    double drift = 0.0;
     norms<double2>(c, bnorm, b, n, N);
     launch_zero<double2>(x, (long long)nN, c.stream);
     MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * nN, cudaMemcpyDeviceToDevice, c.stream));
@@ -703,6 +712,24 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
         launch_max_ratio(maxr, rnorm, bnorm, N, c.stream);
         const double ratio = read_scalar(c, maxr);
         if (ratio != ratio) throw Error(MGMLMC_ENAN, "refinement: NaN residual");
+        if (drift > 0.0 && (drift > 1e-2 * ratio || (ratio <= tol && drift > tol / 20))) {
+            double2* rrec = nullptr;
+            if (c.opt.verbose) {
+                rrec = c.scratch<double2>("ir_rrec", nN);
+                MG_CUDA(cudaMemcpyAsync(rrec, r, sizeof(double2) * nN, cudaMemcpyDeviceToDevice, c.stream));
+            }
+            apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
+            if (rrec) {
+                // the error the FP32 updates actually made, against the bound
+                launch_axpy_rhs<double2, double2>(rrec, nullptr, nullptr, -1.0, r, n, N, c.stream);
+                norms<double2>(c, rnorm, rrec, n, N);
+                launch_max_ratio(maxr, rnorm, bnorm, N, c.stream);
+                fprintf(stderr, "[mgmlmc] refine level %d FP64 residual: FP32 drift %.3e (bound %.3e)\n", l + 1,
+                        read_scalar(c, maxr), drift);
+            }
+            drift = 0.0;
+            continue;
+        }
         if (c.opt.verbose)
             fprintf(stderr, "[mgmlmc] refine level %d cycle %d it %lld rel res %.3e\n", l + 1, cycle, it, ratio);
         if (ratio <= tol) {
@@ -717,16 +744,10 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
         // ~1e-6 relative, so the FP64 residual of this loop decides on restarts
         it += fgmres<float2>(c, l, r32, e32, N, inner_tol, maxit - it, true, &iok, 1);
         launch_axpy_rhs<double2, float2>(x, nullptr, rnorm, 1.0, e32, n, N, c.stream);
-        if (ratio <= kRecursiveResidual * tol) {
-            // The residual is already small: r -= |r| D e with an FP32 product.  Its error
-            // (below 1e-4 of |r| even where D e cancels strongly) stays under tol / 20 of
-            // |b|, so the FP64 product is not needed for the last cycle.
-            float2* de = c.scratch<float2>("ir_de32", nN);
-            apply_D<float2>(c, l, de, e32, nullptr, N, 0, nullptr);
-            launch_axpy_rhs<double2, float2>(r, nullptr, rnorm, -1.0, de, n, N, c.stream);
-        } else {
-            apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
-        }
+        float2* de = c.scratch<float2>("ir_de32", nN);
+        apply_D<float2>(c, l, de, e32, nullptr, N, 0, nullptr);
+        launch_axpy_rhs<double2, float2>(r, nullptr, rnorm, -1.0, de, n, N, c.stream);
+        drift += kFp32Drift * ratio;
     }
     c.last_iters = it;
     check_device_error(c);

@@ -103,6 +103,32 @@ def test_skip_level_terms(pkg):
             assert rel_sample_error(got, ref) < TOL64, term
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("k", [4, 5])
+def test_deflation_above_a_solver_only_level(pkg, prec, k):
+    # the last term of the sum on level 2 of 3 (level 3 serves only the solver), its
+    # operator's k smallest triplets found by the eigensolver (subspace of b = 20 / 21):
+    # |lambda| of Q_2 = Gamma5 D_2 has a slow gap after the 21st (0.8107 / 0.8117), so a
+    # Rayleigh-Ritz step with Q_2 itself meets spurious Ritz values in the spectral gap
+    # around 0; the triplets, tau and the deflated samples must match the oracle's
+    agg, nvec, m0 = ((2, 2), (2, 2)), (2, 4), 0.05
+    theta = inputs.metropolis_u1(16, 16, 3.0, 20, 91)
+    sv = [inputs.start_vectors(91, 1, 16 * 16 * 2, 2), inputs.start_vectors(91, 2, 8 * 8 * 4, 4)]
+    H = ohier.build_hierarchy(theta, m0, agg, nvec, sv, 1)
+    defl = odefl.coarsest_deflation(H.D[1], H.g5[1], k)
+    solvers = oest.DirectSolvers(H)
+    with make_ctx(pkg, theta, m0, agg, nvec, sv, 1, mg_precision=prec) as ctx:
+        ctx.set_terms([3])
+        ctx.compute_deflation(k, 1e-10, 300)
+        lam, L, R, tau = ctx.get_term_deflation(1, k)
+        assert np.abs(np.sort(np.abs(lam)) - np.sort(np.abs(defl.lam))).max() < 1e-9
+        assert abs(tau - defl.trace_term()) < 1e-9 * abs(defl.trace_term())
+        for t, term in enumerate(oest.term_list(3, (3,))):
+            got, _ = ctx.estimate_level(t, 0, 24, 6)
+            ref = oest.noise_samples(H, term, 6, 0, 24, solvers, defl if term[1] is None else None)
+            assert rel_sample_error(got, ref) < TOL64, (prec, k, term)
+
+
 def test_mlmc_loop_matches_oracle_rule(pkg, c1):
     w, theta, sv, H, defl = c1
     solvers = oest.DirectSolvers(H)
