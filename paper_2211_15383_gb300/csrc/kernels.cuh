@@ -102,6 +102,8 @@ template <typename C>
 void launch_block_stencil(C* y, const C* x, const C* b, const C* A, int lx, int lt, int d, int N,
                           int mode, double2* part, int groups, cudaStream_t s);
 int stencil_groups(int nsites, int N);
+// Row groups (partials) of launch_wilson_bf16.
+int stencil_groups_bf16(int nsites, int N);
 // Row groups (grid.y) the block-stencil launcher expects for (nsites, d, N); the MR
 // partials array holds groups * 2 * N values.
 int block_stencil_groups(int nsites, int d, int N);

@@ -683,6 +683,13 @@ __global__ void k_gamma5(C* __restrict__ y, const C* __restrict__ x, long long r
 static inline dim3 blk() { return dim3(kRhsTile, kRowLanes); }
 
 int stencil_groups(int nsites, int N) { return row_groups(nsites, N, 8); }
+// k_wilson_bf16 launches N / 128 (four rhs per thread) or N / 64 column blocks of 256
+// threads, three resident per SM: row groups for one wave of three CTAs per SM.
+int stencil_groups_bf16(int nsites, int N) {
+    const int gx = (N % 128 == 0) ? N / 128 : (N / 2 + kRhsTile - 1) / kRhsTile;
+    const long long need = (nsites + kRowLanes - 1) / kRowLanes;
+    return (int)std::max(1LL, std::min(need, 3LL * kNumSM / gx));
+}
 
 // FP32 Wilson operator with two rhs per thread: 16-byte loads and stores (a warp
 // moves 512 B per access), half the index arithmetic per rhs.  N even.
@@ -824,9 +831,9 @@ __device__ __forceinline__ uint32_t f2_bf(float2 v) {
 // RPT right-hand sides per thread (4: 16-byte accesses, a warp spans 128 rhs; 2: 8-byte
 // accesses, 64 rhs, so that a block of 64 keeps every lane busy).
 template <int RPT>
-__global__ void __launch_bounds__(256) k_wilson_bf16(uint32_t* __restrict__ y, const uint32_t* __restrict__ x,
-                                                     const float2* __restrict__ U, float mass, int lx, int lt, int N,
-                                                     double2* __restrict__ part) {
+__global__ void __launch_bounds__(256, 3) k_wilson_bf16(uint32_t* __restrict__ y, const uint32_t* __restrict__ x,
+                                                        const float2* __restrict__ U, float mass, int lx, int lt,
+                                                        int N, double2* __restrict__ part) {
     const int j = RPT * (blockIdx.x * kRhsTile + threadIdx.x);
     const int V = lx * lt;
     float2 dyx[RPT];
@@ -937,7 +944,8 @@ __global__ void k_pack_bf16(uint32_t* __restrict__ y, const float2* __restrict__
     if (i < count) y[i] = f2_bf(x[i]);
 }
 
-// Two rhs per thread: 8-byte BF16 and 16-byte FP32 accesses.  N even.
+// Two rhs per thread: 8-byte BF16 and 16-byte FP32 accesses; two rows per loop trip
+// with all their loads issued first.  N even.
 __global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restrict__ r, const uint32_t* __restrict__ p,
                                       const double2* __restrict__ dots, long long n, int N, bool e_is_zero) {
     const int j = 2 * (blockIdx.x * kRhsTile + threadIdx.x);
@@ -949,16 +957,32 @@ __global__ void k_mr_update_fine_bf16(float2* __restrict__ e, uint32_t* __restri
         const double pp = dots[N + j + q].x;
         a[q] = pp > 0.0 ? make_float2((float)(pr.x / pp), (float)(pr.y / pp)) : make_float2(0.f, 0.f);
     }
-    for (long long i = (long long)blockIdx.y * kRowLanes + threadIdx.y; i < n; i += (long long)gridDim.y * kRowLanes) {
-        const long long idx = i * N + j;
-        const uint2 rw = *reinterpret_cast<const uint2*>(r + idx), pw = *reinterpret_cast<const uint2*>(p + idx);
-        float4 ev = e_is_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(e + idx);
-        const float2 r0 = bf2_lo(rw.x), r1 = bf2_lo(rw.y), p0 = bf2_lo(pw.x), p1 = bf2_lo(pw.y);
-        float2 e0 = make_float2(ev.x, ev.y), e1 = make_float2(ev.z, ev.w);
-        cfma(e0, a[0], r0);
-        cfma(e1, a[1], r1);
-        *reinterpret_cast<float4*>(e + idx) = make_float4(e0.x, e0.y, e1.x, e1.y);
-        *reinterpret_cast<uint2*>(r + idx) = make_uint2(f2_bf(csub(r0, cmul(a[0], p0))), f2_bf(csub(r1, cmul(a[1], p1))));
+    const long long S = (long long)gridDim.y * kRowLanes;
+    for (long long i0 = (long long)blockIdx.y * kRowLanes + threadIdx.y; i0 < n; i0 += 2 * S) {
+        uint2 rw[2], pw[2];
+        float4 ev[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long i = i0 + u * S;
+            const bool in = i < n;
+            const long long idx = i * N + j;
+            rw[u] = in ? *reinterpret_cast<const uint2*>(r + idx) : make_uint2(0u, 0u);
+            pw[u] = in ? *reinterpret_cast<const uint2*>(p + idx) : make_uint2(0u, 0u);
+            ev[u] = (in && !e_is_zero) ? *reinterpret_cast<const float4*>(e + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long i = i0 + u * S;
+            if (i >= n) break;
+            const long long idx = i * N + j;
+            const float2 r0 = bf2_lo(rw[u].x), r1 = bf2_lo(rw[u].y), p0 = bf2_lo(pw[u].x), p1 = bf2_lo(pw[u].y);
+            float2 e0 = make_float2(ev[u].x, ev[u].y), e1 = make_float2(ev[u].z, ev[u].w);
+            cfma(e0, a[0], r0);
+            cfma(e1, a[1], r1);
+            *reinterpret_cast<float4*>(e + idx) = make_float4(e0.x, e0.y, e1.x, e1.y);
+            *reinterpret_cast<uint2*>(r + idx) =
+                make_uint2(f2_bf(csub(r0, cmul(a[0], p0))), f2_bf(csub(r1, cmul(a[1], p1))));
+        }
     }
 }
 
@@ -983,8 +1007,17 @@ void launch_pack_bf16(uint32_t* y, const float2* x, long long count, cudaStream_
 void launch_mr_update_fine_bf16(float2* e, uint32_t* r, const uint32_t* p, const double2* dots, long long n, int N,
                                 bool e_is_zero, cudaStream_t s) {
     MG_REQUIRE(N % 2 == 0, MGMLMC_EINVAL, "BF16 MR update: N even");
-    k_mr_update_fine_bf16<<<dim3((N / 2 + kRhsTile - 1) / kRhsTile, row_groups(n, N)), blk(), 0, s>>>(e, r, p, dots,
-                                                                                                    n, N, e_is_zero);
+    // N / 64 column blocks (two rhs per thread): row groups for one wave of as many CTAs
+    // per SM as are resident
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mr_update_fine_bf16, kRhsTile * kRowLanes, 0));
+        per_sm = std::max(1, per_sm);
+    }
+    const int gx = (N / 2 + kRhsTile - 1) / kRhsTile;
+    const long long need = (n + kRowLanes - 1) / kRowLanes;
+    const int gy = (int)std::max(1LL, std::min(need, (long long)per_sm * kNumSM / gx));
+    k_mr_update_fine_bf16<<<dim3(gx, gy), blk(), 0, s>>>(e, r, p, dots, n, N, e_is_zero);
     MG_LAUNCHED();
 }
 

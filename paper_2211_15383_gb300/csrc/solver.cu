@@ -276,7 +276,7 @@ bool mr_smooth_fine_bf16<float2>(Ctx& c, int l, float2* e, float2* r, int N, int
     uint32_t* rb = c.scratch<uint32_t>("mrf_rb", nN);
     uint32_t* pb = c.scratch<uint32_t>("mrf_pb", nN);
     double2* dots = c.scratch<double2>(nm("mr_dots", 0, sizeof(float2)), 2 * (size_t)N);
-    const int groups = stencil_groups(L.nsites, N);
+    const int groups = stencil_groups_bf16(L.nsites, N);
     double2* part = c.scratch<double2>("part_st", (size_t)groups * 2 * N);
     {
         ProfScope ps(c, "pack1.bf16", (double)nN * (8 + 4), 0.0);
@@ -405,6 +405,24 @@ __global__ void k_lazy_column(double2* __restrict__ h, double* __restrict__ hn2,
 __global__ void k_eta_range(double* __restrict__ eta, double* __restrict__ rsc, int N) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < N) keep_eta(eta + r, rsc + r, eta[r]);
+}
+
+// out = max_j a_j b_j / c_j (terms with c_j = 0 skipped; NaN kept visible).
+__global__ void k_max_scaled_ratio(double* out, const double* a, const double* b, const double* cden, int N) {
+    __shared__ double sh[256];
+    double m = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double v = (cden[j] > 0.0) ? a[j] * b[j] / cden[j] : 0.0;
+        if (v != v) v = __longlong_as_double(0x7ff8000000000000ll);
+        if (!(v <= m)) m = v;
+    }
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st && !(sh[threadIdx.x + st] <= sh[threadIdx.x])) sh[threadIdx.x] = sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
 }
 
 static void sqrt_inplace(Ctx& c, double* v, int n) {
@@ -690,16 +708,21 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
     // inner tolerance: the reduction still needed this cycle (with margin), but no
     // tighter than FP32 arithmetic can deliver
     const double inner_floor = 2e-7;
-    // The next residual comes from an FP32 product, r <- r - |r| D e: its error against
-    // the FP64 residual b - D x is below kFp32Drift |r| (FP32 rounding of D e, amplified
-    // where D e cancels).  drift bounds the error accumulated since the last FP64
-    // residual (relative to |b|, max over the rhs); the FP64 residual is recomputed once
-    // drift exceeds 1 % of the residual, and for the convergence decision unless drift is
-    // below tol / 20.  Cycles that reduce the residual a little (hard coarse solves)
-    // then share one FP64 residual, which on a coarse level costs as much as tens of FP32
-    // products (d = 16: 1/64 of the FP32 FMA rate); a cycle that reduces it a lot is
-    // followed by an FP64 residual as before.
-    constexpr double kFp32Drift = 1e-3;
+    // The next residual comes from an FP32 product, r <- r - |r| D e.  Its error against
+    // the FP64 residual b - D x is below kFp32Product ||D|| |e| |r| (rounding of the FP32
+    // operator and of the product's sums), with ||D_l|| <= ||D_1|| <= |m0 + 2| + 4 (each
+    // hopping term has norm 1, the prolongators have orthonormal columns; a sqrt(d)
+    // margin for the entrywise rounding of the coarse blocks).  |e| carries the
+    // cancellation: a correction much longer than its residual (a rhs near the
+    // near-kernel, as in the setup's inverse iteration) makes the FP32 product inexact.
+    // drift bounds the error accumulated since the last FP64 residual (relative to |b|,
+    // max over the rhs); the FP64 residual is recomputed once drift exceeds 1 % of the
+    // residual, and for the convergence decision unless drift is below tol / 20.  Cycles
+    // that reduce the residual a little then share one FP64 residual, which on a coarse
+    // level costs as much as tens of FP32 products (d = 16: 1/64 of the FP32 FMA rate).
+    constexpr double kFp32Product = 32.0 * 0x1p-24;
+    const double dnorm = (std::fabs(c.m0 + 2.0) + 4.0) * (l > 0 ? std::sqrt((double)L.d) : 1.0);
+    double* enorm = c.scratch<double>("ir_en", N);
     double drift = 0.0;
     norms<double2>(c, bnorm, b, n, N);
     launch_zero<double2>(x, (long long)nN, c.stream);
@@ -747,7 +770,11 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
         float2* de = c.scratch<float2>("ir_de32", nN);
         apply_D<float2>(c, l, de, e32, nullptr, N, 0, nullptr);
         launch_axpy_rhs<double2, float2>(r, nullptr, rnorm, -1.0, de, n, N, c.stream);
-        drift += kFp32Drift * ratio;
+        // the bound of this update: max_j |e_j| |r_j| / |b_j|
+        norms<float2>(c, enorm, e32, n, N);
+        k_max_scaled_ratio<<<1, 256, 0, c.stream>>>(maxr, enorm, rnorm, bnorm, N);
+        MG_LAUNCHED();
+        drift += kFp32Product * dnorm * read_scalar(c, maxr);
     }
     c.last_iters = it;
     check_device_error(c);
