@@ -80,6 +80,12 @@ TermLevels term_levels(const Ctx& c, int t) {
 bool run_term_block(Ctx& c, const TermLevels& tl, const double2* X, int Nb, double2* smp, long long* iters) {
     const mg::Level& La = c.lev[tl.a];
     const double tol = c.opt.solve_tol;
+    struct Fp32Residuals {
+        Ctx& c;
+        bool keep;
+        ~Fp32Residuals() { c.fp32_residual_updates = keep; }
+    } fp32_residuals{c, c.fp32_residual_updates};
+    c.fp32_residual_updates = true;
     bool all_ok = true;
     int ok = 0;
     double2* Z = c.scratch<double2>("est_Z", (size_t)La.n * Nb);

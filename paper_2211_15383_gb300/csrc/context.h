@@ -136,6 +136,9 @@ struct Ctx {
     // iterations of the last inner FGMRES cycle, by level, rhs count and decade of its
     // tolerance
     std::map<long long, int> cycle_hint;
+    // the refinement loop may take its residuals from FP32 products between FP64 ones
+    // (the estimator's solves: Z2 right-hand sides, no strong cancellation in D e)
+    bool fp32_residual_updates = false;
 
     // ---- memory
     struct Buf { void* p = nullptr; size_t bytes = 0; };

@@ -708,7 +708,8 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
     // inner tolerance: the reduction still needed this cycle (with margin), but no
     // tighter than FP32 arithmetic can deliver
     const double inner_floor = 2e-7;
-    // The next residual comes from an FP32 product, r <- r - |r| D e.  Its error against
+    // In the estimator's solves (c.fp32_residual_updates) the next residual comes from an
+    // FP32 product, r <- r - |r| D e, between FP64 ones.  Its error against
     // the FP64 residual b - D x is below kFp32Product ||D|| |e| |r| (rounding of the FP32
     // operator and of the product's sums), with ||D_l|| <= ||D_1|| <= |m0 + 2| + 4 (each
     // hopping term has norm 1, the prolongators have orthonormal columns; a sqrt(d)
@@ -720,7 +721,13 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
     // residual, and for the convergence decision unless drift is below tol / 20.  Cycles
     // that reduce the residual a little then share one FP64 residual, which on a coarse
     // level costs as much as tens of FP32 products (d = 16: 1/64 of the FP32 FMA rate).
+    // Every other solve (the setup's inverse iteration and the eigensolvers, whose
+    // right-hand sides lie near the near-kernel) takes the FP64 residual after every
+    // cycle but the last: below 500 tol the FP32 product's error (under 1e-4 |r|) stays
+    // below tol / 20 of |b|.
     constexpr double kFp32Product = 32.0 * 0x1p-24;
+    constexpr double kRecursiveResidual = 500.0;
+    const bool fp32_updates = c.fp32_residual_updates;
     const double dnorm = (std::fabs(c.m0 + 2.0) + 4.0) * (l > 0 ? std::sqrt((double)L.d) : 1.0);
     double* enorm = c.scratch<double>("ir_en", N);
     double drift = 0.0;
@@ -767,9 +774,14 @@ static long long solve_block(Ctx& c, int l, const double2* b, double2* x, int N,
         // ~1e-6 relative, so the FP64 residual of this loop decides on restarts
         it += fgmres<float2>(c, l, r32, e32, N, inner_tol, maxit - it, true, &iok, 1);
         launch_axpy_rhs<double2, float2>(x, nullptr, rnorm, 1.0, e32, n, N, c.stream);
+        if (!fp32_updates && ratio > kRecursiveResidual * tol) {
+            apply_D<double2>(c, l, r, x, b, N, 1, nullptr);
+            continue;
+        }
         float2* de = c.scratch<float2>("ir_de32", nN);
         apply_D<float2>(c, l, de, e32, nullptr, N, 0, nullptr);
         launch_axpy_rhs<double2, float2>(r, nullptr, rnorm, -1.0, de, n, N, c.stream);
+        if (!fp32_updates) continue;   // the last cycle: accepted on this residual
         // the bound of this update: max_j |e_j| |r_j| / |b_j|
         norms<float2>(c, enorm, e32, n, N);
         k_max_scaled_ratio<<<1, 256, 0, c.stream>>>(maxr, enorm, rnorm, bnorm, N);
