@@ -201,15 +201,19 @@ def source_sha(fn):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if os.path.exists(path) else None
 
 
-def ncu_traffic(kclass):
+def ncu_traffic(kclass, impl_bytes_per_launch=None):
     """DRAM bytes per launch of a kernel class from a committed ncu summary, if the
-    kernel's source file has not changed since the counters were taken."""
+    kernel's source file has not changed since the counters were taken.  A class whose
+    per-launch work varies with the schedule (Gram-Schmidt: the Arnoldi index) stores
+    its measured traffic per implementation byte, scaled here to this run's launches."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     e = json.load(open(p)).get("classes", {}).get(kclass)
     if e is None or source_sha(e.get("source", "")) != e.get("source_sha"):
         return None
+    if e.get("per_implementation_byte") and impl_bytes_per_launch:
+        return e["per_implementation_byte"] * impl_bytes_per_launch
     return e.get("dram_bytes_per_launch")
 
 
@@ -255,7 +259,7 @@ def roofline(report, peaks, fp64_peak, fp32_peak, cls=None):
                 "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                 "implementation_bytes_per_launch": impl_l,
                 "implementation_GB_per_s": impl_l / per_launch_s / 1e9,
-                "traffic": ncu_traffic(cls), "share_of_profiled_time":
+                "traffic": ncu_traffic(cls, impl_l), "share_of_profiled_time":
                     st["ms"] / sum(v["ms"] for v in report.values())})
     return out
 
