@@ -318,7 +318,7 @@ def make_ctx(pkg, w, prec, nrhs=None, restart=None, k=None, tune=False, test_vec
     tuned = None
     if tune:
         t4 = time.time()
-        tuned = ctx.autotune(max_trials=6)
+        tuned = ctx.autotune(max_trials=8)
         setup["autotune_s"] = time.time() - t4
     return ctx, setup, tuned
 

@@ -892,10 +892,17 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
         return b <= budget;
     };
     const uint64_t kSeed = 0x2211153839ull;
-    int trials = 0, last_N = -1;
+    int trials = 0, last_N = -1, warm_m = 0, warm_kc = -1;
     double best_rate = -1;
     Cand best{start.max_block_rhs, start.fgmres_restart, start.nu_post, start.kcycle_iters};
+    std::vector<Cand> tried;
+    auto was_tried = [&](const Cand& q) {
+        for (const Cand& t : tried)
+            if (t.N == q.N && t.m == q.m && t.nu == q.nu && t.kc == q.kc) return true;
+        return false;
+    };
     auto time_one = [&](const Cand& q) -> double {
+        tried.push_back(q);
         c.opt.max_block_rhs = q.N;
         c.opt.fgmres_restart = q.m;
         c.opt.nu_post = q.nu;
@@ -912,10 +919,15 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
                            "autotune: a trial solve did not converge");
             }
         };
-        if (q.N != last_N) {                    // work space of this width: allocate untimed
-            release_scratch(c);
+        // work space of this width, a longer restart or another coarse-grid correction:
+        // allocated in an untimed run
+        if (q.N != last_N || q.m > warm_m || q.kc != warm_kc) {
+            if (q.N != last_N) release_scratch(c);
             run_all();
+            if (q.N != last_N) warm_m = 0;
             last_N = q.N;
+            warm_m = std::max(warm_m, q.m);
+            warm_kc = q.kc;
         }
         cudaEvent_t e0, e1;
         MG_CUDA(cudaEventCreate(&e0));
@@ -956,18 +968,20 @@ extern "C" int mgmlmc_autotune(mgmlmc_ctx* h, size_t hbm_budget, int max_trials,
         MG_REQUIRE(!widths.empty(), MGMLMC_ENOMEM, "autotune: no block width fits the budget");
         for (size_t i = 0; i < widths.size() && i < 3 && trials < max_trials; ++i)
             time_one(Cand{widths[i], m1, start.nu_post, start.kcycle_iters});
-        // 2. restart length, 3. smoother steps, 4. coarse-grid correction
-        for (int m : {8, 16, 24}) {
+        // 2. restart length: 8, then 4 where 8 won; 12; 24 where 16 still leads
+        for (int m : {8, 4, 12, 24}) {
+            if ((m == 4 && best.m != 8) || (m == 24 && best.m != 16)) continue;
             Cand q{best.N, m, best.nu, best.kc};
-            if (m != best.m && trials < max_trials && fits(q, nullptr)) time_one(q);
+            if (trials < max_trials && !was_tried(q) && fits(q, nullptr)) time_one(q);
         }
+        // 3. smoother steps, 4. coarse-grid correction
         for (int nu : {2, 6}) {
             Cand q{best.N, best.m, nu, best.kc};
-            if (nu != best.nu && trials < max_trials) time_one(q);
+            if (trials < max_trials && !was_tried(q)) time_one(q);
         }
         if (c.L >= 4) {
             Cand q{best.N, best.m, best.nu, best.kc > 0 ? 0 : 2};
-            if (trials < max_trials && fits(q, nullptr)) time_one(q);
+            if (trials < max_trials && !was_tried(q) && fits(q, nullptr)) time_one(q);
         }
     } catch (...) {
         c.opt = start;
