@@ -607,7 +607,10 @@ def gpu_arm(args, rank, ws, local):
                               "frac_of_measured_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                               "frac_of_8TBs": v["bytes"] / (v["ms"] * 1e-3) / 8e12,
                               "avg_launch_us": v["ms"] * 1e3 / v["count"], "launches": v["count"],
-                              "bytes_per_launch": v["bytes"] / v["count"]}
+                              "bytes_per_launch": v["bytes"] / v["count"],
+                              # DRAM bytes per launch from the committed ncu capture (null once
+                              # the kernel's source has changed)
+                              "traffic": ncu_traffic("D1.f32", v["bytes"] / v["count"])}
     return out, w
 
 

@@ -96,6 +96,31 @@ def test_results_same_alone_and_in_the_mix(pkg, mix):
     assert abs(res["trace"] - exact) < 5 * res["rel_err"] * abs(exact)
 
 
+@pytest.mark.slow
+def test_large_request_same_alone_and_in_the_mix(pkg, mix):
+    """A 256^2 request shaped like the serving benchmark's (a 3-term sum over 131072 /
+    65536 / 16384 unknowns with a solver-only level of 4096 below it, k = 64, BF16
+    smoother and deflation) gives the same rounds, sample counts and estimate alone
+    and while two small requests run beside it."""
+    L = 256
+    th = inputs.metropolis_u1(L, L, 5.0, 50, 5266)
+    agg = ((4, 4), (2, 2), (2, 2))
+    dims = [(L, L, 2), (L // 4, L // 4, 16), (L // 8, L // 8, 16)]
+    sv = [inputs.start_vectors(7256, i + 1, lx * lt * d, 8) for i, (lx, lt, d) in enumerate(dims)]
+    n0, n1, n2 = 2 * L * L, L * L, L * L // 4
+    big = pkg.make_request(th, -0.03, agg, (8, 8, 8), sv, 1e-2, 41, k=64, setup_iters=4, defl_tol=1e-3,
+                           defl_max_iters=60, costs=[(n0 + n1) / n0, (n1 + n2) / n0, n2 / n0], mg_precision=16,
+                           sum_levels=3)
+    alone = _serve(pkg, [big], max_active=1)[0][0]
+    assert alone["status"] == 0, alone["error"]
+    assert 0 < alone["peak_bytes"] <= alone["reserved_bytes"], (alone["peak_bytes"], alone["reserved_bytes"])
+    assert len(alone["result"]["terms"]) == 3
+    reqs, _ = mix
+    mixed, st = _serve(pkg, [reqs[0], big, reqs[1]], max_active=3)
+    assert st["max_active_seen"] >= 2 and st["completed"] == 3
+    _same(mixed[1], alone)
+
+
 def test_admission_under_a_small_budget(pkg, mix):
     reqs, _ = mix
     fp = pkg.request_footprint(reqs[0])
