@@ -510,11 +510,15 @@ def gpu_arm(args, rank, ws, local):
         t0 = time.time()
         res = ctx.estimate_trace(args.ttt_tol, 10 ** 7, seed + 1)
         tt = time.time() - t0
-        setup_s = sum(v for k_, v in setup.items() if k_.endswith("_s"))
+        # the library's setup of this problem: gauge upload, hierarchy, deflation and the
+        # autotuner; the host synthesis of the gauge field is input data, not counted
+        setup_s = sum(v for k_, v in setup.items() if k_.endswith("_s") and k_ != "gauge_generation_s")
+        tune_s = setup.get("autotune_s", 0.0)
         ttt = {"rel_tol": args.ttt_tol, "samples_per_term": [t["nsamples"] for t in res["terms"]]}
         out["time_to_trace"] = {
             "rel_tol": args.ttt_tol,
             "mixed": {"seconds_excl_setup": tt, "seconds_incl_setup": tt + setup_s,
+                      "seconds_incl_setup_excl_autotune": tt + setup_s - tune_s,
                       "trace": [res["trace"].real, res["trace"].imag], "rel_err": res["rel_err"],
                       "converged": bool(res["converged"]), "samples_per_term": ttt["samples_per_term"],
                       "variance_per_term": [t["variance"] for t in res["terms"]], "what": "measured"}}

@@ -204,29 +204,53 @@ void launch_gemm_hn_fp32(double2* Cm, const double2* A, const double2* B, long l
 // A[:, c] <- T A[:, c] = A[:, c] (rows S zeroed) + A[:, S] A[S, c], one complex GEMM
 // of depth kb, so the whole matrix is streamed once per panel instead of once per
 // column.
+// Pivot candidate of one elimination CTA for the next column of the panel: the largest
+// |A[i][k+1]|^2 over the CTA's rows i > k, ties to the smaller row index.
+struct GJCand {
+    double m;
+    int i;
+    int pad;
+};
 struct GJWork {
     int* perm;       // n
-    double2* fcol;   // n   column k before elimination
+    GJCand* cand;    // (n + 7) / 8 candidates of the next column (16 B each, n slots)
     int* status;     // 1 = zero pivot met
     void* rows;      // B x n copy of the panel's pivot rows (type C)
 };
+
+// |v|^2 in FP64 with separately rounded products, so that the pivot search of the
+// first column of a panel and the candidates of the others rank rows alike.
+template <typename C>
+__device__ __forceinline__ double gj_mag2(C v) {
+    return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
+}
+constexpr int kGJRowsPerCTA = 8;   // k_gj_eliminate: one warp per row
 
 template <typename C> struct GJPanel;
 template <> struct GJPanel<float2> { static constexpr int B = 32; };
 template <> struct GJPanel<double2> { static constexpr int B = 16; };
 
 // Step k of the panel [k0, k0 + kb): pivot search in column k (rows >= k), swap rows
-// k and p within the panel columns, scale the panel part of row k, save column k.
+// k and p within the panel columns, scale the panel part of row k.  The first column
+// of a panel is searched row by row; for the others the elimination of the previous
+// column left one candidate per CTA (ncand of them, in row order), which give the same
+// pivot: the largest |A[i][k]|^2, ties to the smallest row index.
 template <typename C>
-__global__ void __launch_bounds__(1024) k_gj_pivot(C* A, int n, int k, int k0, int kb, GJWork w) {
+__global__ void __launch_bounds__(1024) k_gj_pivot(C* A, int n, int k, int k0, int kb, GJWork w, int ncand) {
     __shared__ double best[1024];
     __shared__ int bidx[1024];
     double bv = -1.0;
     int bi = k;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        const C v = A[(long long)i * n + k];
-        const double m = (double)v.x * v.x + (double)v.y * v.y;
-        if (m > bv) { bv = m; bi = i; }
+    if (ncand > 0) {
+        for (int g = threadIdx.x; g < ncand; g += blockDim.x) {
+            const GJCand cd = w.cand[g];
+            if (cd.m > bv) { bv = cd.m; bi = cd.i; }
+        }
+    } else {
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double m = gj_mag2(A[(long long)i * n + k]);
+            if (m > bv) { bv = m; bi = i; }
+        }
     }
     best[threadIdx.x] = bv;
     bidx[threadIdx.x] = bi;
@@ -264,23 +288,47 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(C* A, int n, int k, int k0, i
         C v = (c == k) ? mk((decltype(piv.x))1, (decltype(piv.x))0) : A[(long long)k * n + c];
         A[(long long)k * n + c] = cmul(v, inv);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) w.fcol[i] = to_d(A[(long long)i * n + k]);
 }
 
 // Elimination of column k from every other row, within the panel columns: one warp
-// per row, lanes over the columns.
+// per row, lanes over the columns (kb <= 32: lane L owns column k0 + L).  The
+// multiplier is A[i][k] as the pivot step left it, read by every lane before the lane
+// of column k overwrites it.  When column k + 1 is in the panel, the CTA also leaves
+// the pivot candidate of that column among its rows i > k (w.cand[blockIdx.x]).
 template <typename C>
-__global__ void __launch_bounds__(256) k_gj_eliminate(C* A, int n, int k, int k0, int kb, GJWork w) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= n || i == k) return;
-    const C f = cvt<C>(w.fcol[i]);
-    for (int c = k0 + lane; c < k0 + kb; c += 32) {
-        const C pk = A[(long long)k * n + c];
-        const long long idx = (long long)i * n + c;
-        const C v = (c == k) ? czero<C>() : A[idx];
-        A[idx] = csub(v, cmul(f, pk));
+__global__ void __launch_bounds__(32 * kGJRowsPerCTA) k_gj_eliminate(C* A, int n, int k, int k0, int kb, GJWork w) {
+    __shared__ double cm[kGJRowsPerCTA];
+    __shared__ int ci[kGJRowsPerCTA];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = blockIdx.x * kGJRowsPerCTA + wid;
+    const bool next = k + 1 < k0 + kb;
+    double m = -1.0;
+    if (i < n && i != k) {
+        const C f = A[(long long)i * n + k];
+        __syncwarp();
+        const int c = k0 + lane;
+        if (c < k0 + kb) {
+            const C pk = A[(long long)k * n + c];
+            const long long idx = (long long)i * n + c;
+            const C v = (c == k) ? czero<C>() : A[idx];
+            const C r = csub(v, cmul(f, pk));
+            A[idx] = r;
+            if (c == k + 1 && i > k) m = gj_mag2(r);
+        }
+    }
+    if (!next) return;                                   // uniform over the grid
+    m = __shfl_sync(0xffffffffu, m, k + 1 - k0);
+    if (lane == 0) {
+        cm[wid] = m;
+        ci[wid] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bm = -1.0;
+        int bi = k + 1;
+        for (int q = 0; q < kGJRowsPerCTA; ++q)
+            if (cm[q] > bm) { bm = cm[q]; bi = ci[q]; }
+        w.cand[blockIdx.x] = GJCand{bm, bi, 0};
     }
 }
 
@@ -366,7 +414,7 @@ __global__ void k_gj_unpermute(C* A, int n, GJWork w) {
     }
 }
 
-// fcol (n double2) | perm (n int) | status | pad to 256 B | pivot rows (B x n, 256 n bytes
+// candidates (n slots of 16 B) | perm (n int) | status | pad to 256 B | pivot rows (B x n, 256 n bytes
 // for both instances: 32 x 8 B and 16 x 16 B per column)
 static size_t gj_rows_offset(int n) { return (((size_t)n * sizeof(double2) + (size_t)n * sizeof(int) + 64) + 255) / 256 * 256; }
 size_t gauss_jordan_work_bytes(int n) { return gj_rows_offset(n) + (size_t)n * 256 + 256; }
@@ -376,18 +424,19 @@ void launch_gauss_jordan(C* A, int n, void* work, cudaStream_t s) {
     constexpr int B = GJPanel<C>::B;
     static_assert(B * sizeof(C) == 256, "pivot-row buffer is 256 bytes per column");
     GJWork w;
-    w.fcol = reinterpret_cast<double2*>(work);
-    w.perm = reinterpret_cast<int*>(w.fcol + n);
+    w.cand = reinterpret_cast<GJCand*>(work);
+    w.perm = reinterpret_cast<int*>(reinterpret_cast<double2*>(work) + n);
     w.status = w.perm + n;
     w.rows = reinterpret_cast<char*>(work) + gj_rows_offset(n);
     MG_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s));
     long long launches = 0;
     const dim3 tiles((n + 63) / 64, (n + 63) / 64);
+    const int ncand = (n + kGJRowsPerCTA - 1) / kGJRowsPerCTA;   // <= n slots of 16 B
     for (int k0 = 0; k0 < n; k0 += B) {
         const int kb = n - k0 < B ? n - k0 : B;
         for (int k = k0; k < k0 + kb; ++k) {
-            k_gj_pivot<C><<<1, 1024, 0, s>>>(A, n, k, k0, kb, w);
-            k_gj_eliminate<C><<<(n + 7) / 8, 256, 0, s>>>(A, n, k, k0, kb, w);
+            k_gj_pivot<C><<<1, 1024, 0, s>>>(A, n, k, k0, kb, w, k > k0 ? ncand : 0);
+            k_gj_eliminate<C><<<ncand, 32 * kGJRowsPerCTA, 0, s>>>(A, n, k, k0, kb, w);
         }
         k_gj_swap_rows<C><<<(n + 255) / 256, 256, 0, s>>>(A, n, k0, kb, w);
         k_gj_update<C, B><<<tiles, 256, 0, s>>>(A, n, k0, kb, w);

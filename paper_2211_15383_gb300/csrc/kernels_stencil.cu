@@ -297,6 +297,120 @@ __global__ void __launch_bounds__(128) k_block_stencil_f2(float2* __restrict__ y
     }
 }
 
+// FP32 variant for d = 16 with four adjacent right-hand sides per thread and the 16
+// output rows of a site split over the two halves of the CTA (half h, uniform per warp,
+// computes rows 8h .. 8h + 7).  Each shared-memory read of a block entry serves four
+// rhs, 16 FMA per 8 bytes read, twice as many as with two rhs per thread, whose FMA pipe
+// waits on the shared-memory reads.  Per output the sums run in the same order as in
+// k_block_stencil_f2, so y is the same; the MODE 2 dots add the two halves last.
+// Block = 2 T threads with T = blockDim.x / 2 a multiple of 32; N % 4 == 0.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_block_stencil_f4(float2* __restrict__ y, const float2* __restrict__ x,
+                                                          const float2* __restrict__ b, const float2* __restrict__ A,
+                                                          int lx, int lt, int N, double2* __restrict__ part) {
+    constexpr int D = 16, H = 8;
+    __shared__ float2 At[5 * D * D];
+    __shared__ float red[MODE == 2 ? 64 * 12 : 1];     // half 1's dots, T <= 64
+    const int T = blockDim.x >> 1;
+    const int h = threadIdx.x >= T ? 1 : 0;
+    const int tq = threadIdx.x - h * T;
+    const int j = 4 * (blockIdx.x * T + tq);
+    const int V = lx * lt;
+    float2 dyx[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float dyy[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int site = blockIdx.y; site < V; site += gridDim.y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 5 * D * D; e += blockDim.x) {
+            const int dir = e / (D * D), r = e % (D * D), c = r / D, bb = r % D;
+            At[(dir * D + bb) * D + c] = A[(long long)site * 5 * D * D + e];
+        }
+        __syncthreads();
+        if (j < N) {
+            float2 a[H][4];
+#pragma unroll
+            for (int c = 0; c < H; ++c)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[c][r] = make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int dir = 0; dir < 5; ++dir) {
+                const int nb = nbr_site(site, dir, lx, lt);
+                const float2* xn = x + (long long)nb * D * N + j;
+                const float2* Ad = At + dir * D * D + h * H;
+                // the neighbour's rows in groups of 4, loads first (latency of L2 hits)
+#pragma unroll 1
+                for (int b0 = 0; b0 < D; b0 += 4) {
+                    float4 xv[4][2];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        xv[q][0] = *reinterpret_cast<const float4*>(xn + (long long)(b0 + q) * N);
+                        xv[q][1] = *reinterpret_cast<const float4*>(xn + (long long)(b0 + q) * N + 2);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 x0 = make_float2(xv[q][0].x, xv[q][0].y), x1 = make_float2(xv[q][0].z, xv[q][0].w);
+                        const float2 x2 = make_float2(xv[q][1].x, xv[q][1].y), x3 = make_float2(xv[q][1].z, xv[q][1].w);
+#pragma unroll
+                        for (int c = 0; c < H; ++c) {
+                            const float2 av = Ad[(b0 + q) * D + c];
+                            cfma(a[c][0], av, x0);
+                            cfma(a[c][1], av, x1);
+                            cfma(a[c][2], av, x2);
+                            cfma(a[c][3], av, x3);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < H; ++c) {
+                const long long idx = ((long long)site * D + h * H + c) * N + j;
+                float2 o[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
+                if (MODE == 1) {
+                    const float4 b0v = *reinterpret_cast<const float4*>(b + idx);
+                    const float4 b1v = *reinterpret_cast<const float4*>(b + idx + 2);
+                    o[0] = make_float2(b0v.x - o[0].x, b0v.y - o[0].y);
+                    o[1] = make_float2(b0v.z - o[1].x, b0v.w - o[1].y);
+                    o[2] = make_float2(b1v.x - o[2].x, b1v.y - o[2].y);
+                    o[3] = make_float2(b1v.z - o[3].x, b1v.w - o[3].y);
+                }
+                *reinterpret_cast<float4*>(y + idx) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                *reinterpret_cast<float4*>(y + idx + 2) = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+                if (MODE == 2) {
+                    const float4 x0v = *reinterpret_cast<const float4*>(x + idx);
+                    const float4 x1v = *reinterpret_cast<const float4*>(x + idx + 2);
+                    const float2 xs[4] = {make_float2(x0v.x, x0v.y), make_float2(x0v.z, x0v.w),
+                                          make_float2(x1v.x, x1v.y), make_float2(x1v.z, x1v.w)};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        cfmac(dyx[r], o[r], xs[r]);
+                        dyy[r] = fmaf(o[r].x, o[r].x, fmaf(o[r].y, o[r].y, dyy[r]));
+                    }
+                }
+            }
+        }
+    }
+    if (MODE == 2) {
+        // half 1 hands its sums to half 0, which writes the per-rhs partials
+        if (h == 1)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                red[tq * 12 + 3 * r] = dyx[r].x;
+                red[tq * 12 + 3 * r + 1] = dyx[r].y;
+                red[tq * 12 + 3 * r + 2] = dyy[r];
+            }
+        __syncthreads();
+        if (h == 0 && j < N) {
+            const long long G = gridDim.y;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float2 s = make_float2(dyx[r].x + red[tq * 12 + 3 * r], dyx[r].y + red[tq * 12 + 3 * r + 1]);
+                part[((long long)0 * N + j + r) * G + blockIdx.y] = to_d(s);
+                part[((long long)1 * N + j + r) * G + blockIdx.y] =
+                    make_double2((double)(dyy[r] + red[tq * 12 + 3 * r + 2]), 0.0);
+            }
+        }
+    }
+}
+
 // Narrow-block variant (few rhs, as in the setup solves): thread (tx < 8 rhs,
 // ty < D output row); the blocks of the site are staged in shared memory.
 template <typename C, int D, int MODE>
@@ -1060,6 +1174,18 @@ template <int D>
 static bool bsd_f2(float2* y, const float2* x, const float2* b, const float2* A, int lx, int lt, int N, int mode,
                    double2* part, int groups, cudaStream_t s) {
     if (N % 2 != 0) return false;
+    if (D == 16 && N % 4 == 0 && N >= 128) {
+        // four rhs per thread; T threads per half of the output rows
+        const int T = std::min(64, (N / 4 + 31) / 32 * 32);
+        dim3 g((N / 4 + T - 1) / T, groups);
+        switch (mode) {
+            case 0: k_block_stencil_f4<0><<<g, 2 * T, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+            case 1: k_block_stencil_f4<1><<<g, 2 * T, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+            default: k_block_stencil_f4<2><<<g, 2 * T, 0, s>>>(y, x, b, A, lx, lt, N, part); break;
+        }
+        MG_LAUNCHED();
+        return true;
+    }
     const int threads = std::min(128, (N / 2 + 31) / 32 * 32);
     dim3 g((N / 2 + threads - 1) / threads, groups);
     switch (mode) {
