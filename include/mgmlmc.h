@@ -356,7 +356,8 @@ int mgmlmc_fma_peak(int precision, double* flops_per_s);
  * the library until the process exits; every call overwrites it entirely (no
  * part needs to start at zero), so calls that overlap on the GPU (different
  * streams or threads) race and must be serialised by the caller.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress).  The
+ * on a device looks up that array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture begins.  The
  * call runs on `stream` (a
  * cudaStream_t, NULL = default stream) and synchronises it before returning, to
  * read the kernel's status; MGMLMC_ETIMEOUT if a bounded wait inside the kernel
